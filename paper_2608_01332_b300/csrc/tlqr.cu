@@ -1,0 +1,784 @@
+// libtlqr: C ABI and runtime of the rake-compress solver (Alg. 1) on sm_103a.
+//
+// The runtime owns the device copy of the plan and the workspace of one
+// factorisation, and drives the per-round kernel sequence of kernels.cuh:
+//   factor: condense -> for each round {rake, absorb, compress}
+//           -> for each round backwards {expand} -> local factor
+//           -> for each round {compose transition matrices}
+//   solve:  affine init -> for each round {affine rake, absorb, compress}
+//           -> backwards {affine expand} -> local solve
+//           -> for each round {state compress} -> backwards {state expand}
+//           -> recover
+// In MIXED precision the factor and solve kernels run in FP32 and tlqr_solve
+// adds FP64 iterative refinement (FP64 residual eq. (kkt) -> FP32 correction
+// solve through the stored factors -> FP64 update).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/tlqr.h"
+#include "kernels.cuh"
+#include "plan.hpp"
+#include "residual.cuh"
+
+using namespace tlqr;
+
+namespace {
+
+constexpr int kMaxWarpsPerBlock = 8;
+constexpr size_t kSmemBudget = 200 * 1024;
+
+inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Shared memory of one warp for each kernel, in elements of T (+ ints).
+struct WarpBytes {
+  size_t condense, tau, compress, local_factor, compose_T, aff_init, vec1, local_solve, recover;
+};
+
+WarpBytes warp_bytes(int n, int m, size_t ts) {
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  WarpBytes w;
+  w.condense = align16(ts * (mm + 4 * nm));
+  w.tau = align16(ts * 5 * nn + 4 * n);
+  w.compress = align16(ts * 7 * nn + 4 * n);
+  w.local_factor = align16(ts * (5 * nn + 3 * nm + mm) + 4 * n);
+  w.compose_T = align16(ts * 2 * nn);
+  w.aff_init = align16(ts * (2 * nn + 2 * nm + 2 * n + m));
+  w.vec1 = align16(ts * (nn + n));
+  w.local_solve = align16(ts * (nn + nm + mm + 4 * n + m));
+  w.recover = align16(ts * (nn + nm + 2 * n + std::max(n, m)));
+  return w;
+}
+
+// Per-kind launch counters and optional CUDA-event timing of selected kinds.
+struct Profiler {
+  uint32_t mask = 0;
+  int64_t launches[TLQR_K_COUNT] = {}, units[TLQR_K_COUNT] = {};
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  ~Profiler() {
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// Launch `count` warps, each with `wbytes` of dynamic shared memory.
+template <typename Kernel, typename... Args>
+cudaError_t launch_warps(Profiler* prof, int kind, Kernel kernel, int count, size_t wbytes, cudaStream_t st,
+                         Args... args) {
+  if (count <= 0) return cudaSuccess;
+  int wpb = kMaxWarpsPerBlock;
+  if (wbytes > 0) wpb = (int)std::max<size_t>(1, std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / wbytes));
+  const size_t smem = wbytes * wpb;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = (count + wpb - 1) / wpb;
+  const bool timed = prof && (prof->mask >> kind) & 1u;
+  Profiler::Rec rec{kind, nullptr, nullptr};
+  if (timed) { rec.a = prof->get(); rec.b = prof->get(); cudaEventRecord(rec.a, st); }
+  kernel<<<blocks, 32 * wpb, smem, st>>>(args...);
+  cudaError_t e = cudaGetLastError();
+  if (timed) { cudaEventRecord(rec.b, st); prof->recs.push_back(rec); }
+  if (prof) { prof->launches[kind]++; prof->units[kind] += count; }
+  return e;
+}
+
+template <typename T>
+T* dalloc(size_t count, cudaError_t* err) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+  return (T*)p;
+}
+
+struct DevPlan {
+  int *rake_leaf = nullptr, *rake_parent = nullptr, *seg_parent = nullptr, *seg_start = nullptr;
+  int *comp_j = nullptr, *comp_i = nullptr, *comp_k = nullptr;
+  int *parent = nullptr, *child_start = nullptr, *child_list = nullptr;
+};
+
+}  // namespace
+
+struct tlqr_factor_t {
+  const tlqr_plan_t* plan = nullptr;
+  tlqr_options opt{};
+  int device = 0;
+  size_t ts = 8;                 // bytes per factor element
+  DevPlan dp;
+  std::vector<void*> allocs;
+  // factor workspace (typed by precision)
+  void *U = nullptr, *Ea = nullptr, *Ec = nullptr, *Ep = nullptr, *contrib = nullptr;
+  void *K = nullptr, *Tm = nullptr, *Tr = nullptr, *W = nullptr, *Finv = nullptr, *LG = nullptr;
+  void *h = nullptr, *z = nullptr, *s = nullptr, *cv = nullptr, *bv = nullptr, *kv = nullptr, *xs = nullptr;
+  unsigned char* dflag = nullptr;
+  int* status = nullptr;
+  // FP64 residual buffers and staging for host-memory calls
+  double *res_x = nullptr, *res_u = nullptr, *res_c = nullptr;
+  unsigned long long* maxes = nullptr;
+  unsigned long long* h_maxes = nullptr;   // pinned mirror
+  int* h_status = nullptr;                  // pinned mirror
+  double* stage = nullptr;                  // FP64 staging (host-memory calls), lazily allocated
+  size_t stage_elems = 0;
+  // problem pointers of the last factorisation (device), for refinement/residual
+  tlqr_problem dprob{};
+  bool factored = false;
+  tlqr_info info{};
+  Profiler prof;
+
+  template <typename T>
+  Ws<T> ws(const tlqr_problem& p) const {
+    Ws<T> w{};
+    const tlqr_plan_t* P = plan;
+    w.N = P->N; w.n = opt.n; w.m = opt.m; w.root = P->root;
+    w.has_M = opt.has_M; w.has_delta = opt.has_delta;
+    w.Q = p.Q; w.M = p.M; w.R = p.R; w.A = p.A; w.B = p.B; w.Delta = p.Delta;
+    w.q = p.q; w.r = p.r; w.c = p.c;
+    w.rake_leaf = dp.rake_leaf; w.rake_parent = dp.rake_parent; w.seg_parent = dp.seg_parent;
+    w.seg_start = dp.seg_start; w.comp_j = dp.comp_j; w.comp_i = dp.comp_i; w.comp_k = dp.comp_k;
+    w.parent = dp.parent; w.child_start = dp.child_start; w.child_list = dp.child_list;
+    w.U = (T*)U; w.Ea = (T*)Ea; w.Ec = (T*)Ec; w.Ep = (T*)Ep; w.contrib = (T*)contrib;
+    w.K = (T*)K; w.Tm = (T*)Tm; w.Tr = (T*)Tr; w.W = (T*)W; w.Finv = (T*)Finv; w.LG = (T*)LG;
+    w.dflag = dflag;
+    w.h = (T*)h; w.z = (T*)z; w.s = (T*)s; w.cv = (T*)cv; w.bv = (T*)bv; w.kv = (T*)kv; w.xs = (T*)xs;
+    w.status = status;
+    return w;
+  }
+  ~tlqr_factor_t() {
+    for (void* p : allocs) cudaFree(p);
+    if (h_maxes) cudaFreeHost(h_maxes);
+    if (h_status) cudaFreeHost(h_status);
+  }
+};
+
+namespace {
+
+int map_status(int st) {
+  switch (st) {
+    case ST_OK: return TLQR_OK;
+    case ST_NOT_PD: return TLQR_ERR_NOT_PD;
+    case ST_SINGULAR: return TLQR_ERR_SINGULAR;
+    case ST_NONFINITE: return TLQR_ERR_NONFINITE;
+    default: return TLQR_ERR_CUDA;
+  }
+}
+
+int upload_plan(tlqr_factor_t* f) {
+  const tlqr_plan_t* P = f->plan;
+  cudaError_t err = cudaSuccess;
+  auto up = [&](const std::vector<int32_t>& v, int** dst) {
+    *dst = dalloc<int>(v.size(), &err);
+    if (*dst) f->allocs.push_back(*dst);
+    if (err == cudaSuccess && !v.empty())
+      err = cudaMemcpy(*dst, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice);
+  };
+  up(P->rake_leaf, &f->dp.rake_leaf);
+  up(P->rake_parent, &f->dp.rake_parent);
+  up(P->seg_parent, &f->dp.seg_parent);
+  up(P->seg_start, &f->dp.seg_start);
+  up(P->comp_j, &f->dp.comp_j);
+  up(P->comp_i, &f->dp.comp_i);
+  up(P->comp_k, &f->dp.comp_k);
+  up(P->parent, &f->dp.parent);
+  up(P->child_start, &f->dp.child_start);
+  up(P->child_list, &f->dp.child_list);
+  if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? TLQR_ERR_OOM : TLQR_ERR_CUDA;
+  return TLQR_OK;
+}
+
+template <typename T>
+cudaError_t run_factor(tlqr_factor_t* f, const tlqr_problem& p, cudaStream_t st) {
+  const tlqr_plan_t* P = f->plan;
+  const Ws<T> w = f->ws<T>(p);
+  const WarpBytes wb = warp_bytes(f->opt.n, f->opt.m, sizeof(T));
+  cudaError_t e;
+  if ((e = launch_warps(&f->prof, TLQR_K_CONDENSE, k_condense<T>, P->N, wb.condense, st, w, (int)wb.condense))) return e;
+  for (const tlqr_round& rd : P->rounds) {
+    const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
+    if ((e = launch_warps(&f->prof, TLQR_K_RAKE, k_rake<T>, nr, wb.tau, st, w, rd.rake_begin, nr, (int)wb.tau))) return e;
+    if ((e = launch_warps(&f->prof, TLQR_K_ABSORB, k_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
+    if ((e = launch_warps(&f->prof, TLQR_K_COMPRESS, k_compress<T>, nc, wb.compress, st, w, rd.comp_begin, nc, (int)wb.compress))) return e;
+  }
+  for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
+    const int nc = it->comp_end - it->comp_begin;
+    if ((e = launch_warps(&f->prof, TLQR_K_EXPAND, k_expand<T>, nc, wb.tau, st, w, it->comp_begin, nc, (int)wb.tau))) return e;
+  }
+  if ((e = launch_warps(&f->prof, TLQR_K_LOCAL_FACTOR, k_local_factor<T>, P->N, wb.local_factor, st, w, (int)wb.local_factor))) return e;
+  for (const tlqr_round& rd : P->rounds) {
+    const int nc = rd.comp_end - rd.comp_begin;
+    if ((e = launch_warps(&f->prof, TLQR_K_COMPOSE_T, k_compose_T<T>, nc, wb.compose_T, st, w, rd.comp_begin, nc, (int)wb.compose_T))) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t run_solve(tlqr_factor_t* f, const double* q, const double* r, const double* c, double* x,
+                      double* u, double* y, int accumulate, cudaStream_t st) {
+  const tlqr_plan_t* P = f->plan;
+  tlqr_problem p = f->dprob;
+  p.q = q; p.r = r; p.c = c;
+  const Ws<T> w = f->ws<T>(p);
+  const WarpBytes wb = warp_bytes(f->opt.n, f->opt.m, sizeof(T));
+  cudaError_t e;
+  if ((e = launch_warps(&f->prof, TLQR_K_AFF_INIT, k_aff_init<T>, P->N, wb.aff_init, st, w, (int)wb.aff_init))) return e;
+  for (const tlqr_round& rd : P->rounds) {
+    const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
+    if ((e = launch_warps(&f->prof, TLQR_K_AFF_RAKE, k_aff_rake<T>, nr, wb.vec1, st, w, rd.rake_begin, nr, (int)wb.vec1))) return e;
+    if ((e = launch_warps(&f->prof, TLQR_K_AFF_ABSORB, k_aff_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
+    if ((e = launch_warps(&f->prof, TLQR_K_AFF_COMPRESS, k_aff_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
+  }
+  for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
+    const int nc = it->comp_end - it->comp_begin;
+    if ((e = launch_warps(&f->prof, TLQR_K_AFF_EXPAND, k_aff_expand<T>, nc, wb.vec1, st, w, it->comp_begin, nc, (int)wb.vec1))) return e;
+  }
+  if ((e = launch_warps(&f->prof, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w, (int)wb.local_solve))) return e;
+  for (const tlqr_round& rd : P->rounds) {
+    const int nc = rd.comp_end - rd.comp_begin;
+    if ((e = launch_warps(&f->prof, TLQR_K_STATE_COMPRESS, k_state_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
+  }
+  for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
+    const int nc = it->comp_end - it->comp_begin, nr = it->rake_end - it->rake_begin;
+    if ((e = launch_warps(&f->prof, TLQR_K_STATE_EXPAND, k_state_expand<T>, nc, wb.vec1, st, w, (const int*)f->dp.comp_j,
+                          (const int*)f->dp.comp_i, it->comp_begin, nc, (int)wb.vec1))) return e;
+    if ((e = launch_warps(&f->prof, TLQR_K_STATE_EXPAND, k_state_expand<T>, nr, wb.vec1, st, w, (const int*)f->dp.rake_leaf,
+                          (const int*)f->dp.rake_parent, it->rake_begin, nr, (int)wb.vec1))) return e;
+  }
+  return launch_warps(&f->prof, TLQR_K_RECOVER, k_recover<T>, P->N, wb.recover, st, w, x, u, y, accumulate, (int)wb.recover);
+}
+
+cudaError_t run_residual(tlqr_factor_t* f, const tlqr_problem& p, const double* x, const double* u,
+                         const double* y, cudaStream_t st) {
+  ResidualArgs a{};
+  const tlqr_plan_t* P = f->plan;
+  a.N = P->N; a.n = f->opt.n; a.m = f->opt.m; a.root = P->root;
+  a.parent = f->dp.parent; a.child_start = f->dp.child_start; a.child_list = f->dp.child_list;
+  a.Q = p.Q; a.q = p.q; a.M = f->opt.has_M ? p.M : nullptr; a.R = p.R; a.r = p.r; a.A = p.A;
+  a.B = p.B; a.c = p.c; a.Delta = f->opt.has_delta ? p.Delta : nullptr;
+  a.x = x; a.u = u; a.y = y;
+  a.res_x = f->res_x; a.res_u = f->res_u; a.res_c = f->res_c;
+  a.maxes = f->maxes;
+  cudaError_t e = cudaMemsetAsync(f->maxes, 0, 4 * sizeof(unsigned long long), st);
+  if (e) return e;
+  if ((e = launch_warps(&f->prof, TLQR_K_RESIDUAL, k_residual, P->N, 0, st, a))) return e;
+  return cudaMemcpyAsync(f->h_maxes, f->maxes, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+}
+
+void residual_stats(const tlqr_factor_t* f, double* abs_res, double* eta) {
+  double v[4];
+  for (int t = 0; t < 4; ++t) std::memcpy(&v[t], &f->h_maxes[t], sizeof(double));
+  *abs_res = v[0];
+  const double den = v[3] * v[1] + v[2];
+  *eta = den > 0 ? v[0] / den : v[0];
+  if (!std::isfinite(v[0])) *eta = INFINITY;
+}
+
+size_t problem_elems(int N, int n, int m) {
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m;
+  // Q q M R r A B c Delta  +  x u y P K
+  return (size_t)N * (nn + n + nm + (size_t)m * m + m + nn + nm + n + nn) + (size_t)N * (n + m + n + nn + nm);
+}
+
+int ensure_stage(tlqr_factor_t* f) {
+  if (f->stage) return TLQR_OK;
+  const size_t e = problem_elems(f->plan->N, f->opt.n, f->opt.m);
+  cudaError_t err = cudaSuccess;
+  f->stage = dalloc<double>(e, &err);
+  if (err != cudaSuccess) return TLQR_ERR_OOM;
+  f->allocs.push_back(f->stage);
+  f->stage_elems = e;
+  return TLQR_OK;
+}
+
+// Device staging layout for host-memory calls.
+struct Stage {
+  double *Q, *q, *M, *R, *r, *A, *B, *c, *Delta, *x, *u, *y, *P, *K;
+};
+Stage stage_layout(tlqr_factor_t* f) {
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  Stage s;
+  double* p = f->stage;
+  s.Q = p; p += N * n * n;
+  s.q = p; p += N * n;
+  s.M = p; p += N * n * m;
+  s.R = p; p += N * m * m;
+  s.r = p; p += N * m;
+  s.A = p; p += N * n * n;
+  s.B = p; p += N * n * m;
+  s.c = p; p += N * n;
+  s.Delta = p; p += N * n * n;
+  s.x = p; p += N * n;
+  s.u = p; p += N * m;
+  s.y = p; p += N * n;
+  s.P = p; p += N * n * n;
+  s.K = p;
+  return s;
+}
+
+cudaError_t h2d(double* dst, const double* src, size_t count, cudaStream_t st) {
+  if (!src || !count) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, st);
+}
+cudaError_t d2h(double* dst, const double* src, size_t count, cudaStream_t st) {
+  if (!dst || !count) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost, st);
+}
+
+// Copy a host-memory problem into staging and return the device view.
+int stage_problem(tlqr_factor_t* f, const tlqr_problem* in, tlqr_problem* out, bool matrices, bool rhs,
+                  cudaStream_t st) {
+  int rc = ensure_stage(f);
+  if (rc) return rc;
+  Stage s = stage_layout(f);
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  *out = *in;
+  out->mem = TLQR_MEM_DEVICE;
+  cudaError_t e = cudaSuccess;
+  if (matrices) {
+    if (!e) e = h2d(s.Q, in->Q, N * n * n, st);
+    if (!e && f->opt.has_M) e = h2d(s.M, in->M, N * n * m, st);
+    if (!e) e = h2d(s.R, in->R, N * m * m, st);
+    if (!e) e = h2d(s.A, in->A, N * n * n, st);
+    if (!e) e = h2d(s.B, in->B, N * n * m, st);
+    if (!e && f->opt.has_delta) e = h2d(s.Delta, in->Delta, N * n * n, st);
+    out->Q = s.Q; out->M = f->opt.has_M ? s.M : nullptr; out->R = s.R; out->A = s.A; out->B = s.B;
+    out->Delta = f->opt.has_delta ? s.Delta : nullptr;
+  }
+  if (rhs) {
+    if (!e) e = h2d(s.q, in->q, N * n, st);
+    if (!e) e = h2d(s.r, in->r, N * m, st);
+    if (!e) e = h2d(s.c, in->c, N * n, st);
+    out->q = s.q; out->r = s.r; out->c = s.c;
+  }
+  return e ? TLQR_ERR_CUDA : TLQR_OK;
+}
+
+int check_problem(const tlqr_factor_t* f, const tlqr_problem* p, bool rhs) {
+  if (!p) return TLQR_ERR_ARG;
+  if (p->mem != TLQR_MEM_DEVICE && p->mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
+  if (!p->Q || !p->R || !p->A || !p->B) return TLQR_ERR_ARG;
+  if ((f->opt.has_M != 0) != (p->M != nullptr)) return TLQR_ERR_ARG;
+  if ((f->opt.has_delta != 0) != (p->Delta != nullptr)) return TLQR_ERR_ARG;
+  if (rhs && (!p->q || !p->r || !p->c)) return TLQR_ERR_ARG;
+  return TLQR_OK;
+}
+
+// Read the device status word (synchronises the stream).
+int read_status(tlqr_factor_t* f, cudaStream_t st) {
+  if (cudaMemcpyAsync(f->h_status, f->status, sizeof(int), cudaMemcpyDeviceToHost, st)) return TLQR_ERR_CUDA;
+  if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+  return map_status(*f->h_status);
+}
+
+// Enqueue the factorisation; with `sync` also wait and report its status.
+int factor_impl(tlqr_factor_t* f, const tlqr_problem* dp, cudaStream_t st, bool sync) {
+  f->dprob = *dp;
+  f->factored = false;
+  if (cudaMemsetAsync(f->status, 0, sizeof(int), st)) return TLQR_ERR_CUDA;
+  cudaError_t e = f->ts == 8 ? run_factor<double>(f, *dp, st) : run_factor<float>(f, *dp, st);
+  if (e) return TLQR_ERR_CUDA;
+  f->factored = true;
+  if (!sync) return TLQR_OK;
+  const int rc = read_status(f, st);
+  if (rc != TLQR_OK) f->factored = false;
+  return rc;
+}
+
+cudaError_t solve_impl(tlqr_factor_t* f, const double* q, const double* r, const double* c, double* x,
+                       double* u, double* y, int accumulate, cudaStream_t st) {
+  return f->ts == 8 ? run_solve<double>(f, q, r, c, x, u, y, accumulate, st)
+                    : run_solve<float>(f, q, r, c, x, u, y, accumulate, st);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" const char* tlqr_status_string(int code) {
+  switch (code) {
+    case TLQR_OK: return "ok";
+    case TLQR_ERR_ARG: return "invalid argument";
+    case TLQR_ERR_TOPOLOGY: return "parent array is not a rooted tree";
+    case TLQR_ERR_NOT_PD: return "Cholesky of R or G failed (not positive definite)";
+    case TLQR_ERR_SINGULAR: return "singular or nonfinite pivot in I + C P or I + Delta P";
+    case TLQR_ERR_NONFINITE: return "non-finite value";
+    case TLQR_ERR_OOM: return "out of memory";
+    case TLQR_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TLQR_ERR_NO_CONVERGENCE: return "iterative refinement did not converge";
+    case TLQR_ERR_CUDA: return "CUDA runtime error";
+    case TLQR_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* opts, tlqr_factor_t** out) {
+  if (!plan || !opts || !out) return TLQR_ERR_ARG;
+  *out = nullptr;
+  const int n = opts->n, m = opts->m;
+  if (n < 1 || m < 1 || n > TLQR_MAX_DIM || m > TLQR_MAX_DIM) return TLQR_ERR_ARG;
+  if (opts->precision != TLQR_PREC_FP64 && opts->precision != TLQR_PREC_MIXED) return TLQR_ERR_ARG;
+  tlqr_factor_t* f = new (std::nothrow) tlqr_factor_t;
+  if (!f) return TLQR_ERR_OOM;
+  f->plan = plan;
+  f->opt = *opts;
+  if (f->opt.max_refine <= 0) f->opt.max_refine = 10;
+  if (!(f->opt.refine_tol > 0)) f->opt.refine_tol = 1e-8;
+  f->ts = opts->precision == TLQR_PREC_FP64 ? 8 : 4;
+  if (cudaGetDevice(&f->device)) { delete f; return TLQR_ERR_CUDA; }
+  // per-warp shared memory must fit one warp per block
+  const WarpBytes wb = warp_bytes(n, m, f->ts);
+  const size_t worst = std::max({wb.compress, wb.local_factor, wb.tau, wb.condense});
+  if (worst > kSmemBudget) { delete f; return TLQR_ERR_ARG; }
+  int rc = upload_plan(f);
+  if (rc) { delete f; return rc; }
+  const size_t N = plan->N, nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  const size_t nrake = std::max<size_t>(1, plan->rake_leaf.size());
+  cudaError_t err = cudaSuccess;
+  auto take = [&](size_t elems, size_t es) -> void* {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(1, elems) * es);
+    if (e != cudaSuccess) { if (err == cudaSuccess) err = e; return nullptr; }
+    f->allocs.push_back(p);
+    return p;
+  };
+  const size_t ts = f->ts;
+  f->U = take(N * nn, ts); f->Ea = take(N * nn, ts); f->Ec = take(N * nn, ts); f->Ep = take(N * nn, ts);
+  f->contrib = take(nrake * nn, ts);
+  f->K = take(N * nm, ts); f->Tm = take(N * nn, ts); f->Tr = take(N * nn, ts);
+  f->LG = take(N * mm, ts);
+  if (opts->has_delta) { f->W = take(N * nn, ts); f->Finv = take(N * nn, ts); }
+  f->h = take(N * n, ts); f->z = take(N * n, ts); f->s = take(N * n, ts); f->cv = take(nrake * n, ts);
+  f->bv = take(N * n, ts); f->kv = take(N * m, ts); f->xs = take(N * n, ts);
+  f->dflag = (unsigned char*)take(N, 1);
+  f->status = (int*)take(1, sizeof(int));
+  f->res_x = (double*)take(N * n, 8); f->res_u = (double*)take(N * m, 8); f->res_c = (double*)take(N * n, 8);
+  f->maxes = (unsigned long long*)take(4, 8);
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_maxes, 4 * sizeof(unsigned long long));
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_status, sizeof(int));
+  if (err == cudaSuccess && f->dflag) err = cudaMemset(f->dflag, 0, N);
+  if (err != cudaSuccess) {
+    delete f;
+    return err == cudaErrorMemoryAllocation ? TLQR_ERR_OOM : TLQR_ERR_CUDA;
+  }
+  *out = f;
+  return TLQR_OK;
+}
+
+extern "C" void tlqr_factor_destroy(tlqr_factor_t* f) { delete f; }
+
+extern "C" int tlqr_factor(tlqr_factor_t* f, const tlqr_problem* prob, void* stream) {
+  if (!f) return TLQR_ERR_ARG;
+  int rc = check_problem(f, prob, false);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  tlqr_problem dp = *prob;
+  if (prob->mem == TLQR_MEM_HOST) {
+    if ((rc = stage_problem(f, prob, &dp, true, false, st))) return rc;
+  }
+  return factor_impl(f, &dp, st, true);
+}
+
+extern "C" int tlqr_solve_rhs(tlqr_factor_t* f, int32_t mem, const double* q, const double* r,
+                              const double* c, double* x, double* u, double* y, void* stream) {
+  if (!f || !q || !r || !c || !x || !u || !y) return TLQR_ERR_ARG;
+  if (mem != TLQR_MEM_DEVICE && mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
+  if (!f->factored) return TLQR_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  if (mem == TLQR_MEM_DEVICE) {
+    if (solve_impl(f, q, r, c, x, u, y, 0, st)) return TLQR_ERR_CUDA;
+    return TLQR_OK;
+  }
+  int rc = ensure_stage(f);
+  if (rc) return rc;
+  Stage s = stage_layout(f);
+  cudaError_t e = h2d(s.q, q, N * n, st);
+  if (!e) e = h2d(s.r, r, N * m, st);
+  if (!e) e = h2d(s.c, c, N * n, st);
+  if (!e) e = solve_impl(f, s.q, s.r, s.c, s.x, s.u, s.y, 0, st);
+  if (!e) e = d2h(x, s.x, N * n, st);
+  if (!e) e = d2h(u, s.u, N * m, st);
+  if (!e) e = d2h(y, s.y, N * n, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  return e ? TLQR_ERR_CUDA : TLQR_OK;
+}
+
+extern "C" int tlqr_get_PK(tlqr_factor_t* f, int32_t mem, double* P, double* K, void* stream) {
+  if (!f) return TLQR_ERR_ARG;
+  if (!f->factored) return TLQR_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  double *dP = P, *dK = K;
+  if (mem == TLQR_MEM_HOST) {
+    int rc = ensure_stage(f);
+    if (rc) return rc;
+    Stage s = stage_layout(f);
+    dP = P ? s.P : nullptr;
+    dK = K ? s.K : nullptr;
+  }
+  const int blocks = 4 * 148;
+  if (f->ts == 8)
+    k_export_PK<double><<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, f->plan->root, (const double*)f->U,
+                                                (const double*)f->K, dP, dK);
+  else
+    k_export_PK<float><<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, f->plan->root, (const float*)f->U,
+                                               (const float*)f->K, dP, dK);
+  if (cudaGetLastError()) return TLQR_ERR_CUDA;
+  f->prof.launches[TLQR_K_EXPORT]++;
+  f->prof.units[TLQR_K_EXPORT] += N;
+  if (mem == TLQR_MEM_HOST) {
+    cudaError_t e = d2h(P, dP, N * n * n, st);
+    if (!e) e = d2h(K, dK, N * m * n, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return TLQR_ERR_CUDA;
+  }
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solution* sol, void* stream) {
+  if (!f || !sol || !sol->x || !sol->u || !sol->y) return TLQR_ERR_ARG;
+  if (sol->mem != TLQR_MEM_DEVICE && sol->mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
+  int rc = check_problem(f, prob, true);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  tlqr_problem dp = *prob;
+  if (prob->mem == TLQR_MEM_HOST) {
+    if ((rc = stage_problem(f, prob, &dp, true, true, st))) return rc;
+  }
+  double *x = sol->x, *u = sol->u, *y = sol->y;
+  if (sol->mem == TLQR_MEM_HOST) {
+    if ((rc = ensure_stage(f))) return rc;
+    Stage s = stage_layout(f);
+    x = s.x; u = s.u; y = s.y;
+  }
+  if ((rc = factor_impl(f, &dp, st, false))) return rc;
+  f->info = tlqr_info{};
+  if (solve_impl(f, dp.q, dp.r, dp.c, x, u, y, 0, st)) return TLQR_ERR_CUDA;
+  if (f->opt.precision == TLQR_PREC_MIXED) {
+    // FP64 iterative refinement through the FP32 factors
+    int steps = 0;
+    double absr = 0, eta = INFINITY;
+    for (;;) {
+      if (run_residual(f, dp, x, u, y, st)) return TLQR_ERR_CUDA;
+      if ((rc = read_status(f, st))) { f->factored = false; return rc; }
+      residual_stats(f, &absr, &eta);
+      if (eta <= f->opt.refine_tol || steps >= f->opt.max_refine || !std::isfinite(eta)) break;
+      if (solve_impl(f, f->res_x, f->res_u, f->res_c, x, u, y, 1, st)) return TLQR_ERR_CUDA;
+      ++steps;
+    }
+    f->info.refine_steps = steps;
+    f->info.eta = eta;
+    f->info.abs_residual = absr;
+    if (!std::isfinite(eta)) return TLQR_ERR_NONFINITE;
+    if (eta > f->opt.refine_tol) return TLQR_ERR_NO_CONVERGENCE;
+  }
+  if (sol->P || sol->K) {
+    if (sol->mem == TLQR_MEM_HOST) {
+      if ((rc = tlqr_get_PK(f, TLQR_MEM_HOST, sol->P, sol->K, stream))) return rc;
+    } else if ((rc = tlqr_get_PK(f, TLQR_MEM_DEVICE, sol->P, sol->K, stream))) {
+      return rc;
+    }
+  }
+  if (sol->mem == TLQR_MEM_HOST) {
+    cudaError_t e = d2h(sol->x, x, N * n, st);
+    if (!e) e = d2h(sol->u, u, N * m, st);
+    if (!e) e = d2h(sol->y, y, N * n, st);
+    if (e) return TLQR_ERR_CUDA;
+  }
+  // one status read for factor, solve and recovery (synchronises the stream)
+  if ((rc = read_status(f, st))) { f->factored = false; return rc; }
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_kkt_residual(tlqr_factor_t* f, const tlqr_problem* prob, int32_t mem, const double* x,
+                                 const double* u, const double* y, double* stats, void* stream) {
+  if (!f || !x || !u || !y || !stats) return TLQR_ERR_ARG;
+  int rc = check_problem(f, prob, true);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  tlqr_problem dp = *prob;
+  if (prob->mem == TLQR_MEM_HOST) {
+    if ((rc = stage_problem(f, prob, &dp, true, true, st))) return rc;
+  }
+  const double *dx = x, *du = u, *dy = y;
+  if (mem == TLQR_MEM_HOST) {
+    if ((rc = ensure_stage(f))) return rc;
+    Stage s = stage_layout(f);
+    if (h2d(s.x, x, N * n, st) || h2d(s.u, u, N * m, st) || h2d(s.y, y, N * n, st)) return TLQR_ERR_CUDA;
+    dx = s.x; du = s.u; dy = s.y;
+  }
+  if (run_residual(f, dp, dx, du, dy, st) || cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+  residual_stats(f, &stats[0], &stats[1]);
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_last_info(const tlqr_factor_t* f, tlqr_info* out) {
+  if (!f || !out) return TLQR_ERR_ARG;
+  *out = f->info;
+  return TLQR_OK;
+}
+
+// ------------------------------------------------------- batched primitives
+
+namespace {
+
+template <typename T>
+int batched_ops(int kind, int count, int n, int m, const double* const* in, double* const* out, cudaStream_t st) {
+  // Slots 0..count-1 hold the "left" data, count..2count-1 the "right" data.
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  const size_t S = 2 * (size_t)count;
+  std::vector<void*> mine;
+  cudaError_t err = cudaSuccess;
+  auto take = [&](size_t elems, size_t es) -> void* {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(1, elems) * es);
+    if (e != cudaSuccess) { if (err == cudaSuccess) err = e; return nullptr; }
+    mine.push_back(p);
+    return p;
+  };
+  Ws<T> w{};
+  w.N = count; w.n = n; w.m = m; w.root = -1;
+  T *U = (T*)take(S * nn, sizeof(T)), *Ea = (T*)take(S * nn, sizeof(T)), *Ec = (T*)take(S * nn, sizeof(T)),
+    *Ep = (T*)take(S * nn, sizeof(T)), *contrib = (T*)take(count * nn, sizeof(T));
+  int* idx = (int*)take(S, sizeof(int));
+  int* status = (int*)take(1, sizeof(int));
+  double* tmp = (double*)take(S * nn, sizeof(double));
+  if (err) { for (void* p : mine) cudaFree(p); return TLQR_ERR_OOM; }
+  std::vector<int> hidx(S);
+  for (size_t t = 0; t < S; ++t) hidx[t] = (int)t;
+  cudaMemcpyAsync(idx, hidx.data(), S * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  w.U = U; w.Ea = Ea; w.Ec = Ec; w.Ep = Ep; w.contrib = contrib; w.status = status;
+  const WarpBytes wb = warp_bytes(n, m, sizeof(T));
+  auto conv_in = [&](T* dst, const double* src, size_t elems) {   // FP64 -> T via the load kernel path
+    if (sizeof(T) == 8) cudaMemcpyAsync(dst, src, elems * 8, cudaMemcpyDeviceToDevice, st);
+    else {
+      std::vector<double> h(elems);
+      std::vector<float> hf(elems);
+      cudaMemcpyAsync(h.data(), src, elems * 8, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      for (size_t e = 0; e < elems; ++e) hf[e] = (float)h[e];
+      cudaMemcpyAsync(dst, hf.data(), elems * 4, cudaMemcpyHostToDevice, st);
+      cudaStreamSynchronize(st);
+    }
+  };
+  auto conv_out = [&](double* dst, const T* src, size_t elems) {
+    if (sizeof(T) == 8) cudaMemcpyAsync(dst, src, elems * 8, cudaMemcpyDeviceToDevice, st);
+    else {
+      std::vector<float> hf(elems);
+      std::vector<double> h(elems);
+      cudaMemcpyAsync(hf.data(), src, elems * 4, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      for (size_t e = 0; e < elems; ++e) h[e] = hf[e];
+      cudaMemcpyAsync(dst, h.data(), elems * 8, cudaMemcpyHostToDevice, st);
+      cudaStreamSynchronize(st);
+    }
+  };
+  cudaError_t e = cudaSuccess;
+  if (kind == 0) {              // tau: in = A, C, P, U
+    conv_in(Ea, in[0], count * nn); conv_in(Ec, in[1], count * nn);
+    conv_in(Ep, in[2], count * nn); conv_in(U, in[3], count * nn);
+    w.rake_leaf = idx;
+    e = launch_warps(nullptr, TLQR_K_RAKE, k_rake<T>, count, wb.tau, st, w, 0, count, (int)wb.tau);
+    conv_out(out[0], contrib, count * nn);
+  } else if (kind == 1) {       // compose: in = Al Cl Pl Ar Cr Pr U
+    conv_in(Ea, in[0], count * nn); conv_in(Ec, in[1], count * nn); conv_in(Ep, in[2], count * nn);
+    conv_in(Ea + count * nn, in[3], count * nn); conv_in(Ec + count * nn, in[4], count * nn);
+    conv_in(Ep + count * nn, in[5], count * nn); conv_in(U, in[6], count * nn);
+    w.comp_j = idx; w.comp_k = idx + count;
+    e = launch_warps(nullptr, TLQR_K_COMPRESS, k_compress<T>, count, wb.compress, st, w, 0, count, (int)wb.compress);
+    conv_out(out[0], Ea + count * nn, count * nn); conv_out(out[1], Ec + count * nn, count * nn);
+    conv_out(out[2], Ep + count * nn, count * nn); conv_out(out[3], Ep, count * nn);
+  } else {                      // condense: in = A B R M Delta
+    w.A = in[0]; w.B = in[1]; w.R = in[2]; w.M = in[3]; w.Delta = in[4];
+    w.has_M = in[3] != nullptr; w.has_delta = in[4] != nullptr;
+    w.Q = tmp;  // U <- Q is part of the kernel; feed zeros
+    cudaMemsetAsync(tmp, 0, count * nn * sizeof(double), st);
+    unsigned char* flags = (unsigned char*)take(count, 1);
+    w.dflag = flags;
+    e = launch_warps(nullptr, TLQR_K_CONDENSE, k_condense<T>, count, wb.condense, st, w, (int)wb.condense);
+    conv_out(out[0], Ea, count * nn); conv_out(out[1], Ec, count * nn); conv_out(out[2], Ep, count * nn);
+  }
+  int hs = 0;
+  if (!e) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  for (void* p : mine) cudaFree(p);
+  if (e) return TLQR_ERR_CUDA;
+  (void)mm; (void)nm;
+  return map_status(hs);
+}
+
+}  // namespace
+
+extern "C" int tlqr_batched_tau(int32_t count, int32_t n, const double* A, const double* C,
+                                const double* P, const double* U, double* out, int32_t precision,
+                                void* stream) {
+  if (count < 1 || n < 1 || n > TLQR_MAX_DIM || !A || !C || !P || !U || !out) return TLQR_ERR_ARG;
+  const double* in[4] = {A, C, P, U};
+  double* o[1] = {out};
+  return precision == TLQR_PREC_FP64 ? batched_ops<double>(0, count, n, 1, in, o, (cudaStream_t)stream)
+                                     : batched_ops<float>(0, count, n, 1, in, o, (cudaStream_t)stream);
+}
+
+extern "C" int tlqr_batched_compose(int32_t count, int32_t n, const double* Al, const double* Cl,
+                                    const double* Pl, const double* Ar, const double* Cr, const double* Pr,
+                                    const double* U, double* An, double* Cn, double* Pn, double* Pt,
+                                    int32_t precision, void* stream) {
+  if (count < 1 || n < 1 || n > TLQR_MAX_DIM || !Al || !Cl || !Pl || !Ar || !Cr || !Pr || !U || !An || !Cn ||
+      !Pn || !Pt)
+    return TLQR_ERR_ARG;
+  const double* in[7] = {Al, Cl, Pl, Ar, Cr, Pr, U};
+  double* o[4] = {An, Cn, Pn, Pt};
+  return precision == TLQR_PREC_FP64 ? batched_ops<double>(1, count, n, 1, in, o, (cudaStream_t)stream)
+                                     : batched_ops<float>(1, count, n, 1, in, o, (cudaStream_t)stream);
+}
+
+extern "C" int tlqr_batched_condense(int32_t count, int32_t n, int32_t m, const double* A, const double* B,
+                                     const double* R, const double* M, const double* Delta, double* Abar,
+                                     double* Cbar, double* Pbar, int32_t precision, void* stream) {
+  if (count < 1 || n < 1 || m < 1 || n > TLQR_MAX_DIM || m > TLQR_MAX_DIM || !A || !B || !R || !Abar ||
+      !Cbar || !Pbar)
+    return TLQR_ERR_ARG;
+  const double* in[5] = {A, B, R, M, Delta};
+  double* o[3] = {Abar, Cbar, Pbar};
+  return precision == TLQR_PREC_FP64 ? batched_ops<double>(2, count, n, m, in, o, (cudaStream_t)stream)
+                                     : batched_ops<float>(2, count, n, m, in, o, (cudaStream_t)stream);
+}
+
+extern "C" int tlqr_profile_mask(tlqr_factor_t* f, uint32_t mask) {
+  if (!f) return TLQR_ERR_ARG;
+  f->prof.mask = mask;
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_profile_read(tlqr_factor_t* f, tlqr_kernel_profile* out) {
+  if (!f || !out) return TLQR_ERR_ARG;
+  for (int k = 0; k < TLQR_K_COUNT; ++k) out[k] = tlqr_kernel_profile{f->prof.launches[k], f->prof.units[k], 0, 0.0};
+  int rc = TLQR_OK;
+  for (auto& r : f->prof.recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) rc = TLQR_ERR_CUDA;
+    out[r.kind].timed++;
+    out[r.kind].ms += ms;
+    f->prof.pool.push_back(r.a);
+    f->prof.pool.push_back(r.b);
+  }
+  f->prof.recs.clear();
+  for (int k = 0; k < TLQR_K_COUNT; ++k) { f->prof.launches[k] = 0; f->prof.units[k] = 0; }
+  return rc;
+}

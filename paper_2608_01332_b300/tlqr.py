@@ -1,0 +1,380 @@
+"""Python binding of libtlqr (include/tlqr.h): argument marshalling only.
+
+Every function keeps the C name.  Arrays are float64 and C-contiguous:
+numpy arrays are passed as host memory (TLQR_MEM_HOST), CUDA torch tensors as
+device memory (TLQR_MEM_DEVICE).  All arithmetic happens in the CUDA library;
+if it cannot be loaded the import-time call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libtlqr.so")
+
+TLQR_OK = 0
+TLQR_MEM_DEVICE, TLQR_MEM_HOST = 0, 1
+TLQR_PREC_FP64, TLQR_PREC_MIXED = 0, 1
+TLQR_OP_ROOT, TLQR_OP_RAKE, TLQR_OP_COMPRESS = 0, 1, 2
+TLQR_MAX_DIM = 64
+STATUS_NAMES = {0: "TLQR_OK", 1: "TLQR_ERR_ARG", 2: "TLQR_ERR_TOPOLOGY", 3: "TLQR_ERR_NOT_PD",
+                4: "TLQR_ERR_SINGULAR", 5: "TLQR_ERR_NONFINITE", 6: "TLQR_ERR_OOM",
+                7: "TLQR_ERR_TIMEOUT", 8: "TLQR_ERR_NO_CONVERGENCE", 9: "TLQR_ERR_CUDA",
+                10: "TLQR_ERR_STATE"}
+
+_i32 = ctypes.c_int32
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_vp = ctypes.c_void_p
+
+
+class TLQRError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} ({tlqr_status_string(code)})")
+
+
+class tlqr_options(ctypes.Structure):
+    _fields_ = [("n", _i32), ("m", _i32), ("precision", _i32), ("has_M", _i32), ("has_delta", _i32),
+                ("max_refine", _i32), ("refine_tol", ctypes.c_double), ("use_graphs", _i32),
+                ("reserved", _i32 * 7)]
+
+
+class tlqr_problem(ctypes.Structure):
+    _fields_ = [("mem", _i32), ("Q", _dp), ("q", _dp), ("M", _dp), ("R", _dp), ("r", _dp),
+                ("A", _dp), ("B", _dp), ("c", _dp), ("Delta", _dp)]
+
+
+class tlqr_solution(ctypes.Structure):
+    _fields_ = [("mem", _i32), ("x", _dp), ("u", _dp), ("y", _dp), ("P", _dp), ("K", _dp)]
+
+
+class tlqr_plan_stats_t(ctypes.Structure):
+    _fields_ = [(k, _i32) for k in ("N", "root", "rounds", "n_rake", "n_compress", "n_combine",
+                                    "n_absorb", "levels", "height", "max_degree")]
+
+
+class tlqr_kernel_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("units", ctypes.c_int64), ("timed", ctypes.c_int64),
+                ("ms", ctypes.c_double)]
+
+
+class tlqr_info(ctypes.Structure):
+    _fields_ = [("refine_steps", _i32), ("eta", ctypes.c_double), ("abs_residual", ctypes.c_double)]
+
+
+_lib = None
+EXPORTS = ["tlqr_plan_create", "tlqr_plan_destroy", "tlqr_plan_stats", "tlqr_plan_schedule",
+           "tlqr_factor_create", "tlqr_factor_destroy", "tlqr_factor", "tlqr_solve_rhs", "tlqr_solve",
+           "tlqr_get_PK", "tlqr_kkt_residual", "tlqr_last_info", "tlqr_status_string",
+           "tlqr_batched_tau", "tlqr_batched_compose", "tlqr_batched_condense",
+           "tlqr_lift_node_controls", "tlqr_project_lifted", "tlqr_profile_mask", "tlqr_profile_read"]
+
+KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
+                "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
+                "state_expand", "recover", "residual", "export"]
+
+
+def lib():
+    """Load libtlqr.so (building it first if it is missing or older than its sources)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        try:
+            _build.build()
+        except (OSError, FileNotFoundError) as e:   # no nvcc: use what is there, or fail below
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"libtlqr.so is missing and cannot be built: {e}") from e
+        L = ctypes.CDLL(_LIB_PATH)
+        L.tlqr_status_string.restype = ctypes.c_char_p
+        L.tlqr_status_string.argtypes = [ctypes.c_int]
+        L.tlqr_plan_create.argtypes = [_ip, _i32, ctypes.POINTER(_vp)]
+        L.tlqr_plan_destroy.argtypes = [_vp]
+        L.tlqr_plan_destroy.restype = None
+        L.tlqr_plan_stats.argtypes = [_vp, ctypes.POINTER(tlqr_plan_stats_t)]
+        L.tlqr_plan_schedule.argtypes = [_vp, _ip, _ip]
+        L.tlqr_factor_create.argtypes = [_vp, ctypes.POINTER(tlqr_options), ctypes.POINTER(_vp)]
+        L.tlqr_factor_destroy.argtypes = [_vp]
+        L.tlqr_factor_destroy.restype = None
+        L.tlqr_factor.argtypes = [_vp, ctypes.POINTER(tlqr_problem), _vp]
+        L.tlqr_solve_rhs.argtypes = [_vp, _i32, _dp, _dp, _dp, _dp, _dp, _dp, _vp]
+        L.tlqr_solve.argtypes = [_vp, ctypes.POINTER(tlqr_problem), ctypes.POINTER(tlqr_solution), _vp]
+        L.tlqr_get_PK.argtypes = [_vp, _i32, _dp, _dp, _vp]
+        L.tlqr_kkt_residual.argtypes = [_vp, ctypes.POINTER(tlqr_problem), _i32, _dp, _dp, _dp, _dp, _vp]
+        L.tlqr_last_info.argtypes = [_vp, ctypes.POINTER(tlqr_info)]
+        L.tlqr_batched_tau.argtypes = [_i32, _i32] + [_dp] * 5 + [_i32, _vp]
+        L.tlqr_batched_compose.argtypes = [_i32, _i32] + [_dp] * 11 + [_i32, _vp]
+        L.tlqr_batched_condense.argtypes = [_i32, _i32, _i32] + [_dp] * 8 + [_i32, _vp]
+        L.tlqr_lift_node_controls.argtypes = [_ip, _i32, _i32, _i32] + [_dp] * 9 + [_ip, _ip] + [_dp] * 9 + [_ip]
+        L.tlqr_project_lifted.argtypes = [_i32, _i32, _i32, _ip] + [_dp] * 6
+        L.tlqr_profile_mask.argtypes = [_vp, ctypes.c_uint32]
+        L.tlqr_profile_read.argtypes = [_vp, ctypes.POINTER(tlqr_kernel_profile)]
+        _lib = L
+    return _lib
+
+
+def tlqr_status_string(code: int) -> str:
+    return lib().tlqr_status_string(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != TLQR_OK:
+        raise TLQRError(rc, where)
+
+
+# ------------------------------------------------------------------ pointers
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _mem_of(a) -> int:
+    if a is None:
+        return -1
+    if _is_torch(a):
+        return TLQR_MEM_DEVICE if a.is_cuda else TLQR_MEM_HOST
+    return TLQR_MEM_HOST
+
+
+def _ptr(a):
+    """float64 contiguous array -> double*; None -> NULL."""
+    if a is None:
+        return _dp()
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be float64 and contiguous")
+        return ctypes.cast(ctypes.c_void_p(a.data_ptr()), _dp)
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("arrays must be float64 and C-contiguous")
+    return a.ctypes.data_as(_dp)
+
+
+def _iptr(a):
+    if a is None:
+        return _ip()
+    if a.dtype != np.int32 or not a.flags.c_contiguous:
+        raise TypeError("index arrays must be int32 and C-contiguous")
+    return a.ctypes.data_as(_ip)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _mem_all(arrays) -> int:
+    mems = {_mem_of(a) for a in arrays if a is not None}
+    if len(mems) != 1:
+        raise ValueError("all arrays of one call must be host arrays or all CUDA tensors")
+    return mems.pop()
+
+
+# ------------------------------------------------------------------ plan
+
+def tlqr_plan_create(parent) -> ctypes.c_void_p:
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    h = _vp()
+    _check(lib().tlqr_plan_create(_iptr(parent), len(parent), ctypes.byref(h)), "tlqr_plan_create")
+    return h
+
+
+def tlqr_plan_destroy(plan) -> None:
+    lib().tlqr_plan_destroy(plan)
+
+
+def tlqr_plan_stats(plan) -> dict:
+    s = tlqr_plan_stats_t()
+    _check(lib().tlqr_plan_stats(plan, ctypes.byref(s)), "tlqr_plan_stats")
+    return {k: getattr(s, k) for k, _ in tlqr_plan_stats_t._fields_}
+
+
+def tlqr_plan_schedule(plan, N: int):
+    rnd = np.zeros(N, dtype=np.int32)
+    op = np.zeros(N, dtype=np.int32)
+    _check(lib().tlqr_plan_schedule(plan, _iptr(rnd), _iptr(op)), "tlqr_plan_schedule")
+    return rnd, op
+
+
+# ------------------------------------------------------------------ factor / solve
+
+def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
+                 refine_tol=1e-8, use_graphs=False) -> tlqr_options:
+    o = tlqr_options()
+    o.n, o.m, o.precision = int(n), int(m), int(precision)
+    o.has_M, o.has_delta = int(bool(has_M)), int(bool(has_delta))
+    o.max_refine, o.refine_tol, o.use_graphs = int(max_refine), float(refine_tol), int(bool(use_graphs))
+    return o
+
+
+def tlqr_factor_create(plan, opts: tlqr_options) -> ctypes.c_void_p:
+    h = _vp()
+    _check(lib().tlqr_factor_create(plan, ctypes.byref(opts), ctypes.byref(h)), "tlqr_factor_create")
+    return h
+
+
+def tlqr_factor_destroy(f) -> None:
+    lib().tlqr_factor_destroy(f)
+
+
+def make_problem(data: dict) -> tlqr_problem:
+    keys = ("Q", "q", "M", "R", "r", "A", "B", "c", "Delta")
+    p = tlqr_problem()
+    p.mem = _mem_all([data.get(k) for k in keys])
+    for k in keys:
+        setattr(p, k, _ptr(data.get(k)))
+    return p
+
+
+def make_solution(x, u, y, P=None, K=None) -> tlqr_solution:
+    s = tlqr_solution()
+    s.mem = _mem_all([x, u, y, P, K])
+    s.x, s.u, s.y, s.P, s.K = _ptr(x), _ptr(u), _ptr(y), _ptr(P), _ptr(K)
+    return s
+
+
+def tlqr_factor(f, data: dict, stream=None) -> None:
+    p = make_problem(data)
+    _check(lib().tlqr_factor(f, ctypes.byref(p), _stream(stream)), "tlqr_factor")
+
+
+def tlqr_solve(f, data: dict, x, u, y, P=None, K=None, stream=None) -> None:
+    p = make_problem(data)
+    s = make_solution(x, u, y, P, K)
+    _check(lib().tlqr_solve(f, ctypes.byref(p), ctypes.byref(s), _stream(stream)), "tlqr_solve")
+
+
+def tlqr_solve_rhs(f, q, r, c, x, u, y, stream=None) -> None:
+    mem = _mem_all([q, r, c, x, u, y])
+    _check(lib().tlqr_solve_rhs(f, mem, _ptr(q), _ptr(r), _ptr(c), _ptr(x), _ptr(u), _ptr(y),
+                                _stream(stream)), "tlqr_solve_rhs")
+
+
+def tlqr_get_PK(f, P, K, stream=None) -> None:
+    mem = _mem_all([P, K])
+    _check(lib().tlqr_get_PK(f, mem, _ptr(P), _ptr(K), _stream(stream)), "tlqr_get_PK")
+
+
+def tlqr_kkt_residual(f, data: dict, x, u, y, stream=None):
+    p = make_problem(data)
+    mem = _mem_all([x, u, y])
+    st = np.zeros(2)
+    _check(lib().tlqr_kkt_residual(f, ctypes.byref(p), mem, _ptr(x), _ptr(u), _ptr(y), _ptr(st),
+                                   _stream(stream)), "tlqr_kkt_residual")
+    return dict(abs=float(st[0]), eta=float(st[1]))
+
+
+def tlqr_last_info(f) -> dict:
+    i = tlqr_info()
+    _check(lib().tlqr_last_info(f, ctypes.byref(i)), "tlqr_last_info")
+    return dict(refine_steps=i.refine_steps, eta=i.eta, abs_residual=i.abs_residual)
+
+
+def tlqr_profile_mask(f, kinds) -> None:
+    """Time the launches of the named kernel kinds with CUDA events (empty = off)."""
+    mask = 0
+    for k in kinds:
+        mask |= 1 << KERNEL_KINDS.index(k)
+    _check(lib().tlqr_profile_mask(f, mask), "tlqr_profile_mask")
+
+
+def tlqr_profile_read(f) -> dict:
+    arr = (tlqr_kernel_profile * len(KERNEL_KINDS))()
+    _check(lib().tlqr_profile_read(f, arr), "tlqr_profile_read")
+    return {k: dict(launches=a.launches, units=a.units, timed=a.timed, ms=a.ms)
+            for k, a in zip(KERNEL_KINDS, arr)}
+
+
+# ------------------------------------------------------------------ batched primitives (device)
+
+def tlqr_batched_tau(A, C, P, U, out, precision=TLQR_PREC_FP64, stream=None) -> None:
+    count, n = A.shape[0], A.shape[1]
+    _check(lib().tlqr_batched_tau(count, n, _ptr(A), _ptr(C), _ptr(P), _ptr(U), _ptr(out), precision,
+                                  _stream(stream)), "tlqr_batched_tau")
+
+
+def tlqr_batched_compose(Al, Cl, Pl, Ar, Cr, Pr, U, An, Cn, Pn, Pt, precision=TLQR_PREC_FP64,
+                         stream=None) -> None:
+    count, n = Al.shape[0], Al.shape[1]
+    _check(lib().tlqr_batched_compose(count, n, *[_ptr(a) for a in (Al, Cl, Pl, Ar, Cr, Pr, U, An, Cn, Pn, Pt)],
+                                      precision, _stream(stream)), "tlqr_batched_compose")
+
+
+def tlqr_batched_condense(A, B, R, M, Delta, Abar, Cbar, Pbar, precision=TLQR_PREC_FP64, stream=None) -> None:
+    count, n, m = B.shape
+    _check(lib().tlqr_batched_condense(count, n, m, *[_ptr(a) for a in (A, B, R, M, Delta, Abar, Cbar, Pbar)],
+                                       precision, _stream(stream)), "tlqr_batched_condense")
+
+
+# ------------------------------------------------------------------ lifting (host)
+
+def tlqr_lift_node_controls(parent, n: int, m: int, nd: dict) -> dict:
+    """Prop. 2 lifting; nd holds Q, q, Mv, Rv, rv, Av, Bv, c, Delta (numpy, node-indexed)."""
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    N = len(parent)
+    Nl = _i32(0)
+    L = lib()
+    args = [_ptr(np.ascontiguousarray(nd[k], dtype=np.float64)) if nd.get(k) is not None else _dp()
+            for k in ("Q", "q", "Mv", "Rv", "rv", "Av", "Bv", "c", "Delta")]
+    _check(L.tlqr_lift_node_controls(_iptr(parent), N, n, m, *args, ctypes.byref(Nl), _ip(),
+                                     *([_dp()] * 9), _ip()), "tlqr_lift_node_controls")
+    Nl = Nl.value
+    s = n + m
+    out = dict(parent=np.zeros(Nl, dtype=np.int32), Q=np.zeros((Nl, s, s)), q=np.zeros((Nl, s)),
+               M=np.zeros((Nl, s, m)), R=np.zeros((Nl, m, m)), r=np.zeros((Nl, m)),
+               A=np.zeros((Nl, s, s)), B=np.zeros((Nl, s, m)), c=np.zeros((Nl, s)),
+               Delta=np.zeros((Nl, s, s)), map=np.zeros(2 * N, dtype=np.int32))
+    nl = _i32(0)
+    _check(L.tlqr_lift_node_controls(_iptr(parent), N, n, m, *args, ctypes.byref(nl), _iptr(out["parent"]),
+                                     *[_ptr(out[k]) for k in ("Q", "q", "M", "R", "r", "A", "B", "c", "Delta")],
+                                     _iptr(out["map"])), "tlqr_lift_node_controls")
+    return out
+
+
+def tlqr_project_lifted(N: int, n: int, m: int, lmap, lx, lu, ly):
+    x = np.zeros((N, n)); v = np.zeros((N, m)); y = np.zeros((N, n))
+    _check(lib().tlqr_project_lifted(N, n, m, _iptr(np.ascontiguousarray(lmap, dtype=np.int32)),
+                                     _ptr(np.ascontiguousarray(lx)), _ptr(np.ascontiguousarray(lu)),
+                                     _ptr(np.ascontiguousarray(ly)), _ptr(x), _ptr(v), _ptr(y)),
+           "tlqr_project_lifted")
+    return x, v, y
+
+
+# ------------------------------------------------------------------ ownership helper
+
+class TreeLQR:
+    """Owns one plan and one factor object; every method is a direct C call."""
+
+    def __init__(self, parent, n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, **kw):
+        self.parent = np.ascontiguousarray(parent, dtype=np.int32)
+        self.N, self.n, self.m = len(self.parent), int(n), int(m)
+        self.plan = tlqr_plan_create(self.parent)
+        self.opts = make_options(n, m, precision, has_M, has_delta, **kw)
+        try:
+            self.f = tlqr_factor_create(self.plan, self.opts)
+        except Exception:
+            tlqr_plan_destroy(self.plan)
+            raise
+
+    def stats(self):
+        return tlqr_plan_stats(self.plan)
+
+    def close(self):
+        if getattr(self, "f", None):
+            tlqr_factor_destroy(self.f)
+            self.f = None
+        if getattr(self, "plan", None):
+            tlqr_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

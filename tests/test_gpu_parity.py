@@ -1,0 +1,318 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (derived from the arithmetic; the benchmark spec's targets are stated as
+backward errors):
+  * FP64 path: eta <= 1e-10 (normwise backward error of eq. (kkt)); elementwise
+    |z - z_oracle| <= 1e-8 max|z_oracle| for z = (x, u, y), and P, K within
+    1e-8 of the oracle relative to their largest entry.  Both sides are
+    backward stable FP64 methods on well-conditioned data, so their difference
+    is a few hundred ulps times the condition number.
+  * MIXED path (FP32 factors + FP64 refinement): eta <= 1e-8 after
+    refinement; forward error vs the oracle <= 1e-6.
+  * Batched primitives: FP64 within 1e-10 relative; FP32 within 2e-4 relative
+    (n <= 16, a few FP32 roundings amplified by the local condition number).
+"""
+import numpy as np
+import pytest
+
+from oracle import ops, riccati
+from paper_2608_01332_b300 import inputs, tlqr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = tlqr.TLQR_PREC_FP64, tlqr.TLQR_PREC_MIXED
+
+
+def dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def gpu_solve(parent, n, m, data, precision=FP64, host=False, want_PK=True, **kw):
+    N = len(parent)
+    s = tlqr.TreeLQR(parent, n, m, precision, has_M=data.get("M") is not None,
+                     has_delta=data.get("Delta") is not None, **kw)
+    try:
+        if host:
+            d = {k: (None if v is None else np.ascontiguousarray(v)) for k, v in data.items()}
+            x, u, y = np.zeros((N, n)), np.zeros((N, m)), np.zeros((N, n))
+            P, K = (np.zeros((N, n, n)), np.zeros((N, m, n))) if want_PK else (None, None)
+            tlqr.tlqr_solve(s.f, d, x, u, y, P, K)
+            out = dict(x=x, u=u, y=y, P=P, K=K)
+        else:
+            d = {k: dev(v) for k, v in data.items()}
+            x = torch.zeros((N, n), dtype=torch.float64, device="cuda")
+            u = torch.zeros((N, m), dtype=torch.float64, device="cuda")
+            y = torch.zeros((N, n), dtype=torch.float64, device="cuda")
+            P = torch.zeros((N, n, n), dtype=torch.float64, device="cuda") if want_PK else None
+            K = torch.zeros((N, m, n), dtype=torch.float64, device="cuda") if want_PK else None
+            tlqr.tlqr_solve(s.f, d, x, u, y, P, K)
+            torch.cuda.synchronize()
+            out = dict(x=x.cpu().numpy(), u=u.cpu().numpy(), y=y.cpu().numpy(),
+                       P=None if P is None else P.cpu().numpy(), K=None if K is None else K.cpu().numpy())
+        out["info"] = tlqr.tlqr_last_info(s.f)
+        return out
+    finally:
+        s.close()
+
+
+def check_against_oracle(parent, n, m, data, out, fwd_tol, eta_tol, pk_tol=None):
+    ref = riccati.tree_riccati(parent, n, m, data)
+    fe = riccati.forward_error(out, ref, parent)
+    res = riccati.kkt_residual(parent, n, m, data, out["x"], out["u"], out["y"])
+    assert res["eta"] <= eta_tol, res["eta"]
+    assert fe <= fwd_tol, fe
+    if pk_tol is not None and out.get("P") is not None:
+        nonroot = np.asarray(parent) >= 0
+        assert np.abs(out["P"] - ref["P"]).max() <= pk_tol * np.abs(ref["P"]).max()
+        assert np.abs(out["K"][nonroot] - ref["K"][nonroot]).max() <= pk_tol * max(1.0, np.abs(ref["K"]).max())
+    return fe, res["eta"]
+
+
+# -------------------------------------------------------------------- batched primitives
+
+@pytest.mark.parametrize("n", [1, 3, 4, 12, 16, 32])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_batched_tau_and_compose(n, precision):
+    rng = inputs.rng_for(200 + n)
+    count = 37                                   # several blocks of 8 warps plus a ragged tail
+    def psd(k=None, s=1.0):
+        G = rng.standard_normal((count, n, k or n))
+        return s * G @ G.transpose(0, 2, 1) / n
+    A = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    C, U, P = psd(), psd() + 0.5 * np.eye(n), -psd(1, 0.05)
+    out = dev(np.zeros((count, n, n)))
+    tlqr.tlqr_batched_tau(dev(A), dev(C), dev(P), dev(U), out, precision)
+    ref = np.stack([ops.tau(A[t], C[t], P[t], U[t]) for t in range(count)])
+    tol = 1e-10 if precision == FP64 else 2e-4
+    assert np.abs(out.cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+    Ar = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    Cr, Pr = psd(), -psd(1, 0.05)
+    An, Cn, Pn, Pt = (dev(np.zeros((count, n, n))) for _ in range(4))
+    tlqr.tlqr_batched_compose(dev(A), dev(C), dev(P), dev(Ar), dev(Cr), dev(Pr), dev(U), An, Cn, Pn, Pt,
+                              precision)
+    for t in range(count):
+        (a, c, p), tape = ops.compose((Ar[t], Cr[t], Pr[t]), (A[t], C[t], P[t]), U[t])
+        for got, want in ((An, a), (Cn, c), (Pn, p), (Pt, tape[2])):
+            g = got.cpu().numpy()[t]
+            assert np.abs(g - want).max() <= tol * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (4, 2), (12, 4), (16, 4), (32, 8), (6, 9)])
+@pytest.mark.parametrize("withM", [False, True])
+def test_batched_condense(n, m, withM):
+    rng = inputs.rng_for(300 + n * m)
+    count = 19
+    A = rng.standard_normal((count, n, n)); B = rng.standard_normal((count, n, m))
+    H = rng.standard_normal((count, m, m)); R = np.eye(m) + H @ H.transpose(0, 2, 1)
+    M = 0.3 * rng.standard_normal((count, n, m)) if withM else None
+    Dg = rng.standard_normal((count, n, n)); D = 0.1 * Dg @ Dg.transpose(0, 2, 1)
+    outs = [dev(np.zeros((count, n, n))) for _ in range(3)]
+    tlqr.tlqr_batched_condense(dev(A), dev(B), dev(R), dev(M), dev(D), *outs, FP64)
+    for t in range(count):
+        want = ops.condense(A[t], B[t], R[t], None if M is None else M[t], D[t])
+        for g, w in zip(outs, want):
+            assert np.abs(g.cpu().numpy()[t] - w).max() <= 1e-10 * max(1.0, np.abs(w).max())
+
+
+def test_batched_compose_associativity():
+    """eq. (node-aware-associativity) evaluated by the GPU compress kernel."""
+    rng = inputs.rng_for(401)
+    n, count = 8, 11
+    def tri():
+        G = rng.standard_normal((count, n, n))
+        return (rng.standard_normal((count, n, n)) / np.sqrt(n), G @ G.transpose(0, 2, 1) / n,
+                np.zeros((count, n, n)))
+    e1, e2, e3 = tri(), tri(), tri()
+    U1 = np.eye(n) + 0.3 * np.stack([np.diag(rng.random(n)) for _ in range(count)])
+    U2 = np.eye(n) + 0.3 * np.stack([np.diag(rng.random(n)) for _ in range(count)])
+    def comp(r, l, U):
+        An, Cn, Pn, Pt = (dev(np.zeros((count, n, n))) for _ in range(4))
+        tlqr.tlqr_batched_compose(dev(l[0]), dev(l[1]), dev(l[2]), dev(r[0]), dev(r[1]), dev(r[2]), dev(U),
+                                  An, Cn, Pn, Pt, FP64)
+        return tuple(t.cpu().numpy() for t in (An, Cn, Pn))
+    left = comp(e3, comp(e2, e1, U1), U2)
+    right = comp(comp(e3, e2, U2), e1, U1)
+    for a, b in zip(left, right):
+        assert np.abs(a - b).max() <= 1e-10 * max(1.0, np.abs(a).max())
+
+
+# -------------------------------------------------------------------- end to end, FP64
+
+def e1_population():
+    rng = inputs.rng_for(12)
+    cases = []
+    fixed = [("chain", inputs.chain(9)), ("star", inputs.star(8)),
+             ("irregular", np.array([-1, 0, 1, 1, 2, 4, 4, 5], dtype=np.int32)),
+             ("balanced", inputs.balanced(13)), ("single", np.array([-1], dtype=np.int32))]
+    k = 0
+    for name, p in fixed:
+        for delta in (None, "random"):
+            n, m = 1 + k % 4, 1 + k % 3
+            cases.append((f"{name}-{delta}-n{n}m{m}", p, n, m,
+                          inputs.problem_data(p, n, m, rng, M_scale=0.3 if k % 2 else 0.0, delta=delta,
+                                              delta_value=0.5)))
+            k += 1
+    for t in range(16):
+        N = int(rng.integers(2, 31))
+        p, _ = inputs.permute_labels(inputs.random_recursive(N, rng), rng)
+        n, m = int(rng.integers(1, 5)), int(rng.integers(1, 4))
+        cases.append((f"random{t}-N{N}-n{n}m{m}", p, n, m,
+                      inputs.problem_data(p, n, m, rng, M_scale=0.3 if t % 2 else 0.0,
+                                          delta=("random" if t % 3 else None), delta_value=0.3)))
+    return cases
+
+
+E1 = e1_population()
+
+
+@pytest.mark.parametrize("case", E1, ids=[c[0] for c in E1])
+def test_fp64_small_population(case):
+    _, p, n, m, d = case
+    out = gpu_solve(p, n, m, d)
+    check_against_oracle(p, n, m, d, out, fwd_tol=1e-10, eta_tol=1e-13, pk_tol=1e-10)
+
+
+TOPOLOGIES = [("chain", inputs.chain(1000)), ("star", inputs.star(1000)), ("balanced", inputs.balanced(1023)),
+              ("comb", inputs.comb(1001)), ("tight", inputs.tightness_tree(64))]
+
+
+@pytest.mark.parametrize("topo", TOPOLOGIES, ids=lambda t: t[0])
+@pytest.mark.parametrize("n,m", [(4, 2), (12, 4)])
+def test_fp64_topologies(topo, n, m):
+    _, p = topo
+    rng = inputs.rng_for(500 + n)
+    d = inputs.problem_data(p, n, m, rng, delta="subset", delta_value=0.1, delta_fraction=0.3, M_scale=0.2)
+    out = gpu_solve(p, n, m, d)
+    check_against_oracle(p, n, m, d, out, fwd_tol=1e-8, eta_tol=1e-10, pk_tol=1e-8)
+
+
+def test_fp64_binary_depth6():
+    w = inputs.binary_depth6()
+    out = gpu_solve(w.parent, w.n, w.m, w.data)
+    fe, eta = check_against_oracle(w.parent, w.n, w.m, w.data, out, fwd_tol=1e-10, eta_tol=1e-12, pk_tol=1e-10)
+
+
+def test_fp64_long_trunk_full_size():
+    """The benchmark workload at full size (N = 65,536, n = 12, m = 4)."""
+    w = inputs.long_trunk()
+    out = gpu_solve(w.parent, w.n, w.m, w.data)
+    check_against_oracle(w.parent, w.n, w.m, w.data, out, fwd_tol=1e-8, eta_tol=1e-10, pk_tol=1e-8)
+
+
+def test_fp64_dimensions_32_8():
+    rng = inputs.rng_for(77)
+    p, _ = inputs.permute_labels(inputs.random_recursive(300, rng), rng)
+    d = inputs.problem_data(p, 32, 8, rng, kappa_R=1e4)
+    out = gpu_solve(p, 32, 8, d)
+    check_against_oracle(p, 32, 8, d, out, fwd_tol=1e-8, eta_tol=1e-10, pk_tol=1e-8)
+
+
+def test_host_and_device_memory_agree():
+    rng = inputs.rng_for(78)
+    p = inputs.random_recursive(500, rng)
+    d = inputs.problem_data(p, 6, 2, rng, delta="subset", delta_value=0.2)
+    a = gpu_solve(p, 6, 2, d, host=False)
+    b = gpu_solve(p, 6, 2, d, host=True)
+    for k in ("x", "u", "y", "P", "K"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_zero_delta_paths_agree():
+    """Delta = NULL and an explicit all-zero Delta give the same result."""
+    rng = inputs.rng_for(79)
+    p = inputs.random_recursive(400, rng)
+    d = inputs.problem_data(p, 5, 2, rng)
+    a = gpu_solve(p, 5, 2, d)
+    b = gpu_solve(p, 5, 2, dict(d, Delta=np.zeros((len(p), 5, 5))))
+    for k in ("x", "u", "y", "P", "K"):
+        assert np.abs(a[k] - b[k]).max() <= 1e-12 * max(1.0, np.abs(a[k]).max())
+
+
+def test_factor_reuse_multiple_rhs():
+    """Sec. V: one factorisation serves several right-hand sides (Alg. 1 steps 4-6)."""
+    rng = inputs.rng_for(80)
+    p = inputs.random_recursive(700, rng)
+    n, m = 6, 3
+    d = inputs.problem_data(p, n, m, rng, delta="subset", delta_value=0.3, M_scale=0.2)
+    s = tlqr.TreeLQR(p, n, m, FP64, has_M=True, has_delta=True)
+    try:
+        tlqr.tlqr_factor(s.f, {k: dev(v) for k, v in d.items()})
+        for t in range(3):
+            rhs = inputs.rhs_data(p, n, m, rng)
+            dd = dict(d, **rhs)
+            x = torch.zeros((len(p), n), dtype=torch.float64, device="cuda")
+            u = torch.zeros((len(p), m), dtype=torch.float64, device="cuda")
+            y = torch.zeros((len(p), n), dtype=torch.float64, device="cuda")
+            tlqr.tlqr_solve_rhs(s.f, dev(rhs["q"]), dev(rhs["r"]), dev(rhs["c"]), x, u, y)
+            torch.cuda.synchronize()
+            out = dict(x=x.cpu().numpy(), u=u.cpu().numpy(), y=y.cpu().numpy())
+            check_against_oracle(p, n, m, dd, out, fwd_tol=1e-9, eta_tol=1e-12)
+    finally:
+        s.close()
+
+
+def test_lifted_node_controls_on_gpu():
+    """Prop. 2 end to end: host lifting -> GPU edge-form solve -> projection,
+    against the dense node-control KKT solution."""
+    from oracle import dense
+    from tests.test_boundary_cpu import node_control_instance
+    rng = inputs.rng_for(81)
+    p, _ = inputs.permute_labels(inputs.random_recursive(60, rng), rng)
+    n, m = 4, 2
+    nd = node_control_instance(rng, p, n, m, True)
+    L = tlqr.tlqr_lift_node_controls(p, n, m, nd)
+    data = {k: L[k] for k in ("Q", "q", "M", "R", "r", "A", "B", "c", "Delta")}
+    out = gpu_solve(L["parent"], n + m, m, data, want_PK=False)
+    x, v, y = tlqr.tlqr_project_lifted(len(p), n, m, L["map"], out["x"], out["u"], out["y"])
+    ref = dense.dense_solve_node_control(p, n, m, nd)
+    scale = max(np.abs(ref["x"]).max(), np.abs(ref["v"]).max(), np.abs(ref["y"]).max())
+    for a, b in ((x, ref["x"]), (v, ref["v"]), (y, ref["y"])):
+        assert np.abs(a - b).max() <= 1e-10 * scale
+
+
+def test_gpu_residual_matches_oracle_residual():
+    rng = inputs.rng_for(82)
+    p = inputs.random_recursive(300, rng)
+    n, m = 5, 3
+    d = inputs.problem_data(p, n, m, rng, delta="random", delta_value=0.2, M_scale=0.3)
+    x, u, y = rng.standard_normal((300, n)), rng.standard_normal((300, m)), rng.standard_normal((300, n))
+    u[p < 0] = 0
+    s = tlqr.TreeLQR(p, n, m, FP64, has_M=True, has_delta=True)
+    try:
+        st = tlqr.tlqr_kkt_residual(s.f, {k: dev(v) for k, v in d.items()}, dev(x), dev(u), dev(y))
+    finally:
+        s.close()
+    ref = riccati.kkt_residual(p, n, m, d, x, u, y)
+    assert st["abs"] == pytest.approx(ref["abs"], rel=1e-12)
+    assert st["eta"] == pytest.approx(ref["eta"], rel=1e-12)
+
+
+# -------------------------------------------------------------------- mixed precision
+
+@pytest.mark.parametrize("name", ["binary", "long_trunk"])
+def test_mixed_refined(name):
+    w = inputs.binary_depth6() if name == "binary" else inputs.long_trunk()
+    out = gpu_solve(w.parent, w.n, w.m, w.data, precision=MIXED, want_PK=False)
+    assert out["info"]["eta"] <= 1e-8
+    fe, eta = check_against_oracle(w.parent, w.n, w.m, w.data, out, fwd_tol=1e-6, eta_tol=1e-8)
+
+
+# -------------------------------------------------------------------- errors
+
+def test_indefinite_R_reports_not_pd():
+    p = inputs.chain(20)
+    d = inputs.problem_data(p, 3, 2, inputs.rng_for(83))
+    d["R"][7] = -np.eye(2)
+    with pytest.raises(tlqr.TLQRError) as e:
+        gpu_solve(p, 3, 2, d)
+    assert e.value.code == 3
+
+
+def test_nan_data_is_reported():
+    p = inputs.chain(20)
+    d = inputs.problem_data(p, 3, 2, inputs.rng_for(84))
+    d["Q"][5, 0, 0] = np.nan
+    with pytest.raises(tlqr.TLQRError) as e:
+        gpu_solve(p, 3, 2, d)
+    assert e.value.code in (3, 4, 5)
