@@ -42,12 +42,14 @@ FP64_PEAK_TFLOPS = 1.25
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--total", type=int, default=65536, help="tree size (default: the benchmark workload)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the headline mode only (no FP64 comparison, e2e or CPU legs); for profiler runs")
     return ap.parse_args()
 
 
@@ -80,6 +82,10 @@ def per_unit(kind, n, m, wbytes, has_delta_frac=0.0):
     if kind == "local_factor":
         fl = 6 * n * n * m + 4 * n * m * m + m ** 3 / 3 + has_delta_frac * 20 / 3 * n ** 3
         return fl, (s + f + 2 * n * m + m * m / 2 + m * n + f + m * m / 2) * wbytes + f * 8
+    if kind == "residual":
+        # FP64 rows of eq. (kkt): Q x, A^T y, A x, B u, B^T y, R u (+ Delta y twice) per node
+        fl = 2 * (3 * n * n + 2 * n * m + m * m) + has_delta_frac * 4 * n * n
+        return fl, (2 * f + n * m + m * m + has_delta_frac * f + 8 * n + 4 * m) * 8
     if kind == "condense":
         return m ** 3 / 3 + 2 * n * m * m + 2 * n * n * m, (f + n * m + m * m / 2 + 2 * s) * 8
     return None, None
@@ -92,15 +98,20 @@ class ClockSampler:
         self.index, self.samples, self.reasons, self.stop_ev = index, [], set(), threading.Event()
         self.max_mhz = None
         self.ok = False
+        self.error = None
+        self.proc = None
         try:
             import pynvml
             pynvml.nvmlInit()
             self.nv = pynvml
             self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.samples.append(pynvml.nvmlDeviceGetClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+            self.samples.clear()
             self.ok = True
-        except Exception:
-            pass
+        except Exception as e:
+            self.error = f"nvml: {e!r}"
+
 
     def _run(self):
         nv = self.nv
@@ -120,22 +131,50 @@ class ClockSampler:
                 pass
             self.stop_ev.wait(0.05)
 
+    def _run_smi(self):
+        import subprocess
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:
+            self.error = f"nvidia-smi: {e}"
+            return
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.proc.stdout:
+            f = [v.strip() for v in line.split(",")]
+            try:
+                self.samples.append(float(f[0]))
+                self.max_mhz = float(f[1])
+                for nm, v in zip(names, f[2:]):
+                    if v.lower() == "active":
+                        self.reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+
     def __enter__(self):
-        if self.ok:
-            self.t = threading.Thread(target=self._run, daemon=True)
-            self.t.start()
+        target = self._run if self.ok else self._run_smi
+        self.t = threading.Thread(target=target, daemon=True)
+        self.t.start()
+        time.sleep(0.2)
         return self
 
     def __exit__(self, *a):
-        if self.ok:
-            self.stop_ev.set()
-            self.t.join()
+        self.stop_ev.set()
+        if getattr(self, "proc", None) is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+        self.t.join(timeout=5)
 
     def summary(self):
+        src = "nvml" if self.ok else "nvidia-smi"
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "source": src,
+                    "error": self.error}
         return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(self.reasons), "samples": len(self.samples)}
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": src}
 
 
 # ----------------------------------------------------------------- CPU oracle legs
@@ -223,8 +262,9 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
 
     def timed_steps(solver, K, profile_kinds=()):
-        tlqr.tlqr_profile_read(solver.f)                     # reset counters
         tlqr.tlqr_profile_mask(solver.f, profile_kinds)
+        tlqr.tlqr_solve(solver.f, dd, x, u, y, stream=stream)   # (re)capture graphs outside the timing
+        tlqr.tlqr_profile_read(solver.f)                     # reset counters
         ts = []
         barrier()
         for _ in range(K):
@@ -263,7 +303,7 @@ def run_ours(args, rank, world, dist):
 
     # plain FP64 contraction on the same GPU (the comparison of the metric)
     fp64 = None
-    if mixed:
+    if mixed and not args.quick:
         s64 = tlqr.TreeLQR(w.parent, n, m, tlqr.TLQR_PREC_FP64, has_delta=has_delta)
         for _ in range(2):
             tlqr.tlqr_solve(s64.f, dd, x, u, y, stream=stream)
@@ -275,6 +315,14 @@ def run_ours(args, rank, world, dist):
         s64.close()
 
     # end to end through the public API with pinned host buffers
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "nodes/s", "ms_per_step": ms_per_step,
+                              "steps": args.steps, "eta": res["eta"], "quick": True,
+                              "kernel_ms_per_step": {k: v["ms"] for k, v in prof_all.items() if v["ms"] > 0}}),
+                  flush=True)
+        solver.close()
+        return
     hd = {k: (None if v is None else torch.from_numpy(v).pin_memory()) for k, v in w.data.items()}
     hx = torch.zeros((N, n), dtype=torch.float64).pin_memory()
     hu = torch.zeros((N, m), dtype=torch.float64).pin_memory()
@@ -310,7 +358,8 @@ def run_ours(args, rank, world, dist):
         sec = pd["ms"] / 1e3
         flops = fl * pd["units"] / sec
         bw = by * pd["units"] / sec
-        peak_alu = (FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS) * 1e12
+        fp32_kernel = mixed and dominant != "residual"
+        peak_alu = (FP32_PEAK_TFLOPS if fp32_kernel else FP64_PEAK_TFLOPS) * 1e12
         t_alu = fl / peak_alu
         t_mem = by / (hbm * 1e9)
         if t_mem >= t_alu:
@@ -319,7 +368,7 @@ def run_ours(args, rank, world, dist):
         else:
             roof = {"bound": "alu", "achieved": flops / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                     "frac": flops / peak_alu, "traffic": None,
-                    "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz" if mixed
+                    "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz" if fp32_kernel
                     else "nominal FP64 1.25 TFLOP/s"}
         roof.update({"kernel": f"k_{dominant}", "launches": pd["timed"], "units": pd["units"],
                      "avg_launch_ms": pd["ms"] / pd["timed"], "flops_per_unit": fl, "bytes_per_unit": by})

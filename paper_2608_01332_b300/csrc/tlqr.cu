@@ -18,6 +18,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -55,47 +57,122 @@ WarpBytes warp_bytes(int n, int m, size_t ts) {
   return w;
 }
 
-// Per-kind launch counters and optional CUDA-event timing of selected kinds.
-struct Profiler {
+// Raise (never lower) a kernel's dynamic shared-memory limit; done outside
+// stream capture so that captured launches find it already set.
+template <typename Kernel>
+cudaError_t ensure_smem(Kernel kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> have;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = have[(const void*)kernel];
+  if (cur >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
+inline int warps_per_block(size_t wbytes) {
+  if (wbytes == 0) return kMaxWarpsPerBlock;
+  return (int)std::max<size_t>(1, std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / wbytes));
+}
+
+// What one host-side pass over the plan launched: per-kind launch and unit
+// counts, and CUDA-event pairs around the launches of the kinds in `mask`.
+// When `capture` is set the events are recorded as external event nodes of a
+// CUDA graph (they then fire on every replay).
+struct EvPair { int kind; cudaEvent_t a, b; };
+struct Recorder {
   uint32_t mask = 0;
+  bool capture = false;
   int64_t launches[TLQR_K_COUNT] = {}, units[TLQR_K_COUNT] = {};
-  struct Rec { int kind; cudaEvent_t a, b; };
-  std::vector<Rec> recs;
-  std::vector<cudaEvent_t> pool;
-  cudaEvent_t get() {
-    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+  std::vector<EvPair> recs;
+  std::vector<cudaEvent_t>* pool = nullptr;
+  cudaEvent_t event() {
+    if (pool && !pool->empty()) { cudaEvent_t e = pool->back(); pool->pop_back(); return e; }
     cudaEvent_t e = nullptr;
     cudaEventCreate(&e);
     return e;
   }
+  void record(cudaEvent_t e, cudaStream_t st) {
+    if (capture) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+  }
+};
+
+// Per-factor accumulated profile.
+struct Profiler {
+  uint32_t mask = 0;
+  int64_t launches[TLQR_K_COUNT] = {}, units[TLQR_K_COUNT] = {}, timed[TLQR_K_COUNT] = {};
+  double ms[TLQR_K_COUNT] = {};
+  std::vector<EvPair> pending;
+  std::vector<char> pending_owned;
+  std::vector<cudaEvent_t> pool;
+  bool event_error = false;
+  void add(const Recorder& r, bool owned) {
+    for (int k = 0; k < TLQR_K_COUNT; ++k) { launches[k] += r.launches[k]; units[k] += r.units[k]; }
+    for (const EvPair& p : r.recs) { pending.push_back(p); pending_owned.push_back(owned); }
+  }
+  // Read the events of completed launches (synchronises on them).
+  void harvest() {
+    for (size_t t = 0; t < pending.size(); ++t) {
+      const EvPair& p = pending[t];
+      float v = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&v, p.a, p.b) == cudaSuccess) {
+        ms[p.kind] += v;
+        timed[p.kind]++;
+      } else {
+        event_error = true;
+        cudaGetLastError();
+      }
+      if (pending_owned[t]) { pool.push_back(p.a); pool.push_back(p.b); }
+    }
+    pending.clear();
+    pending_owned.clear();
+  }
   ~Profiler() {
-    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (size_t t = 0; t < pending.size(); ++t)
+      if (pending_owned[t]) { cudaEventDestroy(pending[t].a); cudaEventDestroy(pending[t].b); }
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
 
 // Launch `count` warps, each with `wbytes` of dynamic shared memory.
 template <typename Kernel, typename... Args>
-cudaError_t launch_warps(Profiler* prof, int kind, Kernel kernel, int count, size_t wbytes, cudaStream_t st,
+cudaError_t launch_warps(Recorder* rc, int kind, Kernel kernel, int count, size_t wbytes, cudaStream_t st,
                          Args... args) {
   if (count <= 0) return cudaSuccess;
-  int wpb = kMaxWarpsPerBlock;
-  if (wbytes > 0) wpb = (int)std::max<size_t>(1, std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / wbytes));
+  const int wpb = warps_per_block(wbytes);
   const size_t smem = wbytes * wpb;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!(rc && rc->capture)) {
+    cudaError_t e = ensure_smem(kernel, smem);
     if (e != cudaSuccess) return e;
   }
   const int blocks = (count + wpb - 1) / wpb;
-  const bool timed = prof && (prof->mask >> kind) & 1u;
-  Profiler::Rec rec{kind, nullptr, nullptr};
-  if (timed) { rec.a = prof->get(); rec.b = prof->get(); cudaEventRecord(rec.a, st); }
+  const bool timed = rc && (rc->mask >> kind) & 1u;
+  EvPair ev{kind, nullptr, nullptr};
+  if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
   kernel<<<blocks, 32 * wpb, smem, st>>>(args...);
   cudaError_t e = cudaGetLastError();
-  if (timed) { cudaEventRecord(rec.b, st); prof->recs.push_back(rec); }
-  if (prof) { prof->launches[kind]++; prof->units[kind] += count; }
+  if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
+  if (rc) { rc->launches[kind]++; rc->units[kind] += count; }
   return e;
 }
+
+// An instantiated CUDA graph of one launch sequence, valid for one key (the
+// pointers and flags it was captured with).
+struct GraphCache {
+  std::vector<uintptr_t> key;
+  cudaGraphExec_t exec = nullptr;
+  Recorder rec;                      // counts per replay and the graph's own events
+  void clear() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (const EvPair& p : rec.recs) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    rec = Recorder{};
+    key.clear();
+  }
+};
 
 template <typename T>
 T* dalloc(size_t count, cudaError_t* err) {
@@ -139,6 +216,13 @@ struct tlqr_factor_t {
   bool factored = false;
   tlqr_info info{};
   Profiler prof;
+  // CUDA graphs of the launch sequences (factor, up to four solves, residual)
+  GraphCache g_factor, g_solve[4], g_resid[2];
+  int solve_lru = 0;
+  bool graphs_broken = false;      // a capture failed once: launch directly from then on
+  // own non-blocking work stream (capturable), fenced to the caller's stream
+  cudaStream_t work = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
   template <typename T>
   Ws<T> ws(const tlqr_problem& p) const {
@@ -159,11 +243,36 @@ struct tlqr_factor_t {
     return w;
   }
   ~tlqr_factor_t() {
+    if (work) cudaStreamSynchronize(work);
+    g_factor.clear();
+    for (auto& g : g_solve) g.clear();
+    for (auto& g : g_resid) g.clear();
     for (void* p : allocs) cudaFree(p);
     if (h_maxes) cudaFreeHost(h_maxes);
     if (h_status) cudaFreeHost(h_status);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (work) cudaStreamDestroy(work);
   }
 };
+
+namespace {
+// All work of a public call runs on the factor's own stream, ordered after
+// the caller's stream on entry; on exit the caller's stream waits for it.
+struct StreamScope {
+  tlqr_factor_t* f;
+  cudaStream_t user;
+  cudaStream_t st;
+  StreamScope(tlqr_factor_t* f_, void* stream) : f(f_), user((cudaStream_t)stream), st(f_->work) {
+    cudaEventRecord(f->ev_in, user);
+    cudaStreamWaitEvent(st, f->ev_in, 0);
+  }
+  ~StreamScope() {
+    cudaEventRecord(f->ev_out, st);
+    cudaStreamWaitEvent(user, f->ev_out, 0);
+  }
+};
+}  // namespace
 
 namespace {
 
@@ -201,80 +310,143 @@ int upload_plan(tlqr_factor_t* f) {
 }
 
 template <typename T>
-cudaError_t run_factor(tlqr_factor_t* f, const tlqr_problem& p, cudaStream_t st) {
+cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cudaStream_t st) {
   const tlqr_plan_t* P = f->plan;
   const Ws<T> w = f->ws<T>(p);
   const WarpBytes wb = warp_bytes(f->opt.n, f->opt.m, sizeof(T));
   cudaError_t e;
-  if ((e = launch_warps(&f->prof, TLQR_K_CONDENSE, k_condense<T>, P->N, wb.condense, st, w, (int)wb.condense))) return e;
+  if ((e = cudaMemsetAsync(f->status, 0, sizeof(int), st))) return e;
+  if ((e = launch_warps(rc, TLQR_K_CONDENSE, k_condense<T>, P->N, wb.condense, st, w, (int)wb.condense))) return e;
   for (const tlqr_round& rd : P->rounds) {
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(&f->prof, TLQR_K_RAKE, k_rake<T>, nr, wb.tau, st, w, rd.rake_begin, nr, (int)wb.tau))) return e;
-    if ((e = launch_warps(&f->prof, TLQR_K_ABSORB, k_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
-    if ((e = launch_warps(&f->prof, TLQR_K_COMPRESS, k_compress<T>, nc, wb.compress, st, w, rd.comp_begin, nc, (int)wb.compress))) return e;
+    if ((e = launch_warps(rc, TLQR_K_RAKE, k_rake<T>, nr, wb.tau, st, w, rd.rake_begin, nr, (int)wb.tau))) return e;
+    if ((e = launch_warps(rc, TLQR_K_ABSORB, k_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
+    if ((e = launch_warps(rc, TLQR_K_COMPRESS, k_compress<T>, nc, wb.compress, st, w, rd.comp_begin, nc, (int)wb.compress))) return e;
   }
   for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
     const int nc = it->comp_end - it->comp_begin;
-    if ((e = launch_warps(&f->prof, TLQR_K_EXPAND, k_expand<T>, nc, wb.tau, st, w, it->comp_begin, nc, (int)wb.tau))) return e;
+    if ((e = launch_warps(rc, TLQR_K_EXPAND, k_expand<T>, nc, wb.tau, st, w, it->comp_begin, nc, (int)wb.tau))) return e;
   }
-  if ((e = launch_warps(&f->prof, TLQR_K_LOCAL_FACTOR, k_local_factor<T>, P->N, wb.local_factor, st, w, (int)wb.local_factor))) return e;
+  if ((e = launch_warps(rc, TLQR_K_LOCAL_FACTOR, k_local_factor<T>, P->N, wb.local_factor, st, w, (int)wb.local_factor))) return e;
   for (const tlqr_round& rd : P->rounds) {
     const int nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(&f->prof, TLQR_K_COMPOSE_T, k_compose_T<T>, nc, wb.compose_T, st, w, rd.comp_begin, nc, (int)wb.compose_T))) return e;
+    if ((e = launch_warps(rc, TLQR_K_COMPOSE_T, k_compose_T<T>, nc, wb.compose_T, st, w, rd.comp_begin, nc, (int)wb.compose_T))) return e;
   }
   return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t run_solve(tlqr_factor_t* f, const double* q, const double* r, const double* c, double* x,
-                      double* u, double* y, int accumulate, cudaStream_t st) {
+cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const double* r, const double* c,
+                      double* x, double* u, double* y, int accumulate, cudaStream_t st) {
   const tlqr_plan_t* P = f->plan;
   tlqr_problem p = f->dprob;
   p.q = q; p.r = r; p.c = c;
   const Ws<T> w = f->ws<T>(p);
   const WarpBytes wb = warp_bytes(f->opt.n, f->opt.m, sizeof(T));
   cudaError_t e;
-  if ((e = launch_warps(&f->prof, TLQR_K_AFF_INIT, k_aff_init<T>, P->N, wb.aff_init, st, w, (int)wb.aff_init))) return e;
+  if ((e = launch_warps(rc, TLQR_K_AFF_INIT, k_aff_init<T>, P->N, wb.aff_init, st, w, (int)wb.aff_init))) return e;
   for (const tlqr_round& rd : P->rounds) {
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(&f->prof, TLQR_K_AFF_RAKE, k_aff_rake<T>, nr, wb.vec1, st, w, rd.rake_begin, nr, (int)wb.vec1))) return e;
-    if ((e = launch_warps(&f->prof, TLQR_K_AFF_ABSORB, k_aff_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
-    if ((e = launch_warps(&f->prof, TLQR_K_AFF_COMPRESS, k_aff_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
+    if ((e = launch_warps(rc, TLQR_K_AFF_RAKE, k_aff_rake<T>, nr, wb.vec1, st, w, rd.rake_begin, nr, (int)wb.vec1))) return e;
+    if ((e = launch_warps(rc, TLQR_K_AFF_ABSORB, k_aff_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
+    if ((e = launch_warps(rc, TLQR_K_AFF_COMPRESS, k_aff_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
   }
   for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
     const int nc = it->comp_end - it->comp_begin;
-    if ((e = launch_warps(&f->prof, TLQR_K_AFF_EXPAND, k_aff_expand<T>, nc, wb.vec1, st, w, it->comp_begin, nc, (int)wb.vec1))) return e;
+    if ((e = launch_warps(rc, TLQR_K_AFF_EXPAND, k_aff_expand<T>, nc, wb.vec1, st, w, it->comp_begin, nc, (int)wb.vec1))) return e;
   }
-  if ((e = launch_warps(&f->prof, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w, (int)wb.local_solve))) return e;
+  if ((e = launch_warps(rc, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w, (int)wb.local_solve))) return e;
   for (const tlqr_round& rd : P->rounds) {
     const int nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(&f->prof, TLQR_K_STATE_COMPRESS, k_state_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
+    if ((e = launch_warps(rc, TLQR_K_STATE_COMPRESS, k_state_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
   }
   for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
     const int nc = it->comp_end - it->comp_begin, nr = it->rake_end - it->rake_begin;
-    if ((e = launch_warps(&f->prof, TLQR_K_STATE_EXPAND, k_state_expand<T>, nc, wb.vec1, st, w, (const int*)f->dp.comp_j,
+    if ((e = launch_warps(rc, TLQR_K_STATE_EXPAND, k_state_expand<T>, nc, wb.vec1, st, w, (const int*)f->dp.comp_j,
                           (const int*)f->dp.comp_i, it->comp_begin, nc, (int)wb.vec1))) return e;
-    if ((e = launch_warps(&f->prof, TLQR_K_STATE_EXPAND, k_state_expand<T>, nr, wb.vec1, st, w, (const int*)f->dp.rake_leaf,
+    if ((e = launch_warps(rc, TLQR_K_STATE_EXPAND, k_state_expand<T>, nr, wb.vec1, st, w, (const int*)f->dp.rake_leaf,
                           (const int*)f->dp.rake_parent, it->rake_begin, nr, (int)wb.vec1))) return e;
   }
-  return launch_warps(&f->prof, TLQR_K_RECOVER, k_recover<T>, P->N, wb.recover, st, w, x, u, y, accumulate, (int)wb.recover);
+  return launch_warps(rc, TLQR_K_RECOVER, k_recover<T>, P->N, wb.recover, st, w, x, u, y, accumulate, (int)wb.recover);
 }
 
-cudaError_t run_residual(tlqr_factor_t* f, const tlqr_problem& p, const double* x, const double* u,
-                         const double* y, cudaStream_t st) {
+cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, const double* x,
+                         const double* u, const double* y, int with_knorm, cudaStream_t st) {
   ResidualArgs a{};
   const tlqr_plan_t* P = f->plan;
-  a.N = P->N; a.n = f->opt.n; a.m = f->opt.m; a.root = P->root;
+  a.N = P->N; a.n = f->opt.n; a.m = f->opt.m; a.root = P->root; a.with_knorm = with_knorm;
   a.parent = f->dp.parent; a.child_start = f->dp.child_start; a.child_list = f->dp.child_list;
   a.Q = p.Q; a.q = p.q; a.M = f->opt.has_M ? p.M : nullptr; a.R = p.R; a.r = p.r; a.A = p.A;
   a.B = p.B; a.c = p.c; a.Delta = f->opt.has_delta ? p.Delta : nullptr;
   a.x = x; a.u = u; a.y = y;
   a.res_x = f->res_x; a.res_u = f->res_u; a.res_c = f->res_c;
   a.maxes = f->maxes;
-  cudaError_t e = cudaMemsetAsync(f->maxes, 0, 4 * sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(f->maxes, 0, (with_knorm ? 4 : 3) * sizeof(unsigned long long), st);
   if (e) return e;
-  if ((e = launch_warps(&f->prof, TLQR_K_RESIDUAL, k_residual, P->N, 0, st, a))) return e;
-  return cudaMemcpyAsync(f->h_maxes, f->maxes, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  const size_t rows = (size_t)P->N * (2 * f->opt.n + f->opt.m);
+  const int threads = 256;
+  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 16);
+  k_residual<<<blocks, threads, 0, st>>>(a);
+  if ((e = cudaGetLastError())) return e;
+  if (rc) { rc->launches[TLQR_K_RESIDUAL]++; rc->units[TLQR_K_RESIDUAL] += P->N; }
+  if ((e = cudaMemcpyAsync(f->h_maxes, f->maxes, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st))) return e;
+  return cudaMemcpyAsync(f->h_status, f->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+// Run one launch sequence, through a cached CUDA graph when graphs are on.
+template <typename Body>
+cudaError_t run_seq(tlqr_factor_t* f, GraphCache* g, std::vector<uintptr_t> key, cudaStream_t st, Body body) {
+  key.push_back(f->prof.mask);
+  if (!f->opt.use_graphs || f->graphs_broken || !g) {
+    Recorder r;
+    r.mask = f->prof.mask;
+    r.pool = &f->prof.pool;
+    cudaError_t e = body(&r);
+    f->prof.add(r, true);
+    return e;
+  }
+  if (!g->exec || g->key != key) {
+    g->clear();
+    Recorder r;
+    r.mask = f->prof.mask;
+    r.capture = true;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    cudaError_t eb = e ? e : body(&r);
+    cudaGraph_t graph = nullptr;
+    if (!e) e = cudaStreamEndCapture(st, &graph);
+    if (!e && !eb) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e || eb) {
+      // capture not possible here: fall back to direct launches for good
+      for (const EvPair& p : r.recs) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+      cudaGetLastError();
+      f->graphs_broken = true;
+      return run_seq(f, nullptr, key, st, body);
+    }
+    g->key = key;
+    g->rec = r;
+  }
+  cudaError_t e = cudaGraphLaunch(g->exec, st);
+  f->prof.add(g->rec, false);
+  return e;
+}
+
+uintptr_t up(const void* p) { return (uintptr_t)p; }
+
+std::vector<uintptr_t> problem_key(const tlqr_problem& p) {
+  return {up(p.Q), up(p.q), up(p.M), up(p.R), up(p.r), up(p.A), up(p.B), up(p.c), up(p.Delta)};
+}
+
+GraphCache* solve_cache(tlqr_factor_t* f, const std::vector<uintptr_t>& key) {
+  std::vector<uintptr_t> k = key;
+  k.push_back(f->prof.mask);
+  for (auto& g : f->g_solve)
+    if (g.exec && g.key == k) return &g;
+  GraphCache* g = &f->g_solve[f->solve_lru];
+  f->solve_lru = (f->solve_lru + 1) % 4;
+  return g;
 }
 
 void residual_stats(const tlqr_factor_t* f, double* abs_res, double* eta) {
@@ -383,24 +555,67 @@ int read_status(tlqr_factor_t* f, cudaStream_t st) {
   return map_status(*f->h_status);
 }
 
+// Set the dynamic shared-memory limits of every kernel this factor launches
+// (outside any stream capture).
+template <typename T>
+cudaError_t configure_kernels(int n, int m) {
+  const WarpBytes wb = warp_bytes(n, m, sizeof(T));
+  auto sz = [](size_t w) { return w * warps_per_block(w); };
+  cudaError_t e = cudaSuccess;
+  if (!e) e = ensure_smem(k_condense<T>, sz(wb.condense));
+  if (!e) e = ensure_smem(k_rake<T>, sz(wb.tau));
+  if (!e) e = ensure_smem(k_expand<T>, sz(wb.tau));
+  if (!e) e = ensure_smem(k_compress<T>, sz(wb.compress));
+  if (!e) e = ensure_smem(k_local_factor<T>, sz(wb.local_factor));
+  if (!e) e = ensure_smem(k_compose_T<T>, sz(wb.compose_T));
+  if (!e) e = ensure_smem(k_aff_init<T>, sz(wb.aff_init));
+  if (!e) e = ensure_smem(k_aff_rake<T>, sz(wb.vec1));
+  if (!e) e = ensure_smem(k_aff_compress<T>, sz(wb.vec1));
+  if (!e) e = ensure_smem(k_aff_expand<T>, sz(wb.vec1));
+  if (!e) e = ensure_smem(k_local_solve<T>, sz(wb.local_solve));
+  if (!e) e = ensure_smem(k_state_compress<T>, sz(wb.vec1));
+  if (!e) e = ensure_smem(k_state_expand<T>, sz(wb.vec1));
+  if (!e) e = ensure_smem(k_recover<T>, sz(wb.recover));
+  return e;
+}
+
 // Enqueue the factorisation; with `sync` also wait and report its status.
 int factor_impl(tlqr_factor_t* f, const tlqr_problem* dp, cudaStream_t st, bool sync) {
   f->dprob = *dp;
   f->factored = false;
-  if (cudaMemsetAsync(f->status, 0, sizeof(int), st)) return TLQR_ERR_CUDA;
-  cudaError_t e = f->ts == 8 ? run_factor<double>(f, *dp, st) : run_factor<float>(f, *dp, st);
+  tlqr_problem key = *dp;
+  key.q = key.r = key.c = nullptr;
+  cudaError_t e = run_seq(f, &f->g_factor, problem_key(key), st, [&](Recorder* rc) {
+    return f->ts == 8 ? run_factor<double>(f, rc, *dp, st) : run_factor<float>(f, rc, *dp, st);
+  });
   if (e) return TLQR_ERR_CUDA;
   f->factored = true;
   if (!sync) return TLQR_OK;
   const int rc = read_status(f, st);
+  f->prof.harvest();
   if (rc != TLQR_OK) f->factored = false;
   return rc;
 }
 
 cudaError_t solve_impl(tlqr_factor_t* f, const double* q, const double* r, const double* c, double* x,
                        double* u, double* y, int accumulate, cudaStream_t st) {
-  return f->ts == 8 ? run_solve<double>(f, q, r, c, x, u, y, accumulate, st)
-                    : run_solve<float>(f, q, r, c, x, u, y, accumulate, st);
+  std::vector<uintptr_t> key = problem_key(f->dprob);
+  for (const void* p : {(const void*)q, (const void*)r, (const void*)c, (const void*)x, (const void*)u, (const void*)y})
+    key.push_back(up(p));
+  key.push_back((uintptr_t)accumulate);
+  return run_seq(f, solve_cache(f, key), key, st, [&](Recorder* rc) {
+    return f->ts == 8 ? run_solve<double>(f, rc, q, r, c, x, u, y, accumulate, st)
+                      : run_solve<float>(f, rc, q, r, c, x, u, y, accumulate, st);
+  });
+}
+
+cudaError_t residual_impl(tlqr_factor_t* f, const tlqr_problem& p, const double* x, const double* u,
+                          const double* y, int with_knorm, cudaStream_t st) {
+  std::vector<uintptr_t> key = problem_key(p);
+  for (const void* v : {(const void*)x, (const void*)u, (const void*)y}) key.push_back(up(v));
+  key.push_back((uintptr_t)with_knorm);
+  return run_seq(f, &f->g_resid[with_knorm ? 1 : 0], key, st,
+                 [&](Recorder* rc) { return run_residual(f, rc, p, x, u, y, with_knorm, st); });
 }
 
 }  // namespace
@@ -438,10 +653,20 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   if (!(f->opt.refine_tol > 0)) f->opt.refine_tol = 1e-8;
   f->ts = opts->precision == TLQR_PREC_FP64 ? 8 : 4;
   if (cudaGetDevice(&f->device)) { delete f; return TLQR_ERR_CUDA; }
+  if (cudaStreamCreateWithFlags(&f->work, cudaStreamNonBlocking) ||
+      cudaEventCreateWithFlags(&f->ev_in, cudaEventDisableTiming) ||
+      cudaEventCreateWithFlags(&f->ev_out, cudaEventDisableTiming)) {
+    delete f;
+    return TLQR_ERR_CUDA;
+  }
   // per-warp shared memory must fit one warp per block
   const WarpBytes wb = warp_bytes(n, m, f->ts);
   const size_t worst = std::max({wb.compress, wb.local_factor, wb.tau, wb.condense});
   if (worst > kSmemBudget) { delete f; return TLQR_ERR_ARG; }
+  if ((f->ts == 8 ? configure_kernels<double>(n, m) : configure_kernels<float>(n, m)) != cudaSuccess) {
+    delete f;
+    return TLQR_ERR_CUDA;
+  }
   int rc = upload_plan(f);
   if (rc) { delete f; return rc; }
   const size_t N = plan->N, nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
@@ -483,7 +708,8 @@ extern "C" int tlqr_factor(tlqr_factor_t* f, const tlqr_problem* prob, void* str
   if (!f) return TLQR_ERR_ARG;
   int rc = check_problem(f, prob, false);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
   tlqr_problem dp = *prob;
   if (prob->mem == TLQR_MEM_HOST) {
     if ((rc = stage_problem(f, prob, &dp, true, false, st))) return rc;
@@ -496,7 +722,8 @@ extern "C" int tlqr_solve_rhs(tlqr_factor_t* f, int32_t mem, const double* q, co
   if (!f || !q || !r || !c || !x || !u || !y) return TLQR_ERR_ARG;
   if (mem != TLQR_MEM_DEVICE && mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
   if (!f->factored) return TLQR_ERR_STATE;
-  cudaStream_t st = (cudaStream_t)stream;
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
   const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
   if (mem == TLQR_MEM_DEVICE) {
     if (solve_impl(f, q, r, c, x, u, y, 0, st)) return TLQR_ERR_CUDA;
@@ -513,13 +740,12 @@ extern "C" int tlqr_solve_rhs(tlqr_factor_t* f, int32_t mem, const double* q, co
   if (!e) e = d2h(u, s.u, N * m, st);
   if (!e) e = d2h(y, s.y, N * n, st);
   if (!e) e = cudaStreamSynchronize(st);
+  f->prof.harvest();
   return e ? TLQR_ERR_CUDA : TLQR_OK;
 }
 
-extern "C" int tlqr_get_PK(tlqr_factor_t* f, int32_t mem, double* P, double* K, void* stream) {
-  if (!f) return TLQR_ERR_ARG;
-  if (!f->factored) return TLQR_ERR_STATE;
-  cudaStream_t st = (cudaStream_t)stream;
+namespace {
+int get_PK_impl(tlqr_factor_t* f, int32_t mem, double* P, double* K, cudaStream_t st) {
   const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
   double *dP = P, *dK = K;
   if (mem == TLQR_MEM_HOST) {
@@ -538,7 +764,7 @@ extern "C" int tlqr_get_PK(tlqr_factor_t* f, int32_t mem, double* P, double* K, 
                                                (const float*)f->K, dP, dK);
   if (cudaGetLastError()) return TLQR_ERR_CUDA;
   f->prof.launches[TLQR_K_EXPORT]++;
-  f->prof.units[TLQR_K_EXPORT] += N;
+  f->prof.units[TLQR_K_EXPORT] += (int64_t)N;
   if (mem == TLQR_MEM_HOST) {
     cudaError_t e = d2h(P, dP, N * n * n, st);
     if (!e) e = d2h(K, dK, N * m * n, st);
@@ -547,13 +773,22 @@ extern "C" int tlqr_get_PK(tlqr_factor_t* f, int32_t mem, double* P, double* K, 
   }
   return TLQR_OK;
 }
+}  // namespace
+
+extern "C" int tlqr_get_PK(tlqr_factor_t* f, int32_t mem, double* P, double* K, void* stream) {
+  if (!f) return TLQR_ERR_ARG;
+  if (!f->factored) return TLQR_ERR_STATE;
+  StreamScope scope(f, stream);
+  return get_PK_impl(f, mem, P, K, scope.st);
+}
 
 extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solution* sol, void* stream) {
   if (!f || !sol || !sol->x || !sol->u || !sol->y) return TLQR_ERR_ARG;
   if (sol->mem != TLQR_MEM_DEVICE && sol->mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
   int rc = check_problem(f, prob, true);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
   const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
   tlqr_problem dp = *prob;
   if (prob->mem == TLQR_MEM_HOST) {
@@ -573,8 +808,11 @@ extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solut
     int steps = 0;
     double absr = 0, eta = INFINITY;
     for (;;) {
-      if (run_residual(f, dp, x, u, y, st)) return TLQR_ERR_CUDA;
-      if ((rc = read_status(f, st))) { f->factored = false; return rc; }
+      // residual graph: FP64 residual, ||.|| maxima and the status word to the host
+      if (residual_impl(f, dp, x, u, y, steps == 0 ? 1 : 0, st)) return TLQR_ERR_CUDA;
+      if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+      f->prof.harvest();
+      if ((rc = map_status(*f->h_status))) { f->factored = false; return rc; }
       residual_stats(f, &absr, &eta);
       if (eta <= f->opt.refine_tol || steps >= f->opt.max_refine || !std::isfinite(eta)) break;
       if (solve_impl(f, f->res_x, f->res_u, f->res_c, x, u, y, 1, st)) return TLQR_ERR_CUDA;
@@ -587,11 +825,7 @@ extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solut
     if (eta > f->opt.refine_tol) return TLQR_ERR_NO_CONVERGENCE;
   }
   if (sol->P || sol->K) {
-    if (sol->mem == TLQR_MEM_HOST) {
-      if ((rc = tlqr_get_PK(f, TLQR_MEM_HOST, sol->P, sol->K, stream))) return rc;
-    } else if ((rc = tlqr_get_PK(f, TLQR_MEM_DEVICE, sol->P, sol->K, stream))) {
-      return rc;
-    }
+    if ((rc = get_PK_impl(f, sol->mem, sol->P, sol->K, st))) return rc;
   }
   if (sol->mem == TLQR_MEM_HOST) {
     cudaError_t e = d2h(sol->x, x, N * n, st);
@@ -600,7 +834,9 @@ extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solut
     if (e) return TLQR_ERR_CUDA;
   }
   // one status read for factor, solve and recovery (synchronises the stream)
-  if ((rc = read_status(f, st))) { f->factored = false; return rc; }
+  rc = read_status(f, st);
+  f->prof.harvest();
+  if (rc) { f->factored = false; return rc; }
   return TLQR_OK;
 }
 
@@ -609,7 +845,8 @@ extern "C" int tlqr_kkt_residual(tlqr_factor_t* f, const tlqr_problem* prob, int
   if (!f || !x || !u || !y || !stats) return TLQR_ERR_ARG;
   int rc = check_problem(f, prob, true);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
   const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
   tlqr_problem dp = *prob;
   if (prob->mem == TLQR_MEM_HOST) {
@@ -622,7 +859,7 @@ extern "C" int tlqr_kkt_residual(tlqr_factor_t* f, const tlqr_problem* prob, int
     if (h2d(s.x, x, N * n, st) || h2d(s.u, u, N * m, st) || h2d(s.y, y, N * n, st)) return TLQR_ERR_CUDA;
     dx = s.x; du = s.u; dy = s.y;
   }
-  if (run_residual(f, dp, dx, du, dy, st) || cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+  if (run_residual(f, nullptr, dp, dx, du, dy, 1, st) || cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
   residual_stats(f, &stats[0], &stats[1]);
   return TLQR_OK;
 }
@@ -768,17 +1005,13 @@ extern "C" int tlqr_profile_mask(tlqr_factor_t* f, uint32_t mask) {
 
 extern "C" int tlqr_profile_read(tlqr_factor_t* f, tlqr_kernel_profile* out) {
   if (!f || !out) return TLQR_ERR_ARG;
-  for (int k = 0; k < TLQR_K_COUNT; ++k) out[k] = tlqr_kernel_profile{f->prof.launches[k], f->prof.units[k], 0, 0.0};
-  int rc = TLQR_OK;
-  for (auto& r : f->prof.recs) {
-    float ms = 0.f;
-    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) rc = TLQR_ERR_CUDA;
-    out[r.kind].timed++;
-    out[r.kind].ms += ms;
-    f->prof.pool.push_back(r.a);
-    f->prof.pool.push_back(r.b);
+  f->prof.harvest();
+  for (int k = 0; k < TLQR_K_COUNT; ++k) {
+    out[k] = tlqr_kernel_profile{f->prof.launches[k], f->prof.units[k], f->prof.timed[k], f->prof.ms[k]};
+    f->prof.launches[k] = f->prof.units[k] = f->prof.timed[k] = 0;
+    f->prof.ms[k] = 0.0;
   }
-  f->prof.recs.clear();
-  for (int k = 0; k < TLQR_K_COUNT; ++k) { f->prof.launches[k] = 0; f->prof.units[k] = 0; }
-  return rc;
+  const bool bad = f->prof.event_error;
+  f->prof.event_error = false;
+  return bad ? TLQR_ERR_CUDA : TLQR_OK;
 }

@@ -205,7 +205,7 @@ def tlqr_plan_schedule(plan, N: int):
 # ------------------------------------------------------------------ factor / solve
 
 def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
-                 refine_tol=1e-8, use_graphs=False) -> tlqr_options:
+                 refine_tol=1e-8, use_graphs=True) -> tlqr_options:
     o = tlqr_options()
     o.n, o.m, o.precision = int(n), int(m), int(precision)
     o.has_M, o.has_delta = int(bool(has_M)), int(bool(has_delta))
