@@ -203,6 +203,32 @@ int tlqr_get_PK(tlqr_factor_t *f, int32_t mem, double *P, double *K, void *strea
 int tlqr_kkt_residual(tlqr_factor_t *f, const tlqr_problem *prob, int32_t mem, const double *x,
                       const double *u, const double *y, double *stats, void *stream);
 
+/* Allocation-free FP64 KKT residual.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory while they
+ * run -- for example a receding-horizon controller with a hard deadline
+ * (cudaMalloc / cudaFree can synchronise the device and take unbounded time) or
+ * a process whose device memory belongs to another framework's allocator.  It
+ * computes the same stats as tlqr_kkt_residual() (stats[0] = ||K z - b||_inf,
+ * stats[1] = eta) from a plan alone, without a factor object.
+ *   - prob->mem must be TLQR_MEM_DEVICE; x [N][n], u [N][m], y [N][n] are device
+ *     pointers; stats is a host array of 2 doubles.
+ *   - Scratch (the tree's parent/child lists, the residual vectors and the
+ *     running maxima) lives in one fixed device array of
+ *     TLQR_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
+ *     the process exits; nothing is allocated per call.  A tree that needs
+ *     more scratch (about N (2n + m) 8 + 12 N bytes) is rejected with
+ *     TLQR_ERR_ARG before any work is issued.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the previous call's contents:
+ *     calls whose GPU work can overlap (different streams, different host
+ *     threads) race on it and must be serialised by the caller.
+ *   - Synchronises `stream`. */
+#define TLQR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int tlqr_kkt_residual_noalloc(const tlqr_plan_t *plan, int32_t n, int32_t m, const tlqr_problem *prob,
+                              const double *x, const double *u, const double *y, double *stats,
+                              void *stream);
+
 /* Refinement steps and backward error of the last tlqr_solve. */
 int tlqr_last_info(const tlqr_factor_t *f, tlqr_info *out);
 

@@ -71,7 +71,8 @@ EXPORTS = ["tlqr_plan_create", "tlqr_plan_destroy", "tlqr_plan_stats", "tlqr_pla
            "tlqr_factor_create", "tlqr_factor_destroy", "tlqr_factor", "tlqr_solve_rhs", "tlqr_solve",
            "tlqr_get_PK", "tlqr_kkt_residual", "tlqr_last_info", "tlqr_status_string",
            "tlqr_batched_tau", "tlqr_batched_compose", "tlqr_batched_condense",
-           "tlqr_lift_node_controls", "tlqr_project_lifted", "tlqr_profile_mask", "tlqr_profile_read"]
+           "tlqr_lift_node_controls", "tlqr_project_lifted", "tlqr_profile_mask", "tlqr_profile_read",
+           "tlqr_kkt_residual_noalloc"]
 
 KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
                 "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
@@ -112,6 +113,7 @@ def lib():
         L.tlqr_project_lifted.argtypes = [_i32, _i32, _i32, _ip] + [_dp] * 6
         L.tlqr_profile_mask.argtypes = [_vp, ctypes.c_uint32]
         L.tlqr_profile_read.argtypes = [_vp, ctypes.POINTER(tlqr_kernel_profile)]
+        L.tlqr_kkt_residual_noalloc.argtypes = [_vp, _i32, _i32, ctypes.POINTER(tlqr_problem), _dp, _dp, _dp, _dp, _vp]
         _lib = L
     return _lib
 
@@ -267,6 +269,15 @@ def tlqr_kkt_residual(f, data: dict, x, u, y, stream=None):
     st = np.zeros(2)
     _check(lib().tlqr_kkt_residual(f, ctypes.byref(p), mem, _ptr(x), _ptr(u), _ptr(y), _ptr(st),
                                    _stream(stream)), "tlqr_kkt_residual")
+    return dict(abs=float(st[0]), eta=float(st[1]))
+
+
+def tlqr_kkt_residual_noalloc(plan, n: int, m: int, data: dict, x, u, y, stream=None):
+    """FP64 KKT residual from a plan alone, with no device allocation (device arrays only)."""
+    p = make_problem(data)
+    st = np.zeros(2)
+    _check(lib().tlqr_kkt_residual_noalloc(plan, int(n), int(m), ctypes.byref(p), _ptr(x), _ptr(u), _ptr(y),
+                                           _ptr(st), _stream(stream)), "tlqr_kkt_residual_noalloc")
     return dict(abs=float(st[0]), eta=float(st[1]))
 
 
