@@ -86,7 +86,9 @@ typedef struct {
   int32_t max_refine;    /* MIXED: maximum refinement steps (default 10)          */
   double refine_tol;     /* MIXED: target eta (default 1e-8)                      */
   int32_t use_graphs;    /* 1: replay per-round launch sequences from CUDA graphs */
-  int32_t reserved[7];
+  int32_t generic_kernels; /* 1: use the run-time-n kernels even where compile-time-n
+                              kernels exist (n = 4, 6, 8, 12, 16); for testing        */
+  int32_t reserved[6];
 } tlqr_options;
 
 #define TLQR_MAX_DIM 64

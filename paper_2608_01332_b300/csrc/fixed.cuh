@@ -1,0 +1,993 @@
+// Compile-time-dimension kernels for the n x n local operations of the
+// contraction: rake fold, compression, reconstruction, transition composition,
+// and the O(n^2) right-hand-side passes.  Same arithmetic as kernels.cuh
+// (which handles any n at run time); used when n is one of the instantiated
+// sizes.
+//
+// Mapping: a group of G lanes (G = smallest power of two >= n, at most 32)
+// performs one operation, so a warp runs 32 / G operations side by side.  Lane
+// r of a group holds row r of the block it is working on in registers.  The
+// right operand of a product sits in shared memory (row stride LD, rows 16-byte
+// aligned) and is read as whole 16-byte vectors that every lane of the group
+// reads at the same address (broadcast): a lane performs W = 16 / sizeof(T)
+// FMAs per shared-memory load.  LU with partial pivoting keeps the rows where
+// they are (implicit pivoting): the pivot is found with group shuffles and its
+// row is broadcast through shared memory.  Loops over n are fully unrolled, so
+// all register indexing is static.
+#pragma once
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace tlqr {
+namespace fx {
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using V = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using V = double2; static constexpr int W = 2; };
+
+template <typename T, int N>
+struct D {
+  static constexpr int G = N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
+  static constexpr int W = Vec<T>::W;
+  static constexpr int LD = (N + W - 1) / W * W;       // padded row stride (elements)
+  static constexpr int NV = LD / W;                    // vectors per row
+  static constexpr int OPS = 32 / G;                   // operations per warp
+  static constexpr int MAT = N * LD;                   // elements of one staged matrix
+};
+
+template <typename T> __device__ __forceinline__ T vget(const typename Vec<T>::V& v, int i);
+template <> __device__ __forceinline__ float vget<float>(const float4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+template <> __device__ __forceinline__ double vget<double>(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+
+__device__ __forceinline__ void vset(float4& v, int i, float x) {
+  if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ void vset(double2& v, int i, double x) { if (i == 0) v.x = x; else v.y = x; }
+
+// Group context: lane within the group, group id within the block, validity.
+struct Grp {
+  int gl, gid;
+  bool valid;
+};
+
+template <typename T, int N>
+__device__ __forceinline__ Grp group_of(int count, int* op) {
+  constexpr int G = D<T, N>::G, OPS = D<T, N>::OPS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Grp g;
+  g.gl = lane & (G - 1);
+  g.gid = warp * OPS + lane / G;
+  const int o = blockIdx.x * (blockDim.x / G) + g.gid;
+  g.valid = o < count;
+  *op = g.valid ? o : count - 1;           // invalid groups shadow the last operation, store nothing
+  return g;
+}
+
+// Copy ROWS x COLS contiguous global elements into shared rows of stride LDS.
+template <typename T, int ROWS, int COLS, int LDS, int G, typename S>
+__device__ __forceinline__ void gload(T* dst, const S* src, int gl) {
+#pragma unroll
+  for (int e = gl; e < ROWS * COLS; e += G) {
+    const int r = e / COLS, c = e - (e / COLS) * COLS;
+    dst[r * LDS + c] = (T)src[e];
+  }
+}
+// Copy shared rows to contiguous global memory.
+template <typename T, int ROWS, int COLS, int LDS, int G, typename S>
+__device__ __forceinline__ void gstore(T* dst, const S* src, int gl) {
+#pragma unroll
+  for (int e = gl; e < ROWS * COLS; e += G) {
+    const int r = e / COLS, c = e - (e / COLS) * COLS;
+    dst[e] = (T)src[r * LDS + c];
+  }
+}
+
+// a[0..N) <- shared row (vector loads)
+template <typename T, int N>
+__device__ __forceinline__ void row_load(T (&a)[N], const T* row) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+#pragma unroll
+  for (int q = 0; q < D<T, N>::NV; ++q) {
+    const V v = reinterpret_cast<const V*>(row)[q];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+      if (q * W + i < N) a[q * W + i] = vget<T>(v, i);
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void row_store(T* row, const T (&a)[N]) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+#pragma unroll
+  for (int q = 0; q < D<T, N>::NV; ++q) {
+    V v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) vset(v, i, q * W + i < N ? a[q * W + i] : T(0));
+    reinterpret_cast<V*>(row)[q] = v;
+  }
+}
+
+// c[0..C) += sum_t a[t] * B[t][0..C)   (B in shared memory, row stride LDB, broadcast rows)
+template <typename T, int K, int C, int LDB>
+__device__ __forceinline__ void row_mm(T (&c)[C], const T (&a)[K], const T* B) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+#pragma unroll
+    for (int q = 0; q < (C + W - 1) / W; ++q) {
+      const V v = reinterpret_cast<const V*>(B + t * LDB)[q];
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+        if (q * W + i < C) c[q * W + i] = fma(a[t], vget<T>(v, i), c[q * W + i]);
+    }
+  }
+}
+// c[0..C) += sum_t A[t][r] * B[t][0..C)   (column r of A from shared memory)
+template <typename T, int K, int C, int LDA, int LDB>
+__device__ __forceinline__ void col_mm(T (&c)[C], const T* A, int r, const T* B) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const T at = A[t * LDA + r];
+#pragma unroll
+    for (int q = 0; q < (C + W - 1) / W; ++q) {
+      const V v = reinterpret_cast<const V*>(B + t * LDB)[q];
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+        if (q * W + i < C) c[q * W + i] = fma(at, vget<T>(v, i), c[q * W + i]);
+    }
+  }
+}
+// c[j] += sum_t a[t] * B[j][t]  for j < C  (rows of B from shared memory: a * B^T)
+template <typename T, int K, int C, int LDB>
+__device__ __forceinline__ void row_mmT(T (&c)[C], const T (&a)[K], const T* B) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    T s = c[j];
+#pragma unroll
+    for (int q = 0; q < (K + W - 1) / W; ++q) {
+      const V v = reinterpret_cast<const V*>(B + j * LDB)[q];
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+        if (q * W + i < K) s = fma(a[q * W + i], vget<T>(v, i), s);
+    }
+    c[j] = s;
+  }
+}
+
+template <typename T> __device__ __forceinline__ T pivot_key(T v) { return isnan(v) ? T(INFINITY) : tabs(v); }
+
+// LU with partial (implicit) pivoting of the N x N matrix whose row gl is in
+// a[] (lanes gl < N).  On return lane gl's row was chosen as pivot k = kpos:
+// a[j < k] are the multipliers L[k][j], a[j >= k] the entries U[k][j];
+// order[k] = lane of pivot k.  bc: N shared elements of this group.
+// Returns false (uniformly in the group) on a zero or nonfinite pivot.
+template <typename T, int N, int G>
+__device__ __forceinline__ bool glu(T (&a)[N], int gl, T* bc, int* order, int& kpos) {
+  bool done = gl >= N;
+  kpos = N;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    T v = done ? T(-1) : pivot_key(a[k]);
+    int idx = gl;
+#pragma unroll
+    for (int off = G / 2; off; off >>= 1) {
+      const T ov = __shfl_xor_sync(TLQR_FULL_MASK, v, off, G);
+      const int oi = __shfl_xor_sync(TLQR_FULL_MASK, idx, off, G);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    ok = ok && (v > T(0)) && tfinite(v);
+    if (gl == idx) {
+      kpos = k;
+      done = true;
+      order[k] = gl;
+#pragma unroll
+      for (int j = k; j < N; ++j) bc[j] = a[j];
+    }
+    __syncwarp();
+    if (!done) {
+      const T l = a[k] / bc[k];
+      a[k] = l;
+#pragma unroll
+      for (int j = k + 1; j < N; ++j) a[j] = fma(-l, bc[j], a[j]);
+    }
+    __syncwarp();
+  }
+  return ok;
+}
+
+// Solve (LU) X = B for R right-hand sides held by rows: lane gl holds row gl of
+// B in b[] on entry and row kpos of X on return.  bc: LDR shared elements.
+template <typename T, int N, int R>
+__device__ __forceinline__ void glu_solve(const T (&a)[N], int kpos, T (&b)[R], T* bc) {
+  constexpr int LDR = (R + Vec<T>::W - 1) / Vec<T>::W * Vec<T>::W;
+  (void)LDR;
+  // forward: L y = P b
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (kpos == k) row_store<T, R>(bc, b);
+    __syncwarp();
+    if (kpos > k && kpos < N) {
+      T y[R];
+      row_load<T, R>(y, bc);
+#pragma unroll
+      for (int c = 0; c < R; ++c) b[c] = fma(-a[k], y[c], b[c]);
+    }
+    __syncwarp();
+  }
+  // backward: U x = y
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    if (kpos == k) {
+      const T inv = T(1) / a[k];
+#pragma unroll
+      for (int c = 0; c < R; ++c) b[c] *= inv;
+      row_store<T, R>(bc, b);
+    }
+    __syncwarp();
+    if (kpos < k) {
+      T x[R];
+      row_load<T, R>(x, bc);
+#pragma unroll
+      for (int c = 0; c < R; ++c) b[c] = fma(-a[k], x[c], b[c]);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void zero(T (&a)[N]) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) a[j] = T(0);
+}
+
+// ---------------------------------------------------------------- tau
+// out = P + A^T U (I + C U)^{-1} A  (eq. terminal-fold) for one group.
+// sm (group): U, A, Y matrices + bc (LD) + order (N ints).
+template <typename T, int N>
+struct TauSmem {
+  static constexpr int elems = 3 * D<T, N>::MAT + D<T, N>::LD;
+  static constexpr int bytes = elems * (int)sizeof(T) + ((N * 4 + 15) / 16) * 16;
+};
+
+template <typename T, int N, typename S>
+__device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag, const S* Cg, const S* Pg, T* out,
+                                          T* sm) {
+  using Dm = D<T, N>;
+  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT;
+  T *sU = sm, *sA = sm + MAT, *sY = sm + 2 * MAT, *bc = sm + 3 * MAT;
+  int* order = reinterpret_cast<int*>(sm + 3 * MAT + LD);
+  gload<T, N, N, LD, G>(sU, Ug, g.gl);
+  gload<T, N, N, LD, G>(sA, Ag, g.gl);
+  gload<T, N, N, LD, G>(sY, Cg, g.gl);      // C staged in sY
+  __syncwarp();
+  const int r = g.gl < N ? g.gl : 0;
+  T x[N], b[N];
+  {
+    T crow[N];
+    row_load<T, N>(crow, sY + r * LD);
+    zero(x);
+    row_mm<T, N, N, LD>(x, crow, sU);           // row r of C U
+#pragma unroll
+    for (int c = 0; c < N; ++c) x[c] += (c == r) ? T(1) : T(0);
+  }
+  row_load<T, N>(b, sA + r * LD);               // row r of A (right-hand side)
+  __syncwarp();
+  int kpos;
+  const bool ok = glu<T, N, G>(x, g.gl, bc, order, kpos);
+  glu_solve<T, N, N>(x, kpos, b, bc);           // Y = (I + C U)^{-1} A, row kpos in b
+  if (g.gl < N) row_store<T, N>(sY + kpos * LD, b);
+  __syncwarp();
+  T z[N];
+  {
+    T urow[N];
+    row_load<T, N>(urow, sU + r * LD);
+    zero(z);
+    row_mm<T, N, N, LD>(z, urow, sY);           // row r of Z = U Y
+  }
+  __syncwarp();
+  if (g.gl < N) row_store<T, N>(sU + r * LD, z); // Z over U
+  __syncwarp();
+  T o[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) o[j] = (T)Pg[r * N + j];
+  col_mm<T, N, N, LD, LD>(o, sA, r, sU);        // P + A^T Z
+  if (g.valid && g.gl < N) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) out[r * N + j] = o[j];
+  }
+  return ok;
+}
+
+template <typename T, int N>
+__global__ void kf_rake(Ws<T> w, int begin, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  T* sm = reinterpret_cast<T*>(smem_raw + g.gid * TauSmem<T, N>::bytes);
+  const int rr = begin + op, j = w.rake_leaf[rr];
+  const size_t o = (size_t)j * N * N;
+  const bool ok = tau_group<T, N>(g, w.U + o, w.Ea + o, w.Ec + o, w.Ep + o, w.contrib + (size_t)rr * N * N, sm);
+  if (!ok && g.valid && g.gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
+}
+
+template <typename T, int N>
+__global__ void kf_expand(Ws<T> w, int begin, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  T* sm = reinterpret_cast<T*>(smem_raw + g.gid * TauSmem<T, N>::bytes);
+  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr];
+  const size_t oj = (size_t)j * N * N;
+  const bool ok = tau_group<T, N>(g, w.U + (size_t)k * N * N, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm);
+  if (!ok && g.valid && g.gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
+}
+
+// ---------------------------------------------------------------- compress
+// eq. (compress-intermediates)-(composition) with the tape of
+// eq. (quadratic-compress).  sm (group): Pt, Al, Cl, Ar, Y (2 matrices of
+// 2N columns), bc (2 LD), order.
+template <typename T, int N>
+struct CompSmem {
+  static constexpr int LD2 = 2 * D<T, N>::LD;             // [Y1 | Y2] row stride, Y2 at column LD
+  static constexpr int elems = 4 * D<T, N>::MAT + N * LD2 + LD2;
+  static constexpr int bytes = elems * (int)sizeof(T) + ((N * 4 + 15) / 16) * 16;
+};
+
+template <typename T, int N>
+__global__ void kf_compress(Ws<T> w, int begin, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Dm = D<T, N>;
+  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, LD2 = CompSmem<T, N>::LD2, NN = N * N;
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  T* sm = reinterpret_cast<T*>(smem_raw + g.gid * CompSmem<T, N>::bytes);
+  T *sPt = sm, *sAl = sm + MAT, *sCl = sm + 2 * MAT, *sAr = sm + 3 * MAT, *sY = sm + 4 * MAT,
+    *bc = sm + 4 * MAT + N * LD2;
+  int* order = reinterpret_cast<int*>(bc + LD2);
+  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr];
+  const size_t oj = (size_t)j * NN, ok_ = (size_t)k * NN;
+  const int gl = g.gl, r = gl < N ? gl : 0;
+  // stage; P~ = P_r + U_j
+#pragma unroll
+  for (int e = gl; e < NN; e += G) {
+    const int a = e / N, c = e - (e / N) * N;
+    sPt[a * LD + c] = w.Ep[ok_ + e] + w.U[oj + e];
+  }
+  gload<T, N, N, LD, G>(sAl, w.Ea + oj, gl);
+  gload<T, N, N, LD, G>(sCl, w.Ec + oj, gl);
+  gload<T, N, N, LD, G>(sAr, w.Ea + ok_, gl);
+  __syncwarp();
+  T s[N], b[2 * LD];
+  {
+    T cl[N], t1[N], t2[N];
+    row_load<T, N>(cl, sCl + r * LD);
+    zero(s);
+    row_mm<T, N, N, LD>(s, cl, sPt);            // row r of C_l P~
+#pragma unroll
+    for (int c = 0; c < N; ++c) s[c] += (c == r) ? T(1) : T(0);   // S = I + C_l P~
+    row_load<T, N>(t1, sAl + r * LD);
+    zero(t2);
+    row_mmT<T, N, N, LD>(t2, cl, sAr);          // row r of C_l A_r^T
+#pragma unroll
+    for (int c = 0; c < 2 * LD; ++c)
+      b[c] = c < N ? t1[c] : (c >= LD && c < LD + N) ? t2[c - LD] : T(0);
+  }
+  __syncwarp();
+  int kpos;
+  const bool okf = glu<T, N, G>(s, gl, bc, order, kpos);
+  glu_solve<T, N, 2 * LD>(s, kpos, b, bc);      // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
+  if (gl < N) row_store<T, 2 * LD>(sY + kpos * LD2, b);
+  __syncwarp();
+  // A_new = A_r Y1, C_new = C_r + A_r Y2  (rows r); C_r read before slot k is overwritten
+  T an[N], cn[N];
+  {
+    T ar[N];
+    row_load<T, N>(ar, sAr + r * LD);
+    zero(an);
+    row_mm<T, N, N, LD2>(an, ar, sY);
+#pragma unroll
+    for (int c = 0; c < N; ++c) cn[c] = w.Ec[ok_ + r * N + c];
+    row_mm<T, N, N, LD2>(cn, ar, sY + LD);
+  }
+  // W = P~ Y1 (rows r) -> over C_l ; P_new = P_l + A_l^T W
+  {
+    T pt[N], wr[N];
+    row_load<T, N>(pt, sPt + r * LD);
+    zero(wr);
+    row_mm<T, N, N, LD2>(wr, pt, sY);
+    __syncwarp();
+    if (gl < N) row_store<T, N>(sCl + r * LD, wr);
+  }
+  __syncwarp();
+  T pn[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) pn[c] = w.Ep[oj + r * N + c];    // P_l, read before slot j is overwritten
+  col_mm<T, N, N, LD, LD>(pn, sAl, r, sCl);
+  __syncwarp();
+  if (g.valid && gl < N) {
+    // tape into slot j: (A_r, C_r, P~); composed edge into slot k
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      w.Ea[oj + r * N + c] = sAr[r * LD + c];
+      w.Ec[oj + r * N + c] = w.Ec[ok_ + r * N + c];
+      w.Ep[oj + r * N + c] = sPt[r * LD + c];
+    }
+  }
+  __syncwarp();
+  if (g.valid && gl < N) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      w.Ea[ok_ + r * N + c] = an[c];
+      w.Ec[ok_ + r * N + c] = cn[c];
+      w.Ep[ok_ + r * N + c] = pn[c];
+    }
+  }
+  if (!okf && g.valid && gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
+}
+
+// ---------------------------------------------------------------- composite transitions
+// Tr_j <- T_k ; T_k <- T_k T_j  (eq. transition-compose), one group per compression.
+template <typename T, int N>
+struct ComposeSmem {
+  static constexpr int bytes = D<T, N>::MAT * (int)sizeof(T);
+};
+
+template <typename T, int N>
+__global__ void kf_compose_T(Ws<T> w, int begin, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Dm = D<T, N>;
+  constexpr int G = Dm::G, LD = Dm::LD, NN = N * N;
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  T* sTj = reinterpret_cast<T*>(smem_raw + g.gid * ComposeSmem<T, N>::bytes);
+  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr];
+  const int gl = g.gl, r = gl < N ? gl : 0;
+  gload<T, N, N, LD, G>(sTj, w.Tm + (size_t)j * NN, gl);
+  T tk[N], o[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) tk[c] = w.Tm[(size_t)k * NN + r * N + c];
+  __syncwarp();
+  zero(o);
+  row_mm<T, N, N, LD>(o, tk, sTj);
+  if (g.valid && gl < N) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      w.Tr[(size_t)j * NN + r * N + c] = tk[c];
+      w.Tm[(size_t)k * NN + r * N + c] = o[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- vector passes
+// One group per operation; lane r owns entry r of the output vector.
+template <typename T, int N>
+__device__ __forceinline__ void vec_load(T (&v)[N], const T* src) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) v[c] = src[c];
+}
+
+// contribution cv_r = T_j^T h_j + z_j  (eq. affine-rake)
+template <typename T, int N>
+__global__ void kf_aff_rake(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  const int rr = begin + op, j = w.rake_leaf[rr], r = g.gl < N ? g.gl : 0;
+  const T* Tj = w.Tm + (size_t)j * N * N;
+  T h[N];
+  vec_load(h, w.h + (size_t)j * N);
+  T s = w.z[(size_t)j * N + r];
+#pragma unroll
+  for (int t = 0; t < N; ++t) s = fma(Tj[t * N + r], h[t], s);
+  if (g.valid && g.gl < N) w.cv[(size_t)rr * N + r] = s;
+}
+
+// s_j = h_j + z_k ; z_k <- z_j + T_j^T s_j  (eq. affine-compose)
+template <typename T, int N>
+__global__ void kf_aff_compress(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr], r = g.gl < N ? g.gl : 0;
+  const T* Tj = w.Tm + (size_t)j * N * N;
+  T sv[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) sv[c] = w.h[(size_t)j * N + c] + w.z[(size_t)k * N + c];
+  T acc = w.z[(size_t)j * N + r];
+#pragma unroll
+  for (int t = 0; t < N; ++t) acc = fma(Tj[t * N + r], sv[t], acc);
+  const T sr = w.h[(size_t)j * N + r] + w.z[(size_t)k * N + r];
+  __syncwarp();
+  if (g.valid && g.gl < N) {
+    w.s[(size_t)j * N + r] = sr;
+    w.z[(size_t)k * N + r] = acc;
+  }
+}
+
+// p_j = Tr_j^T p_k + s_j  (affine expansion)
+template <typename T, int N>
+__global__ void kf_aff_expand(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr], r = g.gl < N ? g.gl : 0;
+  const T* Trj = w.Tr + (size_t)j * N * N;
+  T p[N];
+  vec_load(p, w.h + (size_t)k * N);
+  T acc = w.s[(size_t)j * N + r];
+#pragma unroll
+  for (int t = 0; t < N; ++t) acc = fma(Trj[t * N + r], p[t], acc);
+  if (g.valid && g.gl < N) w.h[(size_t)j * N + r] = acc;
+}
+
+// b_k <- Tr_j b_j + b_k  (state-map composition of the offsets)
+template <typename T, int N>
+__global__ void kf_state_compress(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr], r = g.gl < N ? g.gl : 0;
+  const T* Trj = w.Tr + (size_t)j * N * N + r * N;
+  T b[N];
+  vec_load(b, w.bv + (size_t)j * N);
+  T acc = w.bv[(size_t)k * N + r];
+#pragma unroll
+  for (int t = 0; t < N; ++t) acc = fma(Trj[t], b[t], acc);
+  __syncwarp();
+  if (g.valid && g.gl < N) w.bv[(size_t)k * N + r] = acc;
+}
+
+// x_j = T_j x_i + b_j  (state expansion)
+template <typename T, int N>
+__global__ void kf_state_expand(Ws<T> w, const int* nodes, const int* from, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  const int rr = begin + op, j = nodes[rr], i = from[rr], r = g.gl < N ? g.gl : 0;
+  const T* Tj = w.Tm + (size_t)j * N * N + r * N;
+  T x[N];
+  vec_load(x, w.xs + (size_t)i * N);
+  T acc = w.bv[(size_t)j * N + r];
+#pragma unroll
+  for (int t = 0; t < N; ++t) acc = fma(Tj[t], x[t], acc);
+  if (g.valid && g.gl < N) w.xs[(size_t)j * N + r] = acc;
+}
+
+}  // namespace fx
+}  // namespace tlqr
+
+namespace tlqr {
+namespace fx {
+
+// ================================================================ (n, m) kernels
+// One group per node; lane r < N owns row r.  The m x m blocks (R, G) are
+// factored redundantly by every lane of the group (m <= 8).
+
+// Broadcast a length-N vector whose entry r lives in lane r of the group.
+template <typename T, int N, int G>
+__device__ __forceinline__ void gather_vec(T (&v)[N], T mine) {
+#pragma unroll
+  for (int t = 0; t < N; ++t) v[t] = __shfl_sync(TLQR_FULL_MASK, mine, t, G);
+}
+
+// In-register Cholesky of an M x M block (lower), returns false if not PD.
+template <typename T, int M>
+__device__ __forceinline__ bool chol_reg(T (&g)[M][M]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    T d = g[k][k];
+#pragma unroll
+    for (int t = 0; t < k; ++t) d = fma(-g[k][t], g[k][t], d);
+    ok = ok && d > T(0) && tfinite(d);
+    const T s = sqrt(d > T(0) ? d : T(1));
+    g[k][k] = s;
+    const T inv = T(1) / s;
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      T v = g[i][k];
+#pragma unroll
+      for (int t = 0; t < k; ++t) v = fma(-g[i][t], g[k][t], v);
+      g[i][k] = v * inv;
+    }
+  }
+  return ok;
+}
+// Solve L L^T x = b in registers.
+template <typename T, int M>
+__device__ __forceinline__ void chol_solve_reg(const T (&l)[M][M], T (&b)[M]) {
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    T v = b[i];
+#pragma unroll
+    for (int t = 0; t < i; ++t) v = fma(-l[i][t], b[t], v);
+    b[i] = v / l[i][i];
+  }
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i) {
+    T v = b[i];
+#pragma unroll
+    for (int t = i + 1; t < M; ++t) v = fma(-l[t][i], b[t], v);
+    b[i] = v / l[i][i];
+  }
+}
+
+template <typename T, int N, int M>
+struct CondSmem {
+  static constexpr int bytes = ((2 * N * M * (int)sizeof(T) + 15) / 16) * 16;   // B and M blocks
+};
+
+// Condensation eq. (edge-components), U_i <- Q_i, Delta flag.  All groups of a
+// warp run the same instruction sequence; the root's group computes on its
+// (ignored) edge slot and stores nothing but U and the flag.
+template <typename T, int N, int M>
+__global__ void kf_condense(Ws<T> w, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int G = D<T, N>::G, NN = N * N, NM = N * M;
+  int i;
+  const Grp g = group_of<T, N>(count, &i);
+  T* sB = reinterpret_cast<T*>(smem_raw + g.gid * CondSmem<T, N, M>::bytes);
+  T* sM = sB + NM;
+  const int gl = g.gl, r = gl < N ? gl : 0;
+  const size_t oi = (size_t)i * NN;
+  const bool is_root = i == w.root;
+  bool dnz = false;
+  if (w.has_delta) {
+    bool mine = false;
+#pragma unroll
+    for (int e = gl; e < NN; e += G) mine |= (w.Delta[oi + e] != 0.0);
+    const unsigned bal = __ballot_sync(TLQR_FULL_MASK, mine);
+    const int base = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+    dnz = ((bal >> base) & gm) != 0;
+  }
+  if (g.valid) {
+#pragma unroll
+    for (int e = gl; e < NN; e += G) w.U[oi + e] = (T)w.Q[oi + e];
+    if (w.has_delta && gl == 0) w.dflag[i] = dnz ? 1 : 0;
+  }
+  const size_t om = (size_t)i * NM;
+#pragma unroll
+  for (int e = gl; e < NM; e += G) sB[e] = (T)w.B[om + e];
+  if (w.has_M) {
+#pragma unroll
+    for (int e = gl; e < NM; e += G) sM[e] = (T)w.M[om + e];
+  }
+  T Rl[M][M];
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int b = 0; b < M; ++b) Rl[a][b] = (T)w.R[(size_t)i * M * M + a * M + b];
+  const bool ok = chol_reg<T, M>(Rl);
+  __syncwarp();
+  T br[M], mr[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) { br[a] = sB[r * M + a]; mr[a] = w.has_M ? sM[r * M + a] : T(0); }
+  chol_solve_reg<T, M>(Rl, br);                 // row r of B R^{-1}
+  if (w.has_M) chol_solve_reg<T, M>(Rl, mr);    // row r of M R^{-1}
+  if (g.valid && !is_root && gl < N) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      T cb = dnz ? (T)w.Delta[oi + r * N + c] : T(0);
+      T ab = (T)w.A[oi + r * N + c];
+      T pb = T(0);
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        cb = fma(br[a], sB[c * M + a], cb);
+        if (w.has_M) { ab = fma(-br[a], sM[c * M + a], ab); pb = fma(-mr[a], sM[c * M + a], pb); }
+      }
+      w.Ec[oi + r * N + c] = cb;
+      w.Ea[oi + r * N + c] = ab;
+      w.Ep[oi + r * N + c] = pb;
+    }
+  }
+  if (!ok && g.valid && !is_root && gl == 0) atomicCAS(w.status, 0, ST_NOT_PD);
+}
+
+template <typename T, int N, int M>
+struct LfSmem {
+  static constexpr int MAT = D<T, N>::MAT;
+  // P, Finv, A_cl, K (M rows of LD), W B (N x M), B (N x M), bc (LD); then order (N ints)
+  static constexpr int elems = 3 * MAT + M * D<T, N>::LD + 2 * N * M + D<T, N>::LD;
+  static constexpr int tbytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
+  static constexpr int bytes = tbytes + ((N * 4 + 15) / 16) * 16;
+};
+
+// Local factors eq. (FW), (factor-local).  The F = I + Delta P branch runs in
+// every group of a warp when any of them needs it (a group without Delta then
+// factors F = I and ignores the result), so the warp stays converged.
+template <typename T, int N, int M>
+__global__ void kf_local_factor(Ws<T> w, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Dm = D<T, N>;
+  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, NN = N * N, NM = N * M;
+  int j;
+  const Grp g = group_of<T, N>(count, &j);
+  unsigned char* gbase = smem_raw + g.gid * LfSmem<T, N, M>::bytes;
+  T* sm = reinterpret_cast<T*>(gbase);
+  T *sP = sm, *sFi = sm + MAT, *sAc = sm + 2 * MAT, *sK = sm + 3 * MAT, *sWB = sK + M * LD, *sB = sWB + NM,
+    *bc = sB + NM;
+  int* order = reinterpret_cast<int*>(gbase + LfSmem<T, N, M>::tbytes);
+  const int gl = g.gl, r = gl < N ? gl : 0;
+  const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
+  const bool is_root = j == w.root;
+  gload<T, N, N, LD, G>(sP, w.U + oj, gl);
+  const bool dnz = w.has_delta && w.dflag[j];
+  const bool any_dnz = __any_sync(TLQR_FULL_MASK, dnz);
+  __syncwarp();
+  T wrow[N];
+  row_load<T, N>(wrow, sP + r * LD);            // W = P unless Delta_j != 0
+  bool ok = true;
+  if (any_dnz) {
+    T f[N], e[N];
+    zero(f);
+    if (dnz) {
+      T dr[N];
+#pragma unroll
+      for (int c = 0; c < N; ++c) dr[c] = (T)w.Delta[oj + r * N + c];
+      row_mm<T, N, N, LD>(f, dr, sP);           // row r of Delta P
+    }
+#pragma unroll
+    for (int c = 0; c < N; ++c) { f[c] += (c == r) ? T(1) : T(0); e[c] = (c == r) ? T(1) : T(0); }
+    int kpos;
+    ok = glu<T, N, G>(f, gl, bc, order, kpos);
+    glu_solve<T, N, N>(f, kpos, e, bc);         // rows of F^{-1}
+    if (gl < N) row_store<T, N>(sFi + kpos * LD, e);
+    __syncwarp();
+    if (dnz) {
+      zero(wrow);
+      T pr[N];
+      row_load<T, N>(pr, sP + r * LD);
+      row_mm<T, N, N, LD>(wrow, pr, sFi);       // row r of W = P F^{-1}
+      if (g.valid && gl < N) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          w.Finv[oj + r * N + c] = sFi[r * LD + c];
+          w.W[oj + r * N + c] = wrow[c];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int e = gl; e < NM; e += G) sB[e] = (T)w.B[om + e];
+  __syncwarp();
+  T wb[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) wb[a] = T(0);
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+#pragma unroll
+    for (int a = 0; a < M; ++a) wb[a] = fma(wrow[t], sB[t * M + a], wb[a]);
+  if (gl < N) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) sWB[r * M + a] = wb[a];
+  }
+#pragma unroll
+  for (int e = gl; e < NN; e += G) {
+    const int a = e / N, c = e - (e / N) * N;
+    sAc[a * LD + c] = (T)w.A[oj + e];
+  }
+  __syncwarp();
+  // G = R + B^T (W B), factored in every lane of the group
+  T Gl[M][M];
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      T v = (T)w.R[(size_t)j * M * M + a * M + b];
+#pragma unroll
+      for (int t = 0; t < N; ++t) v = fma(sB[t * M + a], sWB[t * M + b], v);
+      Gl[a][b] = v;
+    }
+  const bool okg = chol_reg<T, M>(Gl);
+  // column r of H = (W B)^T A + M^T; K(:, r) = -G^{-1} H(:, r)
+  T hc[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) hc[a] = w.has_M ? (T)w.M[om + r * M + a] : T(0);
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    const T at = sAc[t * LD + r];
+#pragma unroll
+    for (int a = 0; a < M; ++a) hc[a] = fma(sWB[t * M + a], at, hc[a]);
+  }
+  chol_solve_reg<T, M>(Gl, hc);
+  if (gl < N) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) sK[a * LD + r] = -hc[a];
+  }
+  __syncwarp();
+  // row r of A_cl = A + B K
+  T ac[N], brow[M];
+  row_load<T, N>(ac, sAc + r * LD);
+#pragma unroll
+  for (int a = 0; a < M; ++a) brow[a] = sB[r * M + a];
+  row_mm<T, M, N, LD>(ac, brow, sK);
+  const bool store = g.valid && !is_root;
+  if (store && gl < N) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) w.K[om + a * N + r] = sK[a * LD + r];
+  }
+  if (store && gl == 0) {
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+      for (int b = 0; b < M; ++b) w.LG[(size_t)j * M * M + a * M + b] = Gl[a][b];
+  }
+  __syncwarp();
+  if (gl < N) row_store<T, N>(sAc + r * LD, ac);
+  __syncwarp();
+  T t[N];
+  if (any_dnz) {
+    T fr[N];
+    row_load<T, N>(fr, sFi + r * LD);
+    zero(t);
+    row_mm<T, N, N, LD>(t, fr, sAc);           // T = F^{-1} A_cl
+  }
+  if (store && gl < N) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) w.Tm[oj + r * N + c] = dnz ? t[c] : ac[c];
+  }
+  if (g.valid && gl == 0) {
+    if (dnz && !ok) atomicCAS(w.status, 0, ST_SINGULAR);
+    else if (!is_root && !okg) atomicCAS(w.status, 0, ST_NOT_PD);
+  }
+}
+
+// Affine edge data eq. (affine-edge): h = q, z = K^T (r + B^T w) + A^T w, w = W c.
+template <typename T, int N, int M>
+__global__ void kf_aff_init(Ws<T> w, int count) {
+  constexpr int G = D<T, N>::G, NN = N * N, NM = N * M;
+  int j;
+  const Grp g = group_of<T, N>(count, &j);
+  const int gl = g.gl, r = gl < N ? gl : 0;
+  const bool is_root = j == w.root;
+  if (g.valid && gl < N) w.h[(size_t)j * N + r] = (T)w.q[(size_t)j * N + r];
+  const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
+  const bool dnz = w.has_delta && w.dflag[j];
+  const T* Wm = dnz ? w.W + oj : w.U + oj;
+  T wr = T(0);                                  // w = W c, W symmetric: columns, coalesced across lanes
+#pragma unroll
+  for (int t = 0; t < N; ++t) wr = fma(Wm[t * N + r], (T)w.c[(size_t)j * N + t], wr);
+  T wv[N];
+  gather_vec<T, N, G>(wv, wr);
+  T v[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) v[a] = (T)w.r[(size_t)j * M + a];
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+#pragma unroll
+    for (int a = 0; a < M; ++a) v[a] = fma((T)w.B[om + t * M + a], wv[t], v[a]);
+  T z = T(0);
+#pragma unroll
+  for (int a = 0; a < M; ++a) z = fma(w.K[om + a * N + r], v[a], z);
+#pragma unroll
+  for (int t = 0; t < N; ++t) z = fma((T)w.A[oj + t * N + r], wv[t], z);
+  if (g.valid && !is_root && gl < N) w.z[(size_t)j * N + r] = z;
+}
+
+// Local affine solve eq. (local-affine-solve) and the root state eq. (xroot).
+template <typename T, int N, int M>
+__global__ void kf_local_solve(Ws<T> w, int count) {
+  constexpr int G = D<T, N>::G, NN = N * N, NM = N * M;
+  int j;
+  const Grp g = group_of<T, N>(count, &j);
+  const int gl = g.gl, r = gl < N ? gl : 0;
+  const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
+  const bool dnz = w.has_delta && w.dflag[j];
+  const bool is_root = j == w.root;
+  T p[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) p[t] = w.h[(size_t)j * N + t];
+  T pr = p[0];
+#pragma unroll
+  for (int t = 0; t < N; ++t) pr = (t == r) ? p[t] : pr;
+  T fr = -(T)w.c[(size_t)j * N + r];
+  if (dnz) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) fr = fma((T)w.Delta[oj + t * N + r], p[t], fr);   // Delta symmetric
+  }
+  T f[N];
+  gather_vec<T, N, G>(f, fr);                   // f = Delta p - c
+  // root: x = -F^{-1} f
+  T xr = -fr;
+  if (dnz) {
+    xr = T(0);
+#pragma unroll
+    for (int t = 0; t < N; ++t) xr = fma(-w.Finv[oj + r * N + t], f[t], xr);
+  }
+  // g = p - W f
+  const T* Wm = dnz ? w.W + oj : w.U + oj;
+  T gr = pr;
+#pragma unroll
+  for (int t = 0; t < N; ++t) gr = fma(-Wm[t * N + r], f[t], gr);               // W symmetric
+  T gv[N];
+  gather_vec<T, N, G>(gv, gr);
+  // k = -G^{-1}(r + B^T g)
+  T k[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) k[a] = (T)w.r[(size_t)j * M + a];
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+#pragma unroll
+    for (int a = 0; a < M; ++a) k[a] = fma((T)w.B[om + t * M + a], gv[t], k[a]);
+  T Lg[M][M];
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int b = 0; b < M; ++b) Lg[a][b] = is_root ? ((a == b) ? T(1) : T(0)) : w.LG[(size_t)j * M * M + a * M + b];
+  chol_solve_reg<T, M>(Lg, k);
+#pragma unroll
+  for (int a = 0; a < M; ++a) k[a] = -k[a];
+  // b = F^{-1}(B k - f)
+  T tr = -fr;
+#pragma unroll
+  for (int a = 0; a < M; ++a) tr = fma((T)w.B[om + r * M + a], k[a], tr);
+  T tv[N];
+  gather_vec<T, N, G>(tv, tr);
+  T b = tr;
+  if (dnz) {
+    b = T(0);
+#pragma unroll
+    for (int t = 0; t < N; ++t) b = fma(w.Finv[oj + r * N + t], tv[t], b);
+  }
+  if (g.valid) {
+    if (is_root) {
+      if (gl < N) w.xs[(size_t)j * N + r] = xr;
+    } else {
+      if (gl == 0) {
+#pragma unroll
+        for (int a = 0; a < M; ++a) w.kv[(size_t)j * M + a] = k[a];
+      }
+      if (gl < N) w.bv[(size_t)j * N + r] = b;
+    }
+  }
+}
+
+// Recovery eq. (recover) into FP64 x, u, y (written or accumulated).
+template <typename T, int N, int M>
+__global__ void kf_recover(Ws<T> w, double* x, double* u, double* y, int accumulate, int count) {
+  constexpr int NN = N * N, NM = N * M;
+  int j;
+  const Grp g = group_of<T, N>(count, &j);
+  const int gl = g.gl, r = gl < N ? gl : 0;
+  T xv[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) xv[t] = w.xs[(size_t)j * N + t];
+  T xr = xv[0];
+#pragma unroll
+  for (int t = 0; t < N; ++t) xr = (t == r) ? xv[t] : xr;
+  T yr = w.h[(size_t)j * N + r];
+#pragma unroll
+  for (int t = 0; t < N; ++t) yr = fma(w.U[(size_t)j * NN + t * N + r], xv[t], yr);   // P symmetric
+  bool bad = !tfinite(xr) || !tfinite(yr);
+  const bool nonroot = j != w.root;
+  T ur = T(0);
+  if (nonroot && gl < M) {
+    const int par = w.parent[j];
+    ur = w.kv[(size_t)j * M + gl];
+#pragma unroll
+    for (int t = 0; t < N; ++t) ur = fma(w.K[(size_t)j * NM + gl * N + t], w.xs[(size_t)par * N + t], ur);
+    bad |= !tfinite(ur);
+  }
+  if (g.valid) {
+    if (gl < N) {
+      const size_t o = (size_t)j * N + r;
+      if (accumulate) { x[o] += (double)xr; y[o] += (double)yr; }
+      else { x[o] = (double)xr; y[o] = (double)yr; }
+    }
+    if (gl < M) {
+      const size_t o = (size_t)j * M + gl;
+      if (nonroot) { if (accumulate) u[o] += (double)ur; else u[o] = (double)ur; }
+      else if (!accumulate) u[o] = 0.0;
+    }
+    if (bad) atomicCAS(w.status, 0, ST_NONFINITE);
+  }
+}
+
+}  // namespace fx
+}  // namespace tlqr

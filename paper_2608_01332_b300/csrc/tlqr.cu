@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/tlqr.h"
+#include "fixed.cuh"
 #include "kernels.cuh"
 #include "plan.hpp"
 #include "residual.cuh"
@@ -223,6 +224,8 @@ struct tlqr_factor_t {
   // own non-blocking work stream (capturable), fenced to the caller's stream
   cudaStream_t work = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int fixed_n = 0;                 // n of the fixed-dimension kernels in use (0 = run-time n)
+  int fixed_m = 0;                 // m of the fixed (n, m) kernels in use (0 = run-time m)
 
   template <typename T>
   Ws<T> ws(const tlqr_problem& p) const {
@@ -309,33 +312,96 @@ int upload_plan(tlqr_factor_t* f) {
   return TLQR_OK;
 }
 
-template <typename T>
+// Launch `count` operations of a fixed-dimension kernel: groups of G lanes,
+// 128-thread blocks, `gbytes` of shared memory per group.
+template <typename Kernel, typename... Args>
+cudaError_t launch_groups(Recorder* rc, int kind, Kernel kernel, int count, int G, size_t gbytes, cudaStream_t st,
+                          Args... args) {
+  if (count <= 0) return cudaSuccess;
+  constexpr int threads = 128;
+  const int gpb = threads / G;
+  const size_t smem = gbytes * gpb;
+  if (!(rc && rc->capture)) {
+    cudaError_t e = ensure_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = (count + gpb - 1) / gpb;
+  const bool timed = rc && (rc->mask >> kind) & 1u;
+  EvPair ev{kind, nullptr, nullptr};
+  if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
+  kernel<<<blocks, threads, smem, st>>>(args...);
+  cudaError_t e = cudaGetLastError();
+  if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
+  if (rc) { rc->launches[kind]++; rc->units[kind] += count; }
+  return e;
+}
+
+// Factorisation sequence (Alg. 1 steps 2-3).  NF = compile-time n of the
+// fixed-dimension kernels, 0 = the run-time-n kernels.
+template <typename T, int NF, int MF>
 cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cudaStream_t st) {
   const tlqr_plan_t* P = f->plan;
   const Ws<T> w = f->ws<T>(p);
   const WarpBytes wb = warp_bytes(f->opt.n, f->opt.m, sizeof(T));
+  constexpr int NX = NF > 0 ? NF : 4;          // placeholder dimension when NF == 0 (never launched)
+  constexpr int MX = MF > 0 ? MF : 2;
+  constexpr int G = fx::D<T, NX>::G;
   cudaError_t e;
   if ((e = cudaMemsetAsync(f->status, 0, sizeof(int), st))) return e;
-  if ((e = launch_warps(rc, TLQR_K_CONDENSE, k_condense<T>, P->N, wb.condense, st, w, (int)wb.condense))) return e;
+  if constexpr (MF > 0) {
+    if ((e = launch_groups(rc, TLQR_K_CONDENSE, fx::kf_condense<T, NX, MX>, P->N, G, fx::CondSmem<T, NX, MX>::bytes,
+                           st, w, P->N))) return e;
+  } else if ((e = launch_warps(rc, TLQR_K_CONDENSE, k_condense<T>, P->N, wb.condense, st, w, (int)wb.condense))) {
+    return e;
+  }
   for (const tlqr_round& rd : P->rounds) {
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(rc, TLQR_K_RAKE, k_rake<T>, nr, wb.tau, st, w, rd.rake_begin, nr, (int)wb.tau))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_RAKE, fx::kf_rake<T, NX>, nr, G, fx::TauSmem<T, NX>::bytes, st, w,
+                             rd.rake_begin, nr))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_RAKE, k_rake<T>, nr, wb.tau, st, w, rd.rake_begin, nr, (int)wb.tau))) {
+      return e;
+    }
     if ((e = launch_warps(rc, TLQR_K_ABSORB, k_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
-    if ((e = launch_warps(rc, TLQR_K_COMPRESS, k_compress<T>, nc, wb.compress, st, w, rd.comp_begin, nc, (int)wb.compress))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_COMPRESS, fx::kf_compress<T, NX>, nc, G, fx::CompSmem<T, NX>::bytes, st, w,
+                             rd.comp_begin, nc))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_COMPRESS, k_compress<T>, nc, wb.compress, st, w, rd.comp_begin, nc,
+                                 (int)wb.compress))) {
+      return e;
+    }
   }
   for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
     const int nc = it->comp_end - it->comp_begin;
-    if ((e = launch_warps(rc, TLQR_K_EXPAND, k_expand<T>, nc, wb.tau, st, w, it->comp_begin, nc, (int)wb.tau))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_EXPAND, fx::kf_expand<T, NX>, nc, G, fx::TauSmem<T, NX>::bytes, st, w,
+                             it->comp_begin, nc))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_EXPAND, k_expand<T>, nc, wb.tau, st, w, it->comp_begin, nc, (int)wb.tau))) {
+      return e;
+    }
   }
-  if ((e = launch_warps(rc, TLQR_K_LOCAL_FACTOR, k_local_factor<T>, P->N, wb.local_factor, st, w, (int)wb.local_factor))) return e;
+  if constexpr (MF > 0) {
+    if ((e = launch_groups(rc, TLQR_K_LOCAL_FACTOR, fx::kf_local_factor<T, NX, MX>, P->N, G,
+                           fx::LfSmem<T, NX, MX>::bytes, st, w, P->N))) return e;
+  } else if ((e = launch_warps(rc, TLQR_K_LOCAL_FACTOR, k_local_factor<T>, P->N, wb.local_factor, st, w,
+                               (int)wb.local_factor))) {
+    return e;
+  }
   for (const tlqr_round& rd : P->rounds) {
     const int nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(rc, TLQR_K_COMPOSE_T, k_compose_T<T>, nc, wb.compose_T, st, w, rd.comp_begin, nc, (int)wb.compose_T))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_COMPOSE_T, fx::kf_compose_T<T, NX>, nc, G, fx::ComposeSmem<T, NX>::bytes, st,
+                             w, rd.comp_begin, nc))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_COMPOSE_T, k_compose_T<T>, nc, wb.compose_T, st, w, rd.comp_begin, nc,
+                                 (int)wb.compose_T))) {
+      return e;
+    }
   }
   return cudaSuccess;
 }
 
-template <typename T>
+// Right-hand-side sequence (Alg. 1 steps 4-6).
+template <typename T, int NF, int MF>
 cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const double* r, const double* c,
                       double* x, double* u, double* y, int accumulate, cudaStream_t st) {
   const tlqr_plan_t* P = f->plan;
@@ -343,31 +409,103 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
   p.q = q; p.r = r; p.c = c;
   const Ws<T> w = f->ws<T>(p);
   const WarpBytes wb = warp_bytes(f->opt.n, f->opt.m, sizeof(T));
+  constexpr int NX = NF > 0 ? NF : 4;
+  constexpr int MX = MF > 0 ? MF : 2;
+  constexpr int G = fx::D<T, NX>::G;
   cudaError_t e;
-  if ((e = launch_warps(rc, TLQR_K_AFF_INIT, k_aff_init<T>, P->N, wb.aff_init, st, w, (int)wb.aff_init))) return e;
+  if constexpr (MF > 0) {
+    if ((e = launch_groups(rc, TLQR_K_AFF_INIT, fx::kf_aff_init<T, NX, MX>, P->N, G, 0, st, w, P->N))) return e;
+  } else if ((e = launch_warps(rc, TLQR_K_AFF_INIT, k_aff_init<T>, P->N, wb.aff_init, st, w, (int)wb.aff_init))) {
+    return e;
+  }
   for (const tlqr_round& rd : P->rounds) {
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(rc, TLQR_K_AFF_RAKE, k_aff_rake<T>, nr, wb.vec1, st, w, rd.rake_begin, nr, (int)wb.vec1))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_AFF_RAKE, fx::kf_aff_rake<T, NX>, nr, G, 0, st, w, rd.rake_begin, nr))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_AFF_RAKE, k_aff_rake<T>, nr, wb.vec1, st, w, rd.rake_begin, nr,
+                                 (int)wb.vec1))) {
+      return e;
+    }
     if ((e = launch_warps(rc, TLQR_K_AFF_ABSORB, k_aff_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
-    if ((e = launch_warps(rc, TLQR_K_AFF_COMPRESS, k_aff_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_AFF_COMPRESS, fx::kf_aff_compress<T, NX>, nc, G, 0, st, w, rd.comp_begin,
+                             nc))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_AFF_COMPRESS, k_aff_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc,
+                                 (int)wb.vec1))) {
+      return e;
+    }
   }
   for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
     const int nc = it->comp_end - it->comp_begin;
-    if ((e = launch_warps(rc, TLQR_K_AFF_EXPAND, k_aff_expand<T>, nc, wb.vec1, st, w, it->comp_begin, nc, (int)wb.vec1))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_AFF_EXPAND, fx::kf_aff_expand<T, NX>, nc, G, 0, st, w, it->comp_begin,
+                             nc))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_AFF_EXPAND, k_aff_expand<T>, nc, wb.vec1, st, w, it->comp_begin, nc,
+                                 (int)wb.vec1))) {
+      return e;
+    }
   }
-  if ((e = launch_warps(rc, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w, (int)wb.local_solve))) return e;
+  if constexpr (MF > 0) {
+    if ((e = launch_groups(rc, TLQR_K_LOCAL_SOLVE, fx::kf_local_solve<T, NX, MX>, P->N, G, 0, st, w, P->N))) return e;
+  } else if ((e = launch_warps(rc, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w,
+                               (int)wb.local_solve))) {
+    return e;
+  }
   for (const tlqr_round& rd : P->rounds) {
     const int nc = rd.comp_end - rd.comp_begin;
-    if ((e = launch_warps(rc, TLQR_K_STATE_COMPRESS, k_state_compress<T>, nc, wb.vec1, st, w, rd.comp_begin, nc, (int)wb.vec1))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_STATE_COMPRESS, fx::kf_state_compress<T, NX>, nc, G, 0, st, w,
+                             rd.comp_begin, nc))) return e;
+    } else if ((e = launch_warps(rc, TLQR_K_STATE_COMPRESS, k_state_compress<T>, nc, wb.vec1, st, w, rd.comp_begin,
+                                 nc, (int)wb.vec1))) {
+      return e;
+    }
   }
   for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
     const int nc = it->comp_end - it->comp_begin, nr = it->rake_end - it->rake_begin;
-    if ((e = launch_warps(rc, TLQR_K_STATE_EXPAND, k_state_expand<T>, nc, wb.vec1, st, w, (const int*)f->dp.comp_j,
-                          (const int*)f->dp.comp_i, it->comp_begin, nc, (int)wb.vec1))) return e;
-    if ((e = launch_warps(rc, TLQR_K_STATE_EXPAND, k_state_expand<T>, nr, wb.vec1, st, w, (const int*)f->dp.rake_leaf,
-                          (const int*)f->dp.rake_parent, it->rake_begin, nr, (int)wb.vec1))) return e;
+    const int *cj = f->dp.comp_j, *ci = f->dp.comp_i, *rl = f->dp.rake_leaf, *rp = f->dp.rake_parent;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_STATE_EXPAND, fx::kf_state_expand<T, NX>, nc, G, 0, st, w, cj, ci,
+                             it->comp_begin, nc))) return e;
+      if ((e = launch_groups(rc, TLQR_K_STATE_EXPAND, fx::kf_state_expand<T, NX>, nr, G, 0, st, w, rl, rp,
+                             it->rake_begin, nr))) return e;
+    } else {
+      if ((e = launch_warps(rc, TLQR_K_STATE_EXPAND, k_state_expand<T>, nc, wb.vec1, st, w, cj, ci, it->comp_begin,
+                            nc, (int)wb.vec1))) return e;
+      if ((e = launch_warps(rc, TLQR_K_STATE_EXPAND, k_state_expand<T>, nr, wb.vec1, st, w, rl, rp, it->rake_begin,
+                            nr, (int)wb.vec1))) return e;
+    }
   }
+  if constexpr (MF > 0)
+    return launch_groups(rc, TLQR_K_RECOVER, fx::kf_recover<T, NX, MX>, P->N, G, 0, st, w, x, u, y, accumulate, P->N);
   return launch_warps(rc, TLQR_K_RECOVER, k_recover<T>, P->N, wb.recover, st, w, x, u, y, accumulate, (int)wb.recover);
+}
+
+// Dimension dispatch.  fixed_n: compile-time n of the n x n kernels (0 = run time);
+// fixed_m: compile-time m of the (n, m) kernels for that n (0 = run time).
+#define TLQR_FIXED_CASES(X)                                                     \
+  X(4, 0) X(4, 2) X(6, 0) X(6, 2) X(8, 0) X(8, 2) X(12, 0) X(12, 4) X(16, 0) X(16, 4)
+
+template <typename T>
+cudaError_t dispatch_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cudaStream_t st) {
+#define X(n_, m_) if (f->fixed_n == n_ && f->fixed_m == m_) return run_factor<T, n_, m_>(f, rc, p, st);
+  TLQR_FIXED_CASES(X)
+#undef X
+  return run_factor<T, 0, 0>(f, rc, p, st);
+}
+template <typename T>
+cudaError_t dispatch_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const double* r, const double* c,
+                           double* x, double* u, double* y, int accumulate, cudaStream_t st) {
+#define X(n_, m_) \
+  if (f->fixed_n == n_ && f->fixed_m == m_) return run_solve<T, n_, m_>(f, rc, q, r, c, x, u, y, accumulate, st);
+  TLQR_FIXED_CASES(X)
+#undef X
+  return run_solve<T, 0, 0>(f, rc, q, r, c, x, u, y, accumulate, st);
+}
+
+bool has_fixed_kernels(int n) { return n == 4 || n == 6 || n == 8 || n == 12 || n == 16; }
+bool has_fixed_pair(int n, int m) {
+  return (m == 2 && (n == 4 || n == 6 || n == 8)) || (m == 4 && (n == 12 || n == 16));
 }
 
 cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, const double* x,
@@ -579,6 +717,41 @@ cudaError_t configure_kernels(int n, int m) {
   return e;
 }
 
+template <typename T, int N>
+cudaError_t configure_fixed() {
+  constexpr int gpb = 128 / fx::D<T, N>::G;
+  cudaError_t e = ensure_smem(fx::kf_rake<T, N>, (size_t)fx::TauSmem<T, N>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_expand<T, N>, (size_t)fx::TauSmem<T, N>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_compress<T, N>, (size_t)fx::CompSmem<T, N>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_compose_T<T, N>, (size_t)fx::ComposeSmem<T, N>::bytes * gpb);
+  return e;
+}
+template <typename T, int N, int M>
+cudaError_t configure_fixed_nm() {
+  constexpr int gpb = 128 / fx::D<T, N>::G;
+  cudaError_t e = ensure_smem(fx::kf_condense<T, N, M>, (size_t)fx::CondSmem<T, N, M>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_local_factor<T, N, M>, (size_t)fx::LfSmem<T, N, M>::bytes * gpb);
+  return e;
+}
+template <typename T>
+cudaError_t configure_fixed_pair(int n, int m) {
+#define X(n_, m_) if constexpr (m_ > 0) { if (n == n_ && m == m_) return configure_fixed_nm<T, n_, m_>(); }
+  TLQR_FIXED_CASES(X)
+#undef X
+  return cudaSuccess;
+}
+template <typename T>
+cudaError_t configure_fixed_n(int n) {
+  switch (n) {
+    case 4: return configure_fixed<T, 4>();
+    case 6: return configure_fixed<T, 6>();
+    case 8: return configure_fixed<T, 8>();
+    case 12: return configure_fixed<T, 12>();
+    case 16: return configure_fixed<T, 16>();
+    default: return cudaSuccess;
+  }
+}
+
 // Enqueue the factorisation; with `sync` also wait and report its status.
 int factor_impl(tlqr_factor_t* f, const tlqr_problem* dp, cudaStream_t st, bool sync) {
   f->dprob = *dp;
@@ -586,7 +759,7 @@ int factor_impl(tlqr_factor_t* f, const tlqr_problem* dp, cudaStream_t st, bool 
   tlqr_problem key = *dp;
   key.q = key.r = key.c = nullptr;
   cudaError_t e = run_seq(f, &f->g_factor, problem_key(key), st, [&](Recorder* rc) {
-    return f->ts == 8 ? run_factor<double>(f, rc, *dp, st) : run_factor<float>(f, rc, *dp, st);
+    return f->ts == 8 ? dispatch_factor<double>(f, rc, *dp, st) : dispatch_factor<float>(f, rc, *dp, st);
   });
   if (e) return TLQR_ERR_CUDA;
   f->factored = true;
@@ -604,8 +777,8 @@ cudaError_t solve_impl(tlqr_factor_t* f, const double* q, const double* r, const
     key.push_back(up(p));
   key.push_back((uintptr_t)accumulate);
   return run_seq(f, solve_cache(f, key), key, st, [&](Recorder* rc) {
-    return f->ts == 8 ? run_solve<double>(f, rc, q, r, c, x, u, y, accumulate, st)
-                      : run_solve<float>(f, rc, q, r, c, x, u, y, accumulate, st);
+    return f->ts == 8 ? dispatch_solve<double>(f, rc, q, r, c, x, u, y, accumulate, st)
+                      : dispatch_solve<float>(f, rc, q, r, c, x, u, y, accumulate, st);
   });
 }
 
@@ -663,7 +836,15 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   const WarpBytes wb = warp_bytes(n, m, f->ts);
   const size_t worst = std::max({wb.compress, wb.local_factor, wb.tau, wb.condense});
   if (worst > kSmemBudget) { delete f; return TLQR_ERR_ARG; }
-  if ((f->ts == 8 ? configure_kernels<double>(n, m) : configure_kernels<float>(n, m)) != cudaSuccess) {
+  f->fixed_n = (has_fixed_kernels(n) && !opts->generic_kernels) ? n : 0;
+  // FP64: groups of 8 / 16 lanes for n = 6 / 12 leave lanes idle, which costs FP64 issue slots;
+  // the run-time-n kernels keep all 32 lanes busy and are faster there.
+  if (f->ts == 8 && (n == 6 || n == 12)) f->fixed_n = 0;
+  f->fixed_m = (f->fixed_n && has_fixed_pair(n, m)) ? m : 0;
+  if ((f->ts == 8 ? configure_kernels<double>(n, m) : configure_kernels<float>(n, m)) != cudaSuccess ||
+      (f->ts == 8 ? configure_fixed_n<double>(f->fixed_n) : configure_fixed_n<float>(f->fixed_n)) != cudaSuccess ||
+      (f->ts == 8 ? configure_fixed_pair<double>(f->fixed_n, f->fixed_m)
+                  : configure_fixed_pair<float>(f->fixed_n, f->fixed_m)) != cudaSuccess) {
     delete f;
     return TLQR_ERR_CUDA;
   }

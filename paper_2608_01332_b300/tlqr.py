@@ -40,7 +40,7 @@ class TLQRError(RuntimeError):
 class tlqr_options(ctypes.Structure):
     _fields_ = [("n", _i32), ("m", _i32), ("precision", _i32), ("has_M", _i32), ("has_delta", _i32),
                 ("max_refine", _i32), ("refine_tol", ctypes.c_double), ("use_graphs", _i32),
-                ("reserved", _i32 * 7)]
+                ("generic_kernels", _i32), ("reserved", _i32 * 6)]
 
 
 class tlqr_problem(ctypes.Structure):
@@ -207,8 +207,9 @@ def tlqr_plan_schedule(plan, N: int):
 # ------------------------------------------------------------------ factor / solve
 
 def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
-                 refine_tol=1e-8, use_graphs=True) -> tlqr_options:
+                 refine_tol=1e-8, use_graphs=True, generic_kernels=False) -> tlqr_options:
     o = tlqr_options()
+    o.generic_kernels = int(bool(generic_kernels))
     o.n, o.m, o.precision = int(n), int(m), int(precision)
     o.has_M, o.has_delta = int(bool(has_M)), int(bool(has_delta))
     o.max_refine, o.refine_tol, o.use_graphs = int(max_refine), float(refine_tol), int(bool(use_graphs))

@@ -373,3 +373,20 @@ def test_profiler_times_kernels_inside_graphs():
     assert prof["compress"]["timed"] == prof["compress"]["launches"] > 0
     assert prof["compress"]["ms"] > 0 and prof["rake"]["ms"] > 0
     assert prof["expand"]["timed"] == 0
+
+
+# -------------------------------------------------------------------- kernel families
+
+@pytest.mark.parametrize("n,m", [(4, 2), (6, 2), (8, 3), (12, 4), (16, 4)])
+@pytest.mark.parametrize("generic", [False, True])
+def test_fixed_and_runtime_dimension_kernels(n, m, generic):
+    """The compile-time-n kernels (n = 4, 6, 8, 12, 16) and the run-time-n kernels
+    both match the oracle, in FP64 and in refined mixed precision."""
+    rng = inputs.rng_for(600 + n)
+    p, _ = inputs.permute_labels(inputs.random_recursive(1500, rng), rng)
+    d = inputs.problem_data(p, n, m, rng, delta="subset", delta_value=0.05, delta_fraction=0.3, M_scale=0.2)
+    out = gpu_solve(p, n, m, d, generic_kernels=generic)
+    check_against_oracle(p, n, m, d, out, fwd_tol=1e-8, eta_tol=1e-10, pk_tol=1e-8)
+    outm = gpu_solve(p, n, m, d, precision=MIXED, want_PK=False, generic_kernels=generic)
+    assert outm["info"]["eta"] <= 1e-8
+    check_against_oracle(p, n, m, d, outm, fwd_tol=1e-6, eta_tol=1e-8)
