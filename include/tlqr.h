@@ -240,7 +240,8 @@ enum {
   TLQR_K_CONDENSE = 0, TLQR_K_RAKE, TLQR_K_ABSORB, TLQR_K_COMPRESS, TLQR_K_EXPAND,
   TLQR_K_LOCAL_FACTOR, TLQR_K_COMPOSE_T, TLQR_K_AFF_INIT, TLQR_K_AFF_RAKE, TLQR_K_AFF_ABSORB,
   TLQR_K_AFF_COMPRESS, TLQR_K_AFF_EXPAND, TLQR_K_LOCAL_SOLVE, TLQR_K_STATE_COMPRESS,
-  TLQR_K_STATE_EXPAND, TLQR_K_RECOVER, TLQR_K_RESIDUAL, TLQR_K_EXPORT, TLQR_K_COUNT
+  TLQR_K_STATE_EXPAND, TLQR_K_RECOVER, TLQR_K_RESIDUAL, TLQR_K_EXPORT, TLQR_K_AFF_TAIL,
+  TLQR_K_STATE_TAIL, TLQR_K_FACTOR_TAIL, TLQR_K_COUNT
 };
 
 typedef struct {

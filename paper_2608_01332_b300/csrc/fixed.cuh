@@ -469,34 +469,39 @@ __global__ void kf_compose_T(Ws<T> w, int begin, int count) {
 }
 
 // ---------------------------------------------------------------- vector passes
-// One group per operation; lane r owns entry r of the output vector.
+// One group per operation; lane r owns entry r of the output vector.  Each
+// operation is a device function so that the per-round kernels (one launch per
+// phase) and the tail kernel (all small rounds in one block) share it.
 template <typename T, int N>
 __device__ __forceinline__ void vec_load(T (&v)[N], const T* src) {
 #pragma unroll
   for (int c = 0; c < N; ++c) v[c] = src[c];
 }
 
-// contribution cv_r = T_j^T h_j + z_j  (eq. affine-rake)
+// contribution cv_rr = T_j^T h_j + z_j  (eq. affine-rake)
 template <typename T, int N>
-__global__ void kf_aff_rake(Ws<T> w, int begin, int count) {
-  int op;
-  const Grp g = group_of<T, N>(count, &op);
-  const int rr = begin + op, j = w.rake_leaf[rr], r = g.gl < N ? g.gl : 0;
+__device__ __forceinline__ void aff_rake_op(const Ws<T>& w, int rr, bool valid, int gl) {
+  const int j = w.rake_leaf[rr], r = gl < N ? gl : 0;
   const T* Tj = w.Tm + (size_t)j * N * N;
   T h[N];
   vec_load(h, w.h + (size_t)j * N);
   T s = w.z[(size_t)j * N + r];
 #pragma unroll
   for (int t = 0; t < N; ++t) s = fma(Tj[t * N + r], h[t], s);
-  if (g.valid && g.gl < N) w.cv[(size_t)rr * N + r] = s;
+  if (valid && gl < N) w.cv[(size_t)rr * N + r] = s;
 }
-
+// h_i += sum of the segment's contributions, in sibling order
+template <typename T, int N>
+__device__ __forceinline__ void aff_absorb_op(const Ws<T>& w, int sidx, bool valid, int gl) {
+  const int i = w.seg_parent[sidx], b = w.seg_start[sidx], e = w.seg_start[sidx + 1], r = gl < N ? gl : 0;
+  T acc = w.cv[(size_t)b * N + r];
+  for (int t = b + 1; t < e; ++t) acc += w.cv[(size_t)t * N + r];
+  if (valid && gl < N) w.h[(size_t)i * N + r] += acc;
+}
 // s_j = h_j + z_k ; z_k <- z_j + T_j^T s_j  (eq. affine-compose)
 template <typename T, int N>
-__global__ void kf_aff_compress(Ws<T> w, int begin, int count) {
-  int op;
-  const Grp g = group_of<T, N>(count, &op);
-  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr], r = g.gl < N ? g.gl : 0;
+__device__ __forceinline__ void aff_compress_op(const Ws<T>& w, int rr, bool valid, int gl) {
+  const int j = w.comp_j[rr], k = w.comp_k[rr], r = gl < N ? gl : 0;
   const T* Tj = w.Tm + (size_t)j * N * N;
   T sv[N];
 #pragma unroll
@@ -506,33 +511,27 @@ __global__ void kf_aff_compress(Ws<T> w, int begin, int count) {
   for (int t = 0; t < N; ++t) acc = fma(Tj[t * N + r], sv[t], acc);
   const T sr = w.h[(size_t)j * N + r] + w.z[(size_t)k * N + r];
   __syncwarp();
-  if (g.valid && g.gl < N) {
+  if (valid && gl < N) {
     w.s[(size_t)j * N + r] = sr;
     w.z[(size_t)k * N + r] = acc;
   }
 }
-
 // p_j = Tr_j^T p_k + s_j  (affine expansion)
 template <typename T, int N>
-__global__ void kf_aff_expand(Ws<T> w, int begin, int count) {
-  int op;
-  const Grp g = group_of<T, N>(count, &op);
-  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr], r = g.gl < N ? g.gl : 0;
+__device__ __forceinline__ void aff_expand_op(const Ws<T>& w, int rr, bool valid, int gl) {
+  const int j = w.comp_j[rr], k = w.comp_k[rr], r = gl < N ? gl : 0;
   const T* Trj = w.Tr + (size_t)j * N * N;
   T p[N];
   vec_load(p, w.h + (size_t)k * N);
   T acc = w.s[(size_t)j * N + r];
 #pragma unroll
   for (int t = 0; t < N; ++t) acc = fma(Trj[t * N + r], p[t], acc);
-  if (g.valid && g.gl < N) w.h[(size_t)j * N + r] = acc;
+  if (valid && gl < N) w.h[(size_t)j * N + r] = acc;
 }
-
 // b_k <- Tr_j b_j + b_k  (state-map composition of the offsets)
 template <typename T, int N>
-__global__ void kf_state_compress(Ws<T> w, int begin, int count) {
-  int op;
-  const Grp g = group_of<T, N>(count, &op);
-  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr], r = g.gl < N ? g.gl : 0;
+__device__ __forceinline__ void state_compress_op(const Ws<T>& w, int rr, bool valid, int gl) {
+  const int j = w.comp_j[rr], k = w.comp_k[rr], r = gl < N ? gl : 0;
   const T* Trj = w.Tr + (size_t)j * N * N + r * N;
   T b[N];
   vec_load(b, w.bv + (size_t)j * N);
@@ -540,22 +539,113 @@ __global__ void kf_state_compress(Ws<T> w, int begin, int count) {
 #pragma unroll
   for (int t = 0; t < N; ++t) acc = fma(Trj[t], b[t], acc);
   __syncwarp();
-  if (g.valid && g.gl < N) w.bv[(size_t)k * N + r] = acc;
+  if (valid && gl < N) w.bv[(size_t)k * N + r] = acc;
 }
-
 // x_j = T_j x_i + b_j  (state expansion)
 template <typename T, int N>
-__global__ void kf_state_expand(Ws<T> w, const int* nodes, const int* from, int begin, int count) {
-  int op;
-  const Grp g = group_of<T, N>(count, &op);
-  const int rr = begin + op, j = nodes[rr], i = from[rr], r = g.gl < N ? g.gl : 0;
+__device__ __forceinline__ void state_expand_op(const Ws<T>& w, const int* nodes, const int* from, int rr,
+                                                bool valid, int gl) {
+  const int j = nodes[rr], i = from[rr], r = gl < N ? gl : 0;
   const T* Tj = w.Tm + (size_t)j * N * N + r * N;
   T x[N];
   vec_load(x, w.xs + (size_t)i * N);
   T acc = w.bv[(size_t)j * N + r];
 #pragma unroll
   for (int t = 0; t < N; ++t) acc = fma(Tj[t], x[t], acc);
-  if (g.valid && g.gl < N) w.xs[(size_t)j * N + r] = acc;
+  if (valid && gl < N) w.xs[(size_t)j * N + r] = acc;
+}
+
+template <typename T, int N>
+__global__ void kf_aff_rake(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  aff_rake_op<T, N>(w, begin + op, g.valid, g.gl);
+}
+template <typename T, int N>
+__global__ void kf_aff_compress(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  aff_compress_op<T, N>(w, begin + op, g.valid, g.gl);
+}
+template <typename T, int N>
+__global__ void kf_aff_expand(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  aff_expand_op<T, N>(w, begin + op, g.valid, g.gl);
+}
+template <typename T, int N>
+__global__ void kf_state_compress(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  state_compress_op<T, N>(w, begin + op, g.valid, g.gl);
+}
+template <typename T, int N>
+__global__ void kf_state_expand(Ws<T> w, const int* nodes, const int* from, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  state_expand_op<T, N>(w, nodes, from, begin + op, g.valid, g.gl);
+}
+
+// ---------------------------------------------------------------- tail kernels
+// The late structural rounds hold few operations each; running them as one
+// launch per phase costs a kernel launch per handful of operations.  A tail
+// kernel runs rounds [r0, R) of a pass -- and the matching backward rounds --
+// inside ONE block: its groups stride over each phase's operations and the
+// phases are separated by __syncthreads().  No block waits for another.
+struct RoundDesc { int rb, re, sb, se, cb, ce; };
+
+// Loop `count` operations over the block's groups with uniform trip counts.
+#define TLQR_BLOCK_OPS(count, ...)                                             \
+  do {                                                                         \
+    const int cnt_ = (count);                                                  \
+    for (int base_ = 0; base_ < cnt_; base_ += gpb) {                          \
+      const int o_ = base_ + gid;                                              \
+      const bool valid = o_ < cnt_;                                            \
+      const int op = valid ? o_ : cnt_ - 1;                                    \
+      __VA_ARGS__;                                                             \
+    }                                                                          \
+  } while (0)
+
+// Affine pass tail: forward rounds r0..R-1 (rake, absorb, compress), then the
+// backward rounds R-1..r0 (expand).
+template <typename T, int N>
+__global__ void kf_aff_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
+  constexpr int G = D<T, N>::G;
+  const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
+  for (int r = r0; r < R; ++r) {
+    const RoundDesc d = rounds[r];
+    TLQR_BLOCK_OPS(d.re - d.rb, aff_rake_op<T, N>(w, d.rb + op, valid, gl));
+    __syncthreads();
+    TLQR_BLOCK_OPS(d.se - d.sb, aff_absorb_op<T, N>(w, d.sb + op, valid, gl));
+    __syncthreads();
+    TLQR_BLOCK_OPS(d.ce - d.cb, aff_compress_op<T, N>(w, d.cb + op, valid, gl));
+    __syncthreads();
+  }
+  for (int r = R - 1; r >= r0; --r) {
+    const RoundDesc d = rounds[r];
+    TLQR_BLOCK_OPS(d.ce - d.cb, aff_expand_op<T, N>(w, d.cb + op, valid, gl));
+    __syncthreads();
+  }
+}
+
+// State pass tail: forward compositions r0..R-1, then expansion R-1..r0
+// (compressed centres before the leaves raked in the same round).
+template <typename T, int N>
+__global__ void kf_state_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
+  constexpr int G = D<T, N>::G;
+  const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
+  for (int r = r0; r < R; ++r) {
+    const RoundDesc d = rounds[r];
+    TLQR_BLOCK_OPS(d.ce - d.cb, state_compress_op<T, N>(w, d.cb + op, valid, gl));
+    __syncthreads();
+  }
+  for (int r = R - 1; r >= r0; --r) {
+    const RoundDesc d = rounds[r];
+    TLQR_BLOCK_OPS(d.ce - d.cb, state_expand_op<T, N>(w, w.comp_j, w.comp_i, d.cb + op, valid, gl));
+    __syncthreads();
+    TLQR_BLOCK_OPS(d.re - d.rb, state_expand_op<T, N>(w, w.rake_leaf, w.rake_parent, d.rb + op, valid, gl));
+    __syncthreads();
+  }
 }
 
 }  // namespace fx
@@ -617,9 +707,34 @@ __device__ __forceinline__ void chol_solve_reg(const T (&l)[M][M], T (&b)[M]) {
   }
 }
 
+// Copy COUNT contiguous global elements into shared rows of stride LDS
+// (COLS columns per row), converting S -> T.  Uses 16-byte loads when the
+// block is a whole number of vectors and the rows are unpadded.
+template <typename T, typename S, int ROWS, int COLS, int LDS, int G>
+__device__ __forceinline__ void stage(T* dst, const S* src, int gl) {
+  constexpr int COUNT = ROWS * COLS;
+  constexpr int SW = 16 / (int)sizeof(S);
+  if constexpr (COLS == LDS && COUNT % SW == 0) {
+    using VS = typename Vec<S>::V;
+#pragma unroll
+    for (int v = gl; v < COUNT / SW; v += G) {
+      const VS x = reinterpret_cast<const VS*>(src)[v];
+#pragma unroll
+      for (int i = 0; i < SW; ++i) dst[v * SW + i] = (T)vget<S>(x, i);
+    }
+  } else {
+    gload<T, ROWS, COLS, LDS, G>(dst, src, gl);
+  }
+}
+
+template <typename T, int M> struct MPad { static constexpr int LD = (M + Vec<T>::W - 1) / Vec<T>::W * Vec<T>::W; };
+
 template <typename T, int N, int M>
 struct CondSmem {
-  static constexpr int bytes = ((2 * N * M * (int)sizeof(T) + 15) / 16) * 16;   // B and M blocks
+  static constexpr int MLD = MPad<T, M>::LD;
+  // B, M, B R^{-1}, M R^{-1} (N rows of MLD each), R (M rows of MLD)
+  static constexpr int elems = 4 * N * MLD + M * MLD;
+  static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
 // Condensation eq. (edge-components), U_i <- Q_i, Delta flag.  All groups of a
@@ -628,13 +743,13 @@ struct CondSmem {
 template <typename T, int N, int M>
 __global__ void kf_condense(Ws<T> w, int count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int G = D<T, N>::G, NN = N * N, NM = N * M;
+  constexpr int G = D<T, N>::G, NN = N * N, NM = N * M, MLD = CondSmem<T, N, M>::MLD;
   int i;
   const Grp g = group_of<T, N>(count, &i);
   T* sB = reinterpret_cast<T*>(smem_raw + g.gid * CondSmem<T, N, M>::bytes);
-  T* sM = sB + NM;
+  T *sM = sB + N * MLD, *sBR = sM + N * MLD, *sMR = sBR + N * MLD, *sR = sMR + N * MLD;
   const int gl = g.gl, r = gl < N ? gl : 0;
-  const size_t oi = (size_t)i * NN;
+  const size_t oi = (size_t)i * NN, om = (size_t)i * NM;
   const bool is_root = i == w.root;
   bool dnz = false;
   if (w.has_delta) {
@@ -651,39 +766,52 @@ __global__ void kf_condense(Ws<T> w, int count) {
     for (int e = gl; e < NN; e += G) w.U[oi + e] = (T)w.Q[oi + e];
     if (w.has_delta && gl == 0) w.dflag[i] = dnz ? 1 : 0;
   }
-  const size_t om = (size_t)i * NM;
-#pragma unroll
-  for (int e = gl; e < NM; e += G) sB[e] = (T)w.B[om + e];
-  if (w.has_M) {
-#pragma unroll
-    for (int e = gl; e < NM; e += G) sM[e] = (T)w.M[om + e];
-  }
+  stage<T, double, N, M, MLD, G>(sB, w.B + om, gl);
+  if (w.has_M) stage<T, double, N, M, MLD, G>(sM, w.M + om, gl);
+  stage<T, double, M, M, MLD, G>(sR, w.R + (size_t)i * M * M, gl);
+  __syncwarp();
   T Rl[M][M];
 #pragma unroll
-  for (int a = 0; a < M; ++a)
+  for (int a = 0; a < M; ++a) {
+    T row[M];
+    row_load<T, M>(row, sR + a * MLD);
 #pragma unroll
-    for (int b = 0; b < M; ++b) Rl[a][b] = (T)w.R[(size_t)i * M * M + a * M + b];
+    for (int b = 0; b < M; ++b) Rl[a][b] = row[b];
+  }
   const bool ok = chol_reg<T, M>(Rl);
-  __syncwarp();
-  T br[M], mr[M];
-#pragma unroll
-  for (int a = 0; a < M; ++a) { br[a] = sB[r * M + a]; mr[a] = w.has_M ? sM[r * M + a] : T(0); }
+  T br[M];
+  row_load<T, M>(br, sB + r * MLD);
   chol_solve_reg<T, M>(Rl, br);                 // row r of B R^{-1}
-  if (w.has_M) chol_solve_reg<T, M>(Rl, mr);    // row r of M R^{-1}
-  if (g.valid && !is_root && gl < N) {
+  if (gl < N) row_store<T, M>(sBR + r * MLD, br);
+  if (w.has_M) {
+    T mr[M];
+    row_load<T, M>(mr, sM + r * MLD);
+    chol_solve_reg<T, M>(Rl, mr);               // row r of M R^{-1}
+    if (gl < N) row_store<T, M>(sMR + r * MLD, mr);
+  }
+  __syncwarp();
+  // outputs element by element (coalesced): C = Delta + B R^{-1} B^T, A - B R^{-1} M^T, -M R^{-1} M^T
+  if (g.valid && !is_root) {
 #pragma unroll
-    for (int c = 0; c < N; ++c) {
-      T cb = dnz ? (T)w.Delta[oi + r * N + c] : T(0);
-      T ab = (T)w.A[oi + r * N + c];
-      T pb = T(0);
+    for (int e = gl; e < NN; e += G) {
+      const int a = e / N, c = e - (e / N) * N;
+      T x[M], y[M];
+      row_load<T, M>(x, sBR + a * MLD);
+      row_load<T, M>(y, sB + c * MLD);
+      T cb = dnz ? (T)w.Delta[oi + e] : T(0);
 #pragma unroll
-      for (int a = 0; a < M; ++a) {
-        cb = fma(br[a], sB[c * M + a], cb);
-        if (w.has_M) { ab = fma(-br[a], sM[c * M + a], ab); pb = fma(-mr[a], sM[c * M + a], pb); }
+      for (int b = 0; b < M; ++b) cb = fma(x[b], y[b], cb);
+      w.Ec[oi + e] = cb;
+      T ab = (T)w.A[oi + e], pb = T(0);
+      if (w.has_M) {
+        T mm[M], mr[M];
+        row_load<T, M>(mm, sM + c * MLD);
+        row_load<T, M>(mr, sMR + a * MLD);
+#pragma unroll
+        for (int b = 0; b < M; ++b) { ab = fma(-x[b], mm[b], ab); pb = fma(-mr[b], mm[b], pb); }
       }
-      w.Ec[oi + r * N + c] = cb;
-      w.Ea[oi + r * N + c] = ab;
-      w.Ep[oi + r * N + c] = pb;
+      w.Ea[oi + e] = ab;
+      w.Ep[oi + e] = pb;
     }
   }
   if (!ok && g.valid && !is_root && gl == 0) atomicCAS(w.status, 0, ST_NOT_PD);
@@ -691,9 +819,9 @@ __global__ void kf_condense(Ws<T> w, int count) {
 
 template <typename T, int N, int M>
 struct LfSmem {
-  static constexpr int MAT = D<T, N>::MAT;
-  // P, Finv, A_cl, K (M rows of LD), W B (N x M), B (N x M), bc (LD); then order (N ints)
-  static constexpr int elems = 3 * MAT + M * D<T, N>::LD + 2 * N * M + D<T, N>::LD;
+  static constexpr int MAT = D<T, N>::MAT, LD = D<T, N>::LD, MLD = MPad<T, M>::LD;
+  // P, Finv, A (-> A_cl), Delta, K (M x LD), B, W B, M (N x MLD), G (M x MLD), bc (LD); then order
+  static constexpr int elems = 4 * MAT + M * LD + 3 * N * MLD + M * MLD + LD;
   static constexpr int tbytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
   static constexpr int bytes = tbytes + ((N * 4 + 15) / 16) * 16;
 };
@@ -705,20 +833,25 @@ template <typename T, int N, int M>
 __global__ void kf_local_factor(Ws<T> w, int count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using Dm = D<T, N>;
-  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, NN = N * N, NM = N * M;
+  using L = LfSmem<T, N, M>;
+  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, NN = N * N, NM = N * M, MLD = L::MLD;
   int j;
   const Grp g = group_of<T, N>(count, &j);
-  unsigned char* gbase = smem_raw + g.gid * LfSmem<T, N, M>::bytes;
+  unsigned char* gbase = smem_raw + g.gid * L::bytes;
   T* sm = reinterpret_cast<T*>(gbase);
-  T *sP = sm, *sFi = sm + MAT, *sAc = sm + 2 * MAT, *sK = sm + 3 * MAT, *sWB = sK + M * LD, *sB = sWB + NM,
-    *bc = sB + NM;
-  int* order = reinterpret_cast<int*>(gbase + LfSmem<T, N, M>::tbytes);
+  T *sP = sm, *sFi = sm + MAT, *sA = sm + 2 * MAT, *sD = sm + 3 * MAT, *sK = sm + 4 * MAT, *sB = sK + M * LD,
+    *sWB = sB + N * MLD, *sMm = sWB + N * MLD, *sG = sMm + N * MLD, *bc = sG + M * MLD;
+  int* order = reinterpret_cast<int*>(gbase + L::tbytes);
   const int gl = g.gl, r = gl < N ? gl : 0;
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
   const bool is_root = j == w.root;
-  gload<T, N, N, LD, G>(sP, w.U + oj, gl);
   const bool dnz = w.has_delta && w.dflag[j];
   const bool any_dnz = __any_sync(TLQR_FULL_MASK, dnz);
+  stage<T, T, N, N, LD, G>(sP, w.U + oj, gl);
+  stage<T, double, N, N, LD, G>(sA, w.A + oj, gl);
+  stage<T, double, N, M, MLD, G>(sB, w.B + om, gl);
+  if (w.has_M) stage<T, double, N, M, MLD, G>(sMm, w.M + om, gl);
+  if (dnz) stage<T, double, N, N, LD, G>(sD, w.Delta + oj, gl);
   __syncwarp();
   T wrow[N];
   row_load<T, N>(wrow, sP + r * LD);            // W = P unless Delta_j != 0
@@ -728,8 +861,7 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
     zero(f);
     if (dnz) {
       T dr[N];
-#pragma unroll
-      for (int c = 0; c < N; ++c) dr[c] = (T)w.Delta[oj + r * N + c];
+      row_load<T, N>(dr, sD + r * LD);
       row_mm<T, N, N, LD>(f, dr, sP);           // row r of Delta P
     }
 #pragma unroll
@@ -744,56 +876,59 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
       T pr[N];
       row_load<T, N>(pr, sP + r * LD);
       row_mm<T, N, N, LD>(wrow, pr, sFi);       // row r of W = P F^{-1}
-      if (g.valid && gl < N) {
+      if (g.valid) {
 #pragma unroll
-        for (int c = 0; c < N; ++c) {
-          w.Finv[oj + r * N + c] = sFi[r * LD + c];
-          w.W[oj + r * N + c] = wrow[c];
+        for (int e2 = gl; e2 < NN; e2 += G) {
+          const int a = e2 / N, c = e2 - (e2 / N) * N;
+          w.Finv[oj + e2] = sFi[a * LD + c];
+        }
+        if (gl < N) {
+#pragma unroll
+          for (int c = 0; c < N; ++c) w.W[oj + r * N + c] = wrow[c];
         }
       }
     }
   }
-#pragma unroll
-  for (int e = gl; e < NM; e += G) sB[e] = (T)w.B[om + e];
-  __syncwarp();
+  // row r of W B
   T wb[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) wb[a] = T(0);
+  row_mm<T, N, M, MLD>(wb, wrow, sB);
+  if (gl < N) row_store<T, M>(sWB + r * MLD, wb);
+  __syncwarp();
+  // G = R + B^T (W B): entry (a, b) by lane a*M + b, then factored in every lane
 #pragma unroll
-  for (int t = 0; t < N; ++t)
+  for (int e2 = gl; e2 < M * M; e2 += G) {
+    const int a = e2 / M, b = e2 - (e2 / M) * M;
+    T v = (T)w.R[(size_t)j * M * M + e2];
 #pragma unroll
-    for (int a = 0; a < M; ++a) wb[a] = fma(wrow[t], sB[t * M + a], wb[a]);
-  if (gl < N) {
-#pragma unroll
-    for (int a = 0; a < M; ++a) sWB[r * M + a] = wb[a];
-  }
-#pragma unroll
-  for (int e = gl; e < NN; e += G) {
-    const int a = e / N, c = e - (e / N) * N;
-    sAc[a * LD + c] = (T)w.A[oj + e];
+    for (int t = 0; t < N; ++t) v = fma(sB[t * MLD + a], sWB[t * MLD + b], v);
+    sG[a * MLD + b] = v;
   }
   __syncwarp();
-  // G = R + B^T (W B), factored in every lane of the group
   T Gl[M][M];
 #pragma unroll
-  for (int a = 0; a < M; ++a)
+  for (int a = 0; a < M; ++a) {
+    T row[M];
+    row_load<T, M>(row, sG + a * MLD);
 #pragma unroll
-    for (int b = 0; b < M; ++b) {
-      T v = (T)w.R[(size_t)j * M * M + a * M + b];
-#pragma unroll
-      for (int t = 0; t < N; ++t) v = fma(sB[t * M + a], sWB[t * M + b], v);
-      Gl[a][b] = v;
-    }
+    for (int b = 0; b < M; ++b) Gl[a][b] = row[b];
+  }
   const bool okg = chol_reg<T, M>(Gl);
-  // column r of H = (W B)^T A + M^T; K(:, r) = -G^{-1} H(:, r)
+  // column r of H = (W B)^T A + M^T;  K(:, r) = -G^{-1} H(:, r)
   T hc[M];
+  if (w.has_M) row_load<T, M>(hc, sMm + r * MLD);
+  else {
 #pragma unroll
-  for (int a = 0; a < M; ++a) hc[a] = w.has_M ? (T)w.M[om + r * M + a] : T(0);
+    for (int a = 0; a < M; ++a) hc[a] = T(0);
+  }
 #pragma unroll
   for (int t = 0; t < N; ++t) {
-    const T at = sAc[t * LD + r];
+    const T at = sA[t * LD + r];
+    T wbt[M];
+    row_load<T, M>(wbt, sWB + t * MLD);
 #pragma unroll
-    for (int a = 0; a < M; ++a) hc[a] = fma(sWB[t * M + a], at, hc[a]);
+    for (int a = 0; a < M; ++a) hc[a] = fma(wbt[a], at, hc[a]);
   }
   chol_solve_reg<T, M>(Gl, hc);
   if (gl < N) {
@@ -803,30 +938,36 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
   __syncwarp();
   // row r of A_cl = A + B K
   T ac[N], brow[M];
-  row_load<T, N>(ac, sAc + r * LD);
-#pragma unroll
-  for (int a = 0; a < M; ++a) brow[a] = sB[r * M + a];
+  row_load<T, N>(ac, sA + r * LD);
+  row_load<T, M>(brow, sB + r * MLD);
   row_mm<T, M, N, LD>(ac, brow, sK);
   const bool store = g.valid && !is_root;
-  if (store && gl < N) {
+  if (store) {
 #pragma unroll
-    for (int a = 0; a < M; ++a) w.K[om + a * N + r] = sK[a * LD + r];
-  }
-  if (store && gl == 0) {
+    for (int e2 = gl; e2 < M * N; e2 += G) {
+      const int a = e2 / N, c = e2 - (e2 / N) * N;
+      w.K[om + e2] = sK[a * LD + c];
+    }
 #pragma unroll
-    for (int a = 0; a < M; ++a)
+    for (int e2 = gl; e2 < M * M; e2 += G) {
+      const int a = e2 / M, b = e2 - (e2 / M) * M;
+      T v = T(0);
 #pragma unroll
-      for (int b = 0; b < M; ++b) w.LG[(size_t)j * M * M + a * M + b] = Gl[a][b];
+      for (int aa = 0; aa < M; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < M; ++bb) v = (aa == a && bb == b) ? Gl[aa][bb] : v;
+      w.LG[(size_t)j * M * M + e2] = v;
+    }
   }
   __syncwarp();
-  if (gl < N) row_store<T, N>(sAc + r * LD, ac);
+  if (gl < N) row_store<T, N>(sA + r * LD, ac);
   __syncwarp();
   T t[N];
   if (any_dnz) {
     T fr[N];
     row_load<T, N>(fr, sFi + r * LD);
     zero(t);
-    row_mm<T, N, N, LD>(t, fr, sAc);           // T = F^{-1} A_cl
+    row_mm<T, N, N, LD>(t, fr, sA);             // T = F^{-1} A_cl
   }
   if (store && gl < N) {
 #pragma unroll
@@ -838,110 +979,164 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
   }
 }
 
+template <typename T, int N, int M>
+struct AiSmem {
+  static constexpr int LD = D<T, N>::LD, MLD = MPad<T, M>::LD;
+  // W, A (N x LD), K (M x LD), B (N x MLD), c, w (LD), r (MLD)
+  static constexpr int elems = 2 * N * LD + M * LD + N * MLD + 2 * LD + MLD;
+  static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
+};
+
 // Affine edge data eq. (affine-edge): h = q, z = K^T (r + B^T w) + A^T w, w = W c.
 template <typename T, int N, int M>
 __global__ void kf_aff_init(Ws<T> w, int count) {
-  constexpr int G = D<T, N>::G, NN = N * N, NM = N * M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using A_ = AiSmem<T, N, M>;
+  constexpr int G = D<T, N>::G, LD = A_::LD, MLD = A_::MLD, NN = N * N, NM = N * M;
   int j;
   const Grp g = group_of<T, N>(count, &j);
+  T* sW = reinterpret_cast<T*>(smem_raw + g.gid * A_::bytes);
+  T *sA = sW + N * LD, *sK = sA + N * LD, *sB = sK + M * LD, *vc = sB + N * MLD, *vw = vc + LD, *vr = vw + LD;
   const int gl = g.gl, r = gl < N ? gl : 0;
   const bool is_root = j == w.root;
   if (g.valid && gl < N) w.h[(size_t)j * N + r] = (T)w.q[(size_t)j * N + r];
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
   const bool dnz = w.has_delta && w.dflag[j];
-  const T* Wm = dnz ? w.W + oj : w.U + oj;
-  T wr = T(0);                                  // w = W c, W symmetric: columns, coalesced across lanes
+  stage<T, T, N, N, LD, G>(sW, dnz ? w.W + oj : w.U + oj, gl);
+  stage<T, double, N, N, LD, G>(sA, w.A + oj, gl);
+  stage<T, T, M, N, LD, G>(sK, w.K + om, gl);
+  stage<T, double, N, M, MLD, G>(sB, w.B + om, gl);
+  if (gl < N) vc[gl] = (T)w.c[(size_t)j * N + gl];
+  if (gl < M) vr[gl] = (T)w.r[(size_t)j * M + gl];
+  if (gl >= N && gl < LD) vc[gl] = T(0);
+  __syncwarp();
+  T row[N], cv[N];
+  row_load<T, N>(row, sW + r * LD);
+  row_load<T, N>(cv, vc);
+  T wr = T(0);
 #pragma unroll
-  for (int t = 0; t < N; ++t) wr = fma(Wm[t * N + r], (T)w.c[(size_t)j * N + t], wr);
-  T wv[N];
-  gather_vec<T, N, G>(wv, wr);
-  T v[M];
-#pragma unroll
-  for (int a = 0; a < M; ++a) v[a] = (T)w.r[(size_t)j * M + a];
-#pragma unroll
-  for (int t = 0; t < N; ++t)
-#pragma unroll
-    for (int a = 0; a < M; ++a) v[a] = fma((T)w.B[om + t * M + a], wv[t], v[a]);
+  for (int t = 0; t < N; ++t) wr = fma(row[t], cv[t], wr);     // w = W c
+  if (gl < N) vw[gl] = wr;
+  __syncwarp();
+  T wv[N], v[M];
+  row_load<T, N>(wv, vw);
+  row_load<T, M>(v, vr);
+  row_mm<T, N, M, MLD>(v, wv, sB);              // v = r + B^T w
   T z = T(0);
 #pragma unroll
-  for (int a = 0; a < M; ++a) z = fma(w.K[om + a * N + r], v[a], z);
+  for (int a = 0; a < M; ++a) z = fma(sK[a * LD + r], v[a], z);
 #pragma unroll
-  for (int t = 0; t < N; ++t) z = fma((T)w.A[oj + t * N + r], wv[t], z);
+  for (int t = 0; t < N; ++t) z = fma(sA[t * LD + r], wv[t], z);
   if (g.valid && !is_root && gl < N) w.z[(size_t)j * N + r] = z;
 }
+
+template <typename T, int N, int M>
+struct LsSmem {
+  static constexpr int LD = D<T, N>::LD, MLD = MPad<T, M>::LD;
+  // W, Delta, Finv (N x LD), B (N x MLD), LG (M x MLD), p, f, g, t (LD), r (MLD)
+  static constexpr int elems = 3 * N * LD + N * MLD + M * MLD + 4 * LD + MLD;
+  static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
+};
 
 // Local affine solve eq. (local-affine-solve) and the root state eq. (xroot).
 template <typename T, int N, int M>
 __global__ void kf_local_solve(Ws<T> w, int count) {
-  constexpr int G = D<T, N>::G, NN = N * N, NM = N * M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using L = LsSmem<T, N, M>;
+  constexpr int G = D<T, N>::G, LD = L::LD, MLD = L::MLD, NN = N * N, NM = N * M;
   int j;
   const Grp g = group_of<T, N>(count, &j);
+  T* sW = reinterpret_cast<T*>(smem_raw + g.gid * L::bytes);
+  T *sD = sW + N * LD, *sFi = sD + N * LD, *sB = sFi + N * LD, *sL = sB + N * MLD, *vp = sL + M * MLD,
+    *vf = vp + LD, *vg = vf + LD, *vt = vg + LD, *vr = vt + LD;
   const int gl = g.gl, r = gl < N ? gl : 0;
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
   const bool dnz = w.has_delta && w.dflag[j];
   const bool is_root = j == w.root;
+  stage<T, T, N, N, LD, G>(sW, dnz ? w.W + oj : w.U + oj, gl);
+  stage<T, double, N, M, MLD, G>(sB, w.B + om, gl);
+  if (!is_root) stage<T, T, M, M, MLD, G>(sL, w.LG + (size_t)j * M * M, gl);
+  if (dnz) {
+    stage<T, double, N, N, LD, G>(sD, w.Delta + oj, gl);
+    stage<T, T, N, N, LD, G>(sFi, w.Finv + oj, gl);
+  }
+  if (gl < LD) vp[gl] = gl < N ? w.h[(size_t)j * N + gl] : T(0);
+  if (gl < M) vr[gl] = (T)w.r[(size_t)j * M + gl];
+  __syncwarp();
   T p[N];
-#pragma unroll
-  for (int t = 0; t < N; ++t) p[t] = w.h[(size_t)j * N + t];
+  row_load<T, N>(p, vp);
   T pr = p[0];
 #pragma unroll
   for (int t = 0; t < N; ++t) pr = (t == r) ? p[t] : pr;
   T fr = -(T)w.c[(size_t)j * N + r];
   if (dnz) {
+    T dr[N];
+    row_load<T, N>(dr, sD + r * LD);
 #pragma unroll
-    for (int t = 0; t < N; ++t) fr = fma((T)w.Delta[oj + t * N + r], p[t], fr);   // Delta symmetric
+    for (int t = 0; t < N; ++t) fr = fma(dr[t], p[t], fr);   // f = Delta p - c
   }
+  if (gl < LD) vf[gl] = gl < N ? fr : T(0);
+  __syncwarp();
   T f[N];
-  gather_vec<T, N, G>(f, fr);                   // f = Delta p - c
-  // root: x = -F^{-1} f
+  row_load<T, N>(f, vf);
+  // root: x = -F^{-1} f ; others: g = p - W f
   T xr = -fr;
   if (dnz) {
+    T fi[N];
+    row_load<T, N>(fi, sFi + r * LD);
     xr = T(0);
 #pragma unroll
-    for (int t = 0; t < N; ++t) xr = fma(-w.Finv[oj + r * N + t], f[t], xr);
+    for (int t = 0; t < N; ++t) xr = fma(-fi[t], f[t], xr);
   }
-  // g = p - W f
-  const T* Wm = dnz ? w.W + oj : w.U + oj;
+  T wrow[N];
+  row_load<T, N>(wrow, sW + r * LD);
   T gr = pr;
 #pragma unroll
-  for (int t = 0; t < N; ++t) gr = fma(-Wm[t * N + r], f[t], gr);               // W symmetric
-  T gv[N];
-  gather_vec<T, N, G>(gv, gr);
-  // k = -G^{-1}(r + B^T g)
-  T k[M];
-#pragma unroll
-  for (int a = 0; a < M; ++a) k[a] = (T)w.r[(size_t)j * M + a];
-#pragma unroll
-  for (int t = 0; t < N; ++t)
-#pragma unroll
-    for (int a = 0; a < M; ++a) k[a] = fma((T)w.B[om + t * M + a], gv[t], k[a]);
+  for (int t = 0; t < N; ++t) gr = fma(-wrow[t], f[t], gr);
+  if (gl < LD) vg[gl] = gl < N ? gr : T(0);
+  __syncwarp();
+  // k = -G^{-1}(r + B^T g) (every lane)
+  T gv[N], k[M];
+  row_load<T, N>(gv, vg);
+  row_load<T, M>(k, vr);
+  row_mm<T, N, M, MLD>(k, gv, sB);
   T Lg[M][M];
 #pragma unroll
-  for (int a = 0; a < M; ++a)
+  for (int a = 0; a < M; ++a) {
+    T row[M];
+    row_load<T, M>(row, sL + a * MLD);
 #pragma unroll
-    for (int b = 0; b < M; ++b) Lg[a][b] = is_root ? ((a == b) ? T(1) : T(0)) : w.LG[(size_t)j * M * M + a * M + b];
+    for (int b = 0; b < M; ++b) Lg[a][b] = is_root ? ((a == b) ? T(1) : T(0)) : row[b];
+  }
   chol_solve_reg<T, M>(Lg, k);
 #pragma unroll
   for (int a = 0; a < M; ++a) k[a] = -k[a];
   // b = F^{-1}(B k - f)
+  T brow[M];
+  row_load<T, M>(brow, sB + r * MLD);
   T tr = -fr;
 #pragma unroll
-  for (int a = 0; a < M; ++a) tr = fma((T)w.B[om + r * M + a], k[a], tr);
-  T tv[N];
-  gather_vec<T, N, G>(tv, tr);
+  for (int a = 0; a < M; ++a) tr = fma(brow[a], k[a], tr);
+  if (gl < LD) vt[gl] = gl < N ? tr : T(0);
+  __syncwarp();
   T b = tr;
   if (dnz) {
+    T tv[N], fi[N];
+    row_load<T, N>(tv, vt);
+    row_load<T, N>(fi, sFi + r * LD);
     b = T(0);
 #pragma unroll
-    for (int t = 0; t < N; ++t) b = fma(w.Finv[oj + r * N + t], tv[t], b);
+    for (int t = 0; t < N; ++t) b = fma(fi[t], tv[t], b);
   }
   if (g.valid) {
     if (is_root) {
       if (gl < N) w.xs[(size_t)j * N + r] = xr;
     } else {
-      if (gl == 0) {
+      if (gl < M) {
+        T kk = k[0];
 #pragma unroll
-        for (int a = 0; a < M; ++a) w.kv[(size_t)j * M + a] = k[a];
+        for (int a = 0; a < M; ++a) kk = (a == gl) ? k[a] : kk;
+        w.kv[(size_t)j * M + gl] = kk;
       }
       if (gl < N) w.bv[(size_t)j * N + r] = b;
     }

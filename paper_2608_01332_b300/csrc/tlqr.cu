@@ -34,6 +34,8 @@ using namespace tlqr;
 namespace {
 
 constexpr int kMaxWarpsPerBlock = 8;
+constexpr int kTailOps = 512;        // per-phase operation count below which rounds join the tail kernel
+constexpr int kTailThreads = 1024;
 constexpr size_t kSmemBudget = 200 * 1024;
 
 inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -226,6 +228,8 @@ struct tlqr_factor_t {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int fixed_n = 0;                 // n of the fixed-dimension kernels in use (0 = run-time n)
   int fixed_m = 0;                 // m of the fixed (n, m) kernels in use (0 = run-time m)
+  fx::RoundDesc* d_rounds = nullptr;  // device copy of the plan's rounds
+  int tail_r0 = 0;                 // first round handled by the single-block tail kernels
 
   template <typename T>
   Ws<T> ws(const tlqr_problem& p) const {
@@ -308,6 +312,23 @@ int upload_plan(tlqr_factor_t* f) {
   up(P->parent, &f->dp.parent);
   up(P->child_start, &f->dp.child_start);
   up(P->child_list, &f->dp.child_list);
+  {
+    std::vector<int32_t> rd;
+    for (const tlqr_round& r : P->rounds)
+      rd.insert(rd.end(), {r.rake_begin, r.rake_end, r.seg_begin, r.seg_end, r.comp_begin, r.comp_end});
+    int* d = nullptr;
+    up(rd, &d);
+    f->d_rounds = reinterpret_cast<fx::RoundDesc*>(d);
+  }
+  // tail: the longest suffix of rounds whose phases each hold at most kTailOps operations
+  const int R = (int)P->rounds.size();
+  f->tail_r0 = R;
+  while (f->tail_r0 > 0) {
+    const tlqr_round& r = P->rounds[f->tail_r0 - 1];
+    const int mx = std::max({r.rake_end - r.rake_begin, r.seg_end - r.seg_begin, r.comp_end - r.comp_begin});
+    if (mx > kTailOps) break;
+    --f->tail_r0;
+  }
   if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? TLQR_ERR_OOM : TLQR_ERR_CUDA;
   return TLQR_OK;
 }
@@ -333,6 +354,19 @@ cudaError_t launch_groups(Recorder* rc, int kind, Kernel kernel, int count, int 
   cudaError_t e = cudaGetLastError();
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[kind]++; rc->units[kind] += count; }
+  return e;
+}
+
+// One block of kTailThreads threads runs the tail rounds of a pass.
+template <typename Kernel, typename... Args>
+cudaError_t launch_tail(Recorder* rc, int kind, Kernel kernel, cudaStream_t st, Args... args) {
+  const bool timed = rc && (rc->mask >> kind) & 1u;
+  EvPair ev{kind, nullptr, nullptr};
+  if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
+  kernel<<<1, kTailThreads, 0, st>>>(args...);
+  cudaError_t e = cudaGetLastError();
+  if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
+  if (rc) { rc->launches[kind]++; rc->units[kind] += 1; }
   return e;
 }
 
@@ -414,11 +448,14 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
   constexpr int G = fx::D<T, NX>::G;
   cudaError_t e;
   if constexpr (MF > 0) {
-    if ((e = launch_groups(rc, TLQR_K_AFF_INIT, fx::kf_aff_init<T, NX, MX>, P->N, G, 0, st, w, P->N))) return e;
+    if ((e = launch_groups(rc, TLQR_K_AFF_INIT, fx::kf_aff_init<T, NX, MX>, P->N, G, fx::AiSmem<T, NX, MX>::bytes, st, w, P->N))) return e;
   } else if ((e = launch_warps(rc, TLQR_K_AFF_INIT, k_aff_init<T>, P->N, wb.aff_init, st, w, (int)wb.aff_init))) {
     return e;
   }
-  for (const tlqr_round& rd : P->rounds) {
+  const int R = (int)P->rounds.size();
+  const int r_tail = NF > 0 ? f->tail_r0 : R;     // rounds [r_tail, R) run in the tail kernel
+  for (int ri = 0; ri < r_tail; ++ri) {
+    const tlqr_round& rd = P->rounds[ri];
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
     if constexpr (NF > 0) {
       if ((e = launch_groups(rc, TLQR_K_AFF_RAKE, fx::kf_aff_rake<T, NX>, nr, G, 0, st, w, rd.rake_begin, nr))) return e;
@@ -435,7 +472,12 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
       return e;
     }
   }
-  for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
+  if constexpr (NF > 0) {
+    if (r_tail < R && (e = launch_tail(rc, TLQR_K_AFF_TAIL, fx::kf_aff_tail<T, NX>, st, w, f->d_rounds, r_tail, R)))
+      return e;
+  }
+  for (int ri = r_tail - 1; ri >= 0; --ri) {
+    const tlqr_round* it = &P->rounds[ri];
     const int nc = it->comp_end - it->comp_begin;
     if constexpr (NF > 0) {
       if ((e = launch_groups(rc, TLQR_K_AFF_EXPAND, fx::kf_aff_expand<T, NX>, nc, G, 0, st, w, it->comp_begin,
@@ -446,12 +488,13 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
     }
   }
   if constexpr (MF > 0) {
-    if ((e = launch_groups(rc, TLQR_K_LOCAL_SOLVE, fx::kf_local_solve<T, NX, MX>, P->N, G, 0, st, w, P->N))) return e;
+    if ((e = launch_groups(rc, TLQR_K_LOCAL_SOLVE, fx::kf_local_solve<T, NX, MX>, P->N, G, fx::LsSmem<T, NX, MX>::bytes, st, w, P->N))) return e;
   } else if ((e = launch_warps(rc, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w,
                                (int)wb.local_solve))) {
     return e;
   }
-  for (const tlqr_round& rd : P->rounds) {
+  for (int ri = 0; ri < r_tail; ++ri) {
+    const tlqr_round& rd = P->rounds[ri];
     const int nc = rd.comp_end - rd.comp_begin;
     if constexpr (NF > 0) {
       if ((e = launch_groups(rc, TLQR_K_STATE_COMPRESS, fx::kf_state_compress<T, NX>, nc, G, 0, st, w,
@@ -461,7 +504,13 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
       return e;
     }
   }
-  for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
+  if constexpr (NF > 0) {
+    if (r_tail < R &&
+        (e = launch_tail(rc, TLQR_K_STATE_TAIL, fx::kf_state_tail<T, NX>, st, w, f->d_rounds, r_tail, R)))
+      return e;
+  }
+  for (int ri = r_tail - 1; ri >= 0; --ri) {
+    const tlqr_round* it = &P->rounds[ri];
     const int nc = it->comp_end - it->comp_begin, nr = it->rake_end - it->rake_begin;
     const int *cj = f->dp.comp_j, *ci = f->dp.comp_i, *rl = f->dp.rake_leaf, *rp = f->dp.rake_parent;
     if constexpr (NF > 0) {
@@ -508,8 +557,9 @@ bool has_fixed_pair(int n, int m) {
   return (m == 2 && (n == 4 || n == 6 || n == 8)) || (m == 4 && (n == 12 || n == 16));
 }
 
+// ff = 1: float-float kernel on the FP32 pipe (refinement); ff = 0: plain FP64 kernel.
 cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, const double* x,
-                         const double* u, const double* y, int with_knorm, cudaStream_t st) {
+                         const double* u, const double* y, int with_knorm, cudaStream_t st, int ff = 0) {
   ResidualArgs a{};
   const tlqr_plan_t* P = f->plan;
   a.N = P->N; a.n = f->opt.n; a.m = f->opt.m; a.root = P->root; a.with_knorm = with_knorm;
@@ -524,8 +574,13 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   const size_t rows = (size_t)P->N * (2 * f->opt.n + f->opt.m);
   const int threads = 256;
   const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 16);
-  k_residual<<<blocks, threads, 0, st>>>(a);
+  const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
+  EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr};
+  if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
+  if (ff) k_residual_ff<<<blocks, threads, 0, st>>>(a);
+  else k_residual<<<blocks, threads, 0, st>>>(a);
   if ((e = cudaGetLastError())) return e;
+  if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[TLQR_K_RESIDUAL]++; rc->units[TLQR_K_RESIDUAL] += P->N; }
   if ((e = cudaMemcpyAsync(f->h_maxes, f->maxes, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st))) return e;
   return cudaMemcpyAsync(f->h_status, f->status, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -731,6 +786,8 @@ cudaError_t configure_fixed_nm() {
   constexpr int gpb = 128 / fx::D<T, N>::G;
   cudaError_t e = ensure_smem(fx::kf_condense<T, N, M>, (size_t)fx::CondSmem<T, N, M>::bytes * gpb);
   if (!e) e = ensure_smem(fx::kf_local_factor<T, N, M>, (size_t)fx::LfSmem<T, N, M>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_aff_init<T, N, M>, (size_t)fx::AiSmem<T, N, M>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_local_solve<T, N, M>, (size_t)fx::LsSmem<T, N, M>::bytes * gpb);
   return e;
 }
 template <typename T>
@@ -788,7 +845,7 @@ cudaError_t residual_impl(tlqr_factor_t* f, const tlqr_problem& p, const double*
   for (const void* v : {(const void*)x, (const void*)u, (const void*)y}) key.push_back(up(v));
   key.push_back((uintptr_t)with_knorm);
   return run_seq(f, &f->g_resid[with_knorm ? 1 : 0], key, st,
-                 [&](Recorder* rc) { return run_residual(f, rc, p, x, u, y, with_knorm, st); });
+                 [&](Recorder* rc) { return run_residual(f, rc, p, x, u, y, with_knorm, st, 1); });
 }
 
 }  // namespace

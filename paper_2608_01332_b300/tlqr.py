@@ -76,7 +76,7 @@ EXPORTS = ["tlqr_plan_create", "tlqr_plan_destroy", "tlqr_plan_stats", "tlqr_pla
 
 KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
                 "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
-                "state_expand", "recover", "residual", "export"]
+                "state_expand", "recover", "residual", "export", "aff_tail", "state_tail", "factor_tail"]
 
 
 def lib():

@@ -298,6 +298,9 @@ def test_mixed_refined(name):
     out = gpu_solve(w.parent, w.n, w.m, w.data, precision=MIXED, want_PK=False)
     assert out["info"]["eta"] <= 1e-8
     fe, eta = check_against_oracle(w.parent, w.n, w.m, w.data, out, fwd_tol=1e-6, eta_tol=1e-8)
+    # the refinement's residual runs in float-float on the FP32 pipe; its eta for the returned
+    # solution must agree with the oracle's FP64 eta to ~1e-14 of the residual's scale
+    assert abs(out["info"]["eta"] - eta) <= 1e-13
 
 
 # -------------------------------------------------------------------- errors
