@@ -344,17 +344,13 @@ struct CompSmem {
 };
 
 template <typename T, int N>
-__global__ void kf_compress(Ws<T> w, int begin, int count) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g, T* sm) {
   using Dm = D<T, N>;
   constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, LD2 = CompSmem<T, N>::LD2, NN = N * N;
-  int op;
-  const Grp g = group_of<T, N>(count, &op);
-  T* sm = reinterpret_cast<T*>(smem_raw + g.gid * CompSmem<T, N>::bytes);
   T *sPt = sm, *sAl = sm + MAT, *sCl = sm + 2 * MAT, *sAr = sm + 3 * MAT, *sY = sm + 4 * MAT,
     *bc = sm + 4 * MAT + N * LD2;
   int* order = reinterpret_cast<int*>(bc + LD2);
-  const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr];
+  const int j = w.comp_j[rr], k = w.comp_k[rr];
   const size_t oj = (size_t)j * NN, ok_ = (size_t)k * NN;
   const int gl = g.gl, r = gl < N ? gl : 0;
   // stage; P~ = P_r + U_j
@@ -432,7 +428,18 @@ __global__ void kf_compress(Ws<T> w, int begin, int count) {
       w.Ep[ok_ + r * N + c] = pn[c];
     }
   }
-  if (!okf && g.valid && gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
+  __syncwarp();
+  return okf;
+}
+
+template <typename T, int N>
+__global__ void kf_compress(Ws<T> w, int begin, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  T* sm = reinterpret_cast<T*>(smem_raw + g.gid * CompSmem<T, N>::bytes);
+  const bool okf = compress_op<T, N>(w, begin + op, g, sm);
+  if (!okf && g.valid && g.gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
 }
 
 // ---------------------------------------------------------------- composite transitions

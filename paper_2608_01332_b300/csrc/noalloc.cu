@@ -115,7 +115,7 @@ extern "C" int tlqr_kkt_residual_noalloc(const tlqr_plan_t* plan, int32_t n, int
   a.maxes = d_maxes;
   const size_t rows = N * (2 * (size_t)n + (size_t)m);
   const int threads = 256;
-  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 16);
+  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 8);
   tlqr::k_residual<<<blocks, threads, 0, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return TLQR_ERR_CUDA;
   unsigned long long hm[4] = {0, 0, 0, 0};

@@ -36,6 +36,33 @@ __device__ __forceinline__ void warp_max_to(unsigned long long* dst, double v) {
   if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(dst, (unsigned long long)__double_as_longlong(v));
 }
 
+// Block-wide maximum of nonnegative 64-bit keys, one atomicMax per block.
+// Every thread of the block must call it (it synchronises the block).
+__device__ __forceinline__ void block_maxbits_to(unsigned long long* dst, unsigned long long v) {
+  __shared__ unsigned long long red[32];
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? red[lane] : 0ull;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+      v = o > v ? o : v;
+    }
+    if (lane == 0 && v) atomicMax(dst, v);
+  }
+}
+__device__ __forceinline__ unsigned long long dbits_abs(double v) {
+  return isnan(v) ? 0x7ff8000000000000ull : (unsigned long long)__double_as_longlong(fabs(v));
+}
+
 __global__ void k_residual(ResidualArgs a) {
   const int n = a.n, m = a.m;
   const size_t nn = (size_t)n * n, nm = (size_t)n * m;
@@ -111,10 +138,10 @@ __global__ void k_residual(ResidualArgs a) {
       kmax = fmax(kmax, rs);
     }
   }
-  warp_max_to(a.maxes + 0, rmax);
-  warp_max_to(a.maxes + 1, zmax);
-  warp_max_to(a.maxes + 2, bmax);
-  if (ks) warp_max_to(a.maxes + 3, kmax);
+  block_maxbits_to(a.maxes + 0, dbits_abs(rmax));
+  block_maxbits_to(a.maxes + 1, dbits_abs(zmax));
+  block_maxbits_to(a.maxes + 2, dbits_abs(bmax));
+  if (ks) block_maxbits_to(a.maxes + 3, dbits_abs(kmax));
 }
 
 }  // namespace tlqr
@@ -152,11 +179,8 @@ __device__ __forceinline__ void dsplit(double a, float& hi, float& lo) {
 
 struct FF { float h, l; };
 
-// acc += a * x
-__device__ __forceinline__ void ff_fma(FF& acc, double a, double x) {
-  float ah, al, xh, xl;
-  dsplit(a, ah, al);
-  dsplit(x, xh, xl);
+// acc += (ah + al) * (xh + xl), keeping the rounding error of ah*xh exactly
+__device__ __forceinline__ void ff_fma2(FF& acc, float ah, float al, float xh, float xl) {
   const float p = ah * xh;
   float pe = fmaf(ah, xh, -p);
   pe = fmaf(ah, xl, pe);
@@ -167,7 +191,7 @@ __device__ __forceinline__ void ff_fma(FF& acc, double a, double x) {
   acc.l += err + pe;
   acc.h = s;
 }
-// acc += a
+// acc += a (FP64 constant, split here)
 __device__ __forceinline__ void ff_add(FF& acc, double a) {
   float ah, al;
   dsplit(a, ah, al);
@@ -177,17 +201,19 @@ __device__ __forceinline__ void ff_add(FF& acc, double a) {
   acc.l += err + al;
   acc.h = s;
 }
-__device__ __forceinline__ double ff_value(const FF& v) { return (double)v.h + (double)v.l; }
-__device__ __forceinline__ float absf_of(double a) {
-  float h, l;
-  dsplit(a, h, l);
-  return fabsf(h);
+// acc += (h + l) for an already split operand
+__device__ __forceinline__ void ff_add2(FF& acc, float h, float l) {
+  const float s = acc.h + h;
+  const float bb = s - acc.h;
+  const float err = (acc.h - (s - bb)) + (h - bb);
+  acc.l += err + l;
+  acc.h = s;
 }
+__device__ __forceinline__ double ff_value(const FF& v) { return (double)v.h + (double)v.l; }
 // |v| as ordered bits (integer max), NaN sorts above +inf
 __device__ __forceinline__ unsigned long long abits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
-
 __device__ __forceinline__ void warp_maxbits_to(unsigned long long* dst, unsigned long long v) {
 #pragma unroll
   for (int off = 16; off; off >>= 1) {
@@ -197,102 +223,164 @@ __device__ __forceinline__ void warp_maxbits_to(unsigned long long* dst, unsigne
   if ((threadIdx.x & 31) == 0 && v) atomicMax(dst, v);
 }
 
-__global__ void k_residual_ff(ResidualArgs a) {
+// Split FP64 arrays into (hi, lo) FP32 pairs; up to 9 arrays in one launch.
+// Optionally folds |.| maxima of the arrays into maxes[slot] (slot < 0: none).
+struct SplitList {
+  int count;
+  const double* src[9];
+  float *hi[9], *lo[9];
+  size_t len[9];
+  int slot[9];
+  unsigned long long* maxes;
+};
+
+__global__ void k_split_ff(SplitList L) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int a = 0; a < L.count; ++a) {
+    unsigned long long mx = 0;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < L.len[a]; t += stride) {
+      const double v = L.src[a][t];
+      if (L.hi[a]) {
+        float h, l;
+        dsplit(v, h, l);
+        L.hi[a][t] = h;
+        L.lo[a][t] = l;
+      }
+      const unsigned long long b = abits(v);
+      mx = b > mx ? b : mx;
+    }
+    if (L.slot[a] >= 0) block_maxbits_to(L.maxes + L.slot[a], mx);
+  }
+}
+
+// Pre-split vectors of the float-float residual (x, u, y as (hi, lo) FP32 pairs).
+struct FFArgs {
+  const float *xh, *xl, *uh, *ul, *yh, *yl;
+};
+
+// acc += a * (xh + xl) with the FP64 matrix entry a split on the fly; returns |a_hi|
+__device__ __forceinline__ float ff_fma_d(FF& acc, double a, float xh, float xl) {
+  float ah, al;
+  dsplit(a, ah, al);
+  ff_fma2(acc, ah, al, xh, xl);
+  return fabsf(ah);
+}
+
+// Residual rows of eq. (kkt) in float-float arithmetic: matrix entries (FP64,
+// read once per use) are split on the fly, the vectors x, u, y come pre-split.
+// ||z|| and ||b|| maxima are formed by the split pass; this kernel adds ||res||
+// and (optionally) the FP32 row sums of ||K||.
+__global__ void k_residual_ff(ResidualArgs a, FFArgs f) {
   const int n = a.n, m = a.m;
   const size_t nn = (size_t)n * n, nm = (size_t)n * m;
   const size_t rows_x = (size_t)a.N * n, rows_u = (size_t)a.N * m, total = 2 * rows_x + rows_u;
-  unsigned long long rmax = 0, zmax = 0, bmax = 0;
+  unsigned long long rmax = 0;
   float kmax = 0.f;
   const bool ks = a.with_knorm;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     double out;
+    float rs = 0.f;
     if (t < rows_x) {                                   // (kkt-x)
       const int i = (int)(t / n), r = (int)(t - (size_t)i * n);
       const double* Qr = a.Q + (size_t)i * nn + (size_t)r * n;
-      const double* xi = a.x + (size_t)i * n;
-      const double yir = a.y[t];
+      const size_t xo = (size_t)i * n;
       FF s{0.f, 0.f};
       ff_add(s, a.q[t]);
-      ff_add(s, -yir);
-      float rs = 1.f;
-      for (int b = 0; b < n; ++b) { ff_fma(s, Qr[b], xi[b]); if (ks) rs += absf_of(Qr[b]); }
+      ff_add2(s, -f.yh[t], -f.yl[t]);
+      rs = 1.f;
+#pragma unroll 4
+      for (int b = 0; b < n; ++b) {
+        const float aq = ff_fma_d(s, Qr[b], f.xh[xo + b], f.xl[xo + b]);
+        if (ks) rs += aq;
+      }
       for (int k = a.child_start[i]; k < a.child_start[i + 1]; ++k) {
         const int j = a.child_list[k];
         const double* Aj = a.A + (size_t)j * nn + r;
-        const double* yj = a.y + (size_t)j * n;
-        for (int b = 0; b < n; ++b) { ff_fma(s, Aj[(size_t)b * n], yj[b]); if (ks) rs += absf_of(Aj[(size_t)b * n]); }
+        const size_t yo = (size_t)j * n;
+#pragma unroll 4
+        for (int b = 0; b < n; ++b) {
+          const float aa = ff_fma_d(s, Aj[(size_t)b * n], f.yh[yo + b], f.yl[yo + b]);
+          if (ks) rs += aa;
+        }
         if (a.M) {
           const double* Mr = a.M + (size_t)j * nm + (size_t)r * m;
-          const double* uj = a.u + (size_t)j * m;
-          for (int b = 0; b < m; ++b) { ff_fma(s, Mr[b], uj[b]); if (ks) rs += absf_of(Mr[b]); }
+          const size_t uo = (size_t)j * m;
+          for (int b = 0; b < m; ++b) {
+            const float am = ff_fma_d(s, Mr[b], f.uh[uo + b], f.ul[uo + b]);
+            if (ks) rs += am;
+          }
         }
       }
       out = ff_value(s);
       a.res_x[t] = out;
-      kmax = fmaxf(kmax, rs);
-      const unsigned long long zx = abits(a.x[t]), zy = abits(yir);
-      zmax = zx > zmax ? zx : zmax;
-      zmax = zy > zmax ? zy : zmax;
-      const unsigned long long bq = abits(a.q[t]), bc = abits(a.c[t]);
-      bmax = bq > bmax ? bq : bmax;
-      bmax = bc > bmax ? bc : bmax;
     } else if (t < rows_x + rows_u) {                   // (kkt-u)
       const size_t tu = t - rows_x;
       const int i = (int)(tu / m), r = (int)(tu - (size_t)i * m);
       if (i == a.root) { a.res_u[tu] = 0.0; continue; }
       const int p = a.parent[i];
-      const double* xp = a.x + (size_t)p * n;
-      const double* ui = a.u + (size_t)i * m;
-      const double* yi = a.y + (size_t)i * n;
+      const size_t xo = (size_t)p * n, uo = (size_t)i * m, yo = (size_t)i * n;
       const double* Bc = a.B + (size_t)i * nm + r;
       const double* Rr = a.R + (size_t)i * m * m + (size_t)r * m;
       FF s{0.f, 0.f};
       ff_add(s, a.r[tu]);
-      float rs = 0.f;
       if (a.M) {
         const double* Mc = a.M + (size_t)i * nm + r;
-        for (int b = 0; b < n; ++b) { ff_fma(s, Mc[(size_t)b * m], xp[b]); if (ks) rs += absf_of(Mc[(size_t)b * m]); }
+        for (int b = 0; b < n; ++b) {
+          const float am = ff_fma_d(s, Mc[(size_t)b * m], f.xh[xo + b], f.xl[xo + b]);
+          if (ks) rs += am;
+        }
       }
-      for (int b = 0; b < m; ++b) { ff_fma(s, Rr[b], ui[b]); if (ks) rs += absf_of(Rr[b]); }
-      for (int b = 0; b < n; ++b) { ff_fma(s, Bc[(size_t)b * m], yi[b]); if (ks) rs += absf_of(Bc[(size_t)b * m]); }
+      for (int b = 0; b < m; ++b) {
+        const float ar = ff_fma_d(s, Rr[b], f.uh[uo + b], f.ul[uo + b]);
+        if (ks) rs += ar;
+      }
+#pragma unroll 4
+      for (int b = 0; b < n; ++b) {
+        const float ab = ff_fma_d(s, Bc[(size_t)b * m], f.yh[yo + b], f.yl[yo + b]);
+        if (ks) rs += ab;
+      }
       out = ff_value(s);
       a.res_u[tu] = out;
-      kmax = fmaxf(kmax, rs);
-      const unsigned long long zu = abits(ui[r]), br = abits(a.r[tu]);
-      zmax = zu > zmax ? zu : zmax;
-      bmax = br > bmax ? br : bmax;
     } else {                                            // constraint entering i
       const size_t tc = t - rows_x - rows_u;
       const int i = (int)(tc / n), r = (int)(tc - (size_t)i * n);
-      const double* yi = a.y + (size_t)i * n;
+      const size_t yo = (size_t)i * n;
       FF s{0.f, 0.f};
       ff_add(s, a.c[tc]);
-      ff_add(s, -a.x[tc]);
-      float rs = 1.f;
+      ff_add2(s, -f.xh[tc], -f.xl[tc]);
+      rs = 1.f;
       if (a.Delta) {
         const double* Dr = a.Delta + (size_t)i * nn + (size_t)r * n;
-        for (int b = 0; b < n; ++b) { ff_fma(s, -Dr[b], yi[b]); if (ks) rs += absf_of(Dr[b]); }
+#pragma unroll 4
+        for (int b = 0; b < n; ++b) {
+          const float ad = ff_fma_d(s, -Dr[b], f.yh[yo + b], f.yl[yo + b]);
+          if (ks) rs += ad;
+        }
       }
       if (i != a.root) {
         const int p = a.parent[i];
-        const double* xp = a.x + (size_t)p * n;
-        const double* ui = a.u + (size_t)i * m;
+        const size_t xo = (size_t)p * n, uo = (size_t)i * m;
         const double* Ar = a.A + (size_t)i * nn + (size_t)r * n;
         const double* Br = a.B + (size_t)i * nm + (size_t)r * m;
-        for (int b = 0; b < n; ++b) { ff_fma(s, Ar[b], xp[b]); if (ks) rs += absf_of(Ar[b]); }
-        for (int b = 0; b < m; ++b) { ff_fma(s, Br[b], ui[b]); if (ks) rs += absf_of(Br[b]); }
+#pragma unroll 4
+        for (int b = 0; b < n; ++b) {
+          const float aa = ff_fma_d(s, Ar[b], f.xh[xo + b], f.xl[xo + b]);
+          if (ks) rs += aa;
+        }
+        for (int b = 0; b < m; ++b) {
+          const float ab = ff_fma_d(s, Br[b], f.uh[uo + b], f.ul[uo + b]);
+          if (ks) rs += ab;
+        }
       }
       out = ff_value(s);
       a.res_c[tc] = out;
-      kmax = fmaxf(kmax, rs);
     }
+    kmax = fmaxf(kmax, rs);
     const unsigned long long ob = abits(out);
     rmax = ob > rmax ? ob : rmax;
   }
-  warp_maxbits_to(a.maxes + 0, rmax);
-  warp_maxbits_to(a.maxes + 1, zmax);
-  warp_maxbits_to(a.maxes + 2, bmax);
-  if (ks) warp_maxbits_to(a.maxes + 3, abits((double)kmax));
+  block_maxbits_to(a.maxes + 0, rmax);
+  if (ks) block_maxbits_to(a.maxes + 3, abits((double)kmax));
 }
 
 }  // namespace tlqr

@@ -209,6 +209,8 @@ struct tlqr_factor_t {
   int* status = nullptr;
   // FP64 residual buffers and staging for host-memory calls
   double *res_x = nullptr, *res_u = nullptr, *res_c = nullptr;
+  // MIXED: (hi, lo) FP32 splits of x, u, y for the float-float residual
+  float *xh = nullptr, *xl = nullptr, *uh = nullptr, *ul = nullptr, *yh = nullptr, *yl = nullptr;
   unsigned long long* maxes = nullptr;
   unsigned long long* h_maxes = nullptr;   // pinned mirror
   int* h_status = nullptr;                  // pinned mirror
@@ -367,6 +369,14 @@ cudaError_t launch_tail(Recorder* rc, int kind, Kernel kernel, cudaStream_t st, 
   cudaError_t e = cudaGetLastError();
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[kind]++; rc->units[kind] += 1; }
+  return e;
+}
+
+cudaError_t launch_split(Recorder* rc, const SplitList& L, cudaStream_t st) {
+  const int blocks = 148 * 4, threads = 256;
+  k_split_ff<<<blocks, threads, 0, st>>>(L);
+  cudaError_t e = cudaGetLastError();
+  if (rc) { rc->launches[TLQR_K_RESIDUAL]++; }
   return e;
 }
 
@@ -571,13 +581,32 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   a.maxes = f->maxes;
   cudaError_t e = cudaMemsetAsync(f->maxes, 0, (with_knorm ? 4 : 3) * sizeof(unsigned long long), st);
   if (e) return e;
+  FFArgs fa{};
+  if (ff) {
+    // split x, u, y once per call; ||z|| and ||b|| maxima come from the same pass
+    const size_t N = P->N, n = f->opt.n, m = f->opt.m;
+    SplitList L{};
+    auto add = [&](const double* src, float* hi, float* lo, size_t len, int slot) {
+      L.src[L.count] = src; L.hi[L.count] = hi; L.lo[L.count] = lo; L.len[L.count] = len; L.slot[L.count] = slot;
+      ++L.count;
+    };
+    add(x, f->xh, f->xl, N * n, 1);
+    add(u, f->uh, f->ul, N * m, 1);
+    add(y, f->yh, f->yl, N * n, 1);
+    add(p.q, nullptr, nullptr, N * n, 2);
+    add(p.r, nullptr, nullptr, N * m, 2);
+    add(p.c, nullptr, nullptr, N * n, 2);
+    L.maxes = f->maxes;
+    if ((e = launch_split(rc, L, st))) return e;
+    fa = FFArgs{f->xh, f->xl, f->uh, f->ul, f->yh, f->yl};
+  }
   const size_t rows = (size_t)P->N * (2 * f->opt.n + f->opt.m);
   const int threads = 256;
-  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 16);
+  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 32);
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
   EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  if (ff) k_residual_ff<<<blocks, threads, 0, st>>>(a);
+  if (ff) k_residual_ff<<<blocks, threads, 0, st>>>(a, fa);
   else k_residual<<<blocks, threads, 0, st>>>(a);
   if ((e = cudaGetLastError())) return e;
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
@@ -929,6 +958,11 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   f->status = (int*)take(1, sizeof(int));
   f->res_x = (double*)take(N * n, 8); f->res_u = (double*)take(N * m, 8); f->res_c = (double*)take(N * n, 8);
   f->maxes = (unsigned long long*)take(4, 8);
+  if (opts->precision == TLQR_PREC_MIXED) {
+    f->xh = (float*)take(N * n, 4); f->xl = (float*)take(N * n, 4);
+    f->uh = (float*)take(N * m, 4); f->ul = (float*)take(N * m, 4);
+    f->yh = (float*)take(N * n, 4); f->yl = (float*)take(N * n, 4);
+  }
   if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_maxes, 4 * sizeof(unsigned long long));
   if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_status, sizeof(int));
   if (err == cudaSuccess && f->dflag) err = cudaMemset(f->dflag, 0, N);

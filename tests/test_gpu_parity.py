@@ -367,15 +367,15 @@ def test_profiler_times_kernels_inside_graphs():
         x = torch.zeros((len(p), 4), dtype=torch.float64, device="cuda")
         u = torch.zeros((len(p), 2), dtype=torch.float64, device="cuda")
         y = torch.zeros((len(p), 4), dtype=torch.float64, device="cuda")
-        tlqr.tlqr_profile_mask(s.f, ["compress", "rake"])
+        tlqr.tlqr_profile_mask(s.f, ["compress", "expand"])
         for _ in range(3):
             tlqr.tlqr_solve(s.f, dd, x, u, y)
         prof = tlqr.tlqr_profile_read(s.f)
     finally:
         s.close()
     assert prof["compress"]["timed"] == prof["compress"]["launches"] > 0
-    assert prof["compress"]["ms"] > 0 and prof["rake"]["ms"] > 0
-    assert prof["expand"]["timed"] == 0
+    assert prof["compress"]["ms"] > 0 and prof["expand"]["ms"] > 0
+    assert prof["local_factor"]["timed"] == 0 and prof["local_factor"]["launches"] > 0
 
 
 # -------------------------------------------------------------------- kernel families
