@@ -209,7 +209,26 @@ __device__ __forceinline__ void ff_add2(FF& acc, float h, float l) {
   acc.l += err + l;
   acc.h = s;
 }
-__device__ __forceinline__ double ff_value(const FF& v) { return (double)v.h + (double)v.l; }
+// Exact float -> double by bit manipulation (no FP64 instruction).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+  if (e == 0) {
+    if (man == 0) return __longlong_as_double((long long)sign);
+    // subnormal float man * 2^-149: leading bit p becomes the implicit bit
+    const int p = 31 - __clz(man);
+    const unsigned m2 = (man << (23 - p)) & 0x7fffffu;
+    const unsigned long long ex = (unsigned long long)(874 + p);   // 1023 - 149 + p
+    return __longlong_as_double((long long)(sign | (ex << 52) | ((unsigned long long)m2 << 29)));
+  }
+  if (e == 0xffu) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((unsigned long long)man << 29)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)man << 29)));
+}
+// The residual value only feeds an FP32 correction solve and a max-norm: its
+// float-float accumulation removes the cancellation, and the final h + l is
+// rounded to FP32 and widened exactly.
+__device__ __forceinline__ double ff_value(const FF& v) { return f2d_bits(v.h + v.l); }
 // |v| as ordered bits (integer max), NaN sorts above +inf
 __device__ __forceinline__ unsigned long long abits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
@@ -353,7 +372,7 @@ __global__ void k_residual_ff(ResidualArgs a, FFArgs f) {
         const double* Dr = a.Delta + (size_t)i * nn + (size_t)r * n;
 #pragma unroll 4
         for (int b = 0; b < n; ++b) {
-          const float ad = ff_fma_d(s, -Dr[b], f.yh[yo + b], f.yl[yo + b]);
+          const float ad = ff_fma_d(s, Dr[b], -f.yh[yo + b], -f.yl[yo + b]);
           if (ks) rs += ad;
         }
       }
@@ -380,7 +399,7 @@ __global__ void k_residual_ff(ResidualArgs a, FFArgs f) {
     rmax = ob > rmax ? ob : rmax;
   }
   block_maxbits_to(a.maxes + 0, rmax);
-  if (ks) block_maxbits_to(a.maxes + 3, abits((double)kmax));
+  if (ks) block_maxbits_to(a.maxes + 3, abits(f2d_bits(kmax)));
 }
 
 }  // namespace tlqr
