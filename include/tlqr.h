@@ -120,6 +120,7 @@ typedef struct {
                             a reduction's readiness weights exceeded 120 bits      */
   int32_t height;        /* longest root-to-leaf path, in edges                     */
   int32_t max_degree;
+  int32_t n_trees;       /* trees of a forest plan (1 for tlqr_plan_create)          */
 } tlqr_plan_stats_t;
 
 typedef struct {
@@ -139,11 +140,22 @@ typedef struct {
  * TLQR_ERR_OOM. */
 int tlqr_plan_create(const int32_t *parent, int32_t N, tlqr_plan_t **out);
 
+/* Batch of independent problems: a forest.  Same as tlqr_plan_create but
+ * parent[] may hold several -1 entries, one per tree.  The KKT system is then
+ * block diagonal, one block per tree, each the system of eq. (kkt) of its own
+ * tree; every tree is contracted by the same structural rule in the same
+ * rounds, so each tree's schedule -- and, in FP64, each tree's result -- is
+ * exactly the one it has alone, while the whole batch runs in one launch
+ * sequence.  Node and edge arrays of all trees are concatenated in parent[]
+ * order.  Errors as tlqr_plan_create (TLQR_ERR_TOPOLOGY: no root, a cycle, an
+ * index out of range). */
+int tlqr_plan_create_forest(const int32_t *parent, int32_t N, tlqr_plan_t **out);
+
 /* Free a plan (NULL is ignored).  A plan must outlive the factors made from it. */
 void tlqr_plan_destroy(tlqr_plan_t *plan);
 
 /* Counts of the plan: rounds, rakes, compressions (Sec. IX-B: rakes +
- * compressions = N - 1), dependency levels of eq. (earliest-level) with the
+ * compressions = N - 1 per tree), dependency levels of eq. (earliest-level) with the
  * readiness-weighted sibling reduction of eq. (readiness-code-data) (Lemma 3,
  * Lemma 4), height and maximum out-degree.  Host only. */
 int tlqr_plan_stats(const tlqr_plan_t *plan, tlqr_plan_stats_t *out);

@@ -56,12 +56,13 @@ def assemble_kkt(parent, n: int, m: int, data: dict):
         if D is not None:
             K[Y(j), Y(j)] += -D[j]
         b[Y(j)] += c[j]
-    root = int(np.nonzero(parent < 0)[0][0])
-    # (kkt-root): c_rho - x_rho - Delta_rho y_rho = 0
-    K[Y(root), X(root)] += -I
-    if D is not None:
-        K[Y(root), Y(root)] += -D[root]
-    b[Y(root)] += c[root]
+    # (kkt-root): c_rho - x_rho - Delta_rho y_rho = 0, for every root (a forest is a batch)
+    for root in np.nonzero(parent < 0)[0]:
+        root = int(root)
+        K[Y(root), X(root)] += -I
+        if D is not None:
+            K[Y(root), Y(root)] += -D[root]
+        b[Y(root)] += c[root]
     return K, b, (X, U, Y, nonroot)
 
 

@@ -34,23 +34,25 @@ def _children(parent):
 def structural_schedule(parent):
     """Return a list of rounds; each round is dict(rakes=[(j, i)], compresses=[(j, i, k)]).
 
+    parent may hold several roots (a forest); every tree is contracted by the
+    same rule in the same rounds.
+
     (j, i) = raked leaf and its current parent; (j, i, k) = compressed centre,
     its current parent and its current (only) child.  Lists are in increasing j.
     """
     parent = [int(p) for p in parent]
     N = len(parent)
-    roots = [i for i in range(N) if parent[i] < 0]
-    if len(roots) != 1:
-        raise ValueError("parent array must have exactly one root")
-    root = roots[0]
+    roots = {i for i in range(N) if parent[i] < 0}
+    if not roots:
+        raise ValueError("parent array must have a root")
     cur_parent = list(parent)
     ch = _children(parent)
     alive = set(range(N))
     rounds = []
-    while len(alive) > 1:
+    while len(alive) > len(roots):
         rakes = []
         for j in sorted(alive):
-            if j != root and not ch[j]:
+            if j not in roots and not ch[j]:
                 rakes.append((j, cur_parent[j]))
         for j, i in rakes:
             ch[i].discard(j)
@@ -58,7 +60,7 @@ def structural_schedule(parent):
         selected = []
         sel = set()
         for j in sorted(alive):
-            if j == root or len(ch[j]) != 1:
+            if j in roots or len(ch[j]) != 1:
                 continue
             k = next(iter(ch[j]))
             i = cur_parent[j]

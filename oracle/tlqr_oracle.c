@@ -22,7 +22,8 @@
  *
  * Layout: row-major dense blocks; node arrays [N][..]; edge arrays indexed by
  * the child node [N][..] with the root slot ignored.  M and Delta may be NULL
- * (all zero).
+ * (all zero).  parent[] may hold several roots: a forest is a batch of
+ * independent problems, solved tree by tree.
  *
  * Factorisations: F = I + Delta P is nonsymmetric, so it is factored by LU with
  * partial pivoting; G = R + B^T W B is symmetric positive definite (Sec. V-C)
@@ -161,15 +162,16 @@ static void chol_solve(int m, const double *l, double *b, int nrhs) {
 
 /* ---------------- topology ---------------- */
 
-/* Breadth-first order from the root, children visited in increasing index.
- * Returns the root or -1 when parent[] is not a tree. */
+/* Breadth-first order from the roots (a forest is a batch of independent
+ * trees; a single tree has one root), children visited in increasing index.
+ * Returns the number of roots, or -1 when parent[] is not a forest. */
 static int bfs_order(int N, const int32_t *parent, int *order, int *child_start, int *child_list) {
-  int root = -1;
+  int n_roots = 0;
   for (int i = 0; i < N; ++i) {
-    if (parent[i] == -1) { if (root >= 0) return -1; root = i; }
+    if (parent[i] == -1) ++n_roots;
     else if (parent[i] < 0 || parent[i] >= N || parent[i] == i) return -1;
   }
-  if (root < 0) return -1;
+  if (n_roots == 0) return -1;
   memset(child_start, 0, sizeof(int) * (N + 1));
   for (int i = 0; i < N; ++i) if (parent[i] >= 0) child_start[parent[i] + 1]++;
   for (int i = 0; i < N; ++i) child_start[i + 1] += child_start[i];
@@ -179,12 +181,12 @@ static int bfs_order(int N, const int32_t *parent, int *order, int *child_start,
   for (int j = 0; j < N; ++j) if (parent[j] >= 0) child_list[fill[parent[j]]++] = j;  /* increasing j */
   free(fill);
   int head = 0, tail = 0;
-  order[tail++] = root;
+  for (int i = 0; i < N; ++i) if (parent[i] < 0) order[tail++] = i;
   while (head < tail) {
     int i = order[head++];
     for (int t = child_start[i]; t < child_start[i + 1]; ++t) order[tail++] = child_list[t];
   }
-  return tail == N ? root : -1;   /* a cycle leaves nodes unreached */
+  return tail == N ? n_roots : -1;   /* a cycle leaves nodes unreached */
 }
 
 /* ---------------- the recursion ---------------- */
@@ -209,8 +211,7 @@ int oracle_tree_riccati(int32_t N, int32_t n, int32_t m, const int32_t *parent,
   int rc = 0;
   if (!order || !cs || !cl || !Flu || !Fpiv || !W || !Gl || !T || !p || !tmp) { rc = 4; goto done; }
 
-  int root = bfs_order(N, parent, order, cs, cl);
-  if (root < 0) { rc = 1; goto done; }
+  if (bfs_order(N, parent, order, cs, cl) < 0) { rc = 1; goto done; }
 
   double *Acl = tmp, *H = Acl + L, *t1 = H + L, *t2 = t1 + L, *t3 = t2 + L, *Ft = t3 + L,
          *v1 = Ft + L, *v2 = v1 + (n + m), *v3 = v2 + (n + m), *w1 = v3 + (n + m);
@@ -232,7 +233,7 @@ int oracle_tree_riccati(int32_t N, int32_t n, int32_t m, const int32_t *parent,
     for (int a = 0; a < n; ++a) for (int b = 0; b < n; ++b) Ft[IDX(a, b, n)] = Pj[IDX(b, a, n)];
     lu_solve_t(n, Fj, Fpiv + (size_t)n * j, Ft, n);
     for (int a = 0; a < n; ++a) for (int b = 0; b < n; ++b) Wj[IDX(a, b, n)] = Ft[IDX(b, a, n)];
-    if (j == root) continue;
+    if (parent[j] < 0) continue;     /* a root: no entering edge */
     int i = parent[j];
     const double *Ae = A + nn * j, *Be = B + nm * j, *Re = R + mm_ * j;
     const double *Me = M ? M + nm * j : NULL;
@@ -268,8 +269,9 @@ int oracle_tree_riccati(int32_t N, int32_t n, int32_t m, const int32_t *parent,
     mtv(n, n, Acl, v1, pi, 1);
   }
 
-  /* Root: f = Delta p - c, x_rho = -F^{-1} f  (eq. xroot) */
-  {
+  /* Roots: f = Delta p - c, x_rho = -F^{-1} f  (eq. xroot) */
+  for (int root = 0; root < N; ++root) {
+    if (parent[root] >= 0) continue;
     double *f = v1;
     if (Delta) mv(n, n, Delta + nn * root, p + (size_t)n * root, f, 0); else memset(f, 0, sizeof(double) * n);
     for (int a = 0; a < n; ++a) f[a] -= c[(size_t)n * root + a];
@@ -277,8 +279,9 @@ int oracle_tree_riccati(int32_t N, int32_t n, int32_t m, const int32_t *parent,
     for (int a = 0; a < n; ++a) x[(size_t)n * root + a] = -f[a];
   }
   /* Forward pass: parents before children (BFS order). eq. (local-affine-solve), (recover) */
-  for (int oi = 1; oi < N; ++oi) {
+  for (int oi = 0; oi < N; ++oi) {
     int j = order[oi], i = parent[j];
+    if (i < 0) continue;
     const double *pj = p + (size_t)n * j;
     double *f = v1, *g = v2, *bb = v3, *k = w1;
     if (Delta) mv(n, n, Delta + nn * j, pj, f, 0); else memset(f, 0, sizeof(double) * n);
@@ -304,8 +307,11 @@ int oracle_tree_riccati(int32_t N, int32_t n, int32_t m, const int32_t *parent,
     mv(n, n, P + nn * i, x + (size_t)n * i, y + (size_t)n * i, 0);
     for (int a = 0; a < n; ++a) y[(size_t)n * i + a] += p[(size_t)n * i + a];
   }
-  memset(u + (size_t)m * root, 0, sizeof(double) * m);
-  memset(K + nm * root, 0, sizeof(double) * nm);
+  for (int root = 0; root < N; ++root) {
+    if (parent[root] >= 0) continue;
+    memset(u + (size_t)m * root, 0, sizeof(double) * m);
+    memset(K + nm * root, 0, sizeof(double) * nm);
+  }
   if (p_out) memcpy(p_out, p, sizeof(double) * (size_t)n * N);
 
 done:
@@ -331,9 +337,9 @@ int oracle_kkt_residual(int32_t N, int32_t n, int32_t m, const int32_t *parent,
   double *rowsum_x = (double *)calloc((size_t)N * n, sizeof(double));
   if (!rowsum_x) return 4;
   double rmax = 0, Kmax = 0, zmax = 0, bmax = 0;
-  int root = -1;
-  for (int i = 0; i < N; ++i) if (parent[i] < 0) root = i;
-  if (root < 0) { free(rowsum_x); return 1; }
+  int n_roots = 0;
+  for (int i = 0; i < N; ++i) if (parent[i] < 0) ++n_roots;
+  if (n_roots == 0) { free(rowsum_x); return 1; }
   /* node rows: Q x + q - y */
   for (int i = 0; i < N; ++i) {
     mv(n, n, Q + nn * i, x + (size_t)n * i, res_x + (size_t)n * i, 0);
@@ -347,7 +353,7 @@ int oracle_kkt_residual(int32_t N, int32_t n, int32_t m, const int32_t *parent,
   for (int j = 0; j < N; ++j) {
     double *rc_ = res_c + (size_t)n * j;
     double *ru = res_u + (size_t)m * j;
-    if (j == root) {
+    if (parent[j] < 0) {
       for (int a = 0; a < n; ++a) {
         double s = c[(size_t)n * j + a] - x[(size_t)n * j + a];
         double rs = 1.0;
@@ -401,7 +407,7 @@ int oracle_kkt_residual(int32_t N, int32_t n, int32_t m, const int32_t *parent,
     if (fabs(c[t]) > bmax) bmax = fabs(c[t]);
   }
   for (int j = 0; j < N; ++j) {
-    if (j == root) continue;
+    if (parent[j] < 0) continue;
     for (int a = 0; a < m; ++a) {
       size_t t = (size_t)m * j + a;
       if (fabs(res_u[t]) > rmax) rmax = fabs(res_u[t]);

@@ -757,7 +757,7 @@ __global__ void kf_condense(Ws<T> w, int count) {
   T *sM = sB + N * MLD, *sBR = sM + N * MLD, *sMR = sBR + N * MLD, *sR = sMR + N * MLD;
   const int gl = g.gl, r = gl < N ? gl : 0;
   const size_t oi = (size_t)i * NN, om = (size_t)i * NM;
-  const bool is_root = i == w.root;
+  const bool is_root = node_is_root(w, i);
   bool dnz = false;
   if (w.has_delta) {
     bool mine = false;
@@ -851,7 +851,7 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
   int* order = reinterpret_cast<int*>(gbase + L::tbytes);
   const int gl = g.gl, r = gl < N ? gl : 0;
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
-  const bool is_root = j == w.root;
+  const bool is_root = node_is_root(w, j);
   const bool dnz = w.has_delta && w.dflag[j];
   const bool any_dnz = __any_sync(TLQR_FULL_MASK, dnz);
   stage<T, T, N, N, LD, G>(sP, w.U + oj, gl);
@@ -1005,7 +1005,7 @@ __global__ void kf_aff_init(Ws<T> w, int count) {
   T* sW = reinterpret_cast<T*>(smem_raw + g.gid * A_::bytes);
   T *sA = sW + N * LD, *sK = sA + N * LD, *sB = sK + M * LD, *vc = sB + N * MLD, *vw = vc + LD, *vr = vw + LD;
   const int gl = g.gl, r = gl < N ? gl : 0;
-  const bool is_root = j == w.root;
+  const bool is_root = node_is_root(w, j);
   if (g.valid && gl < N) w.h[(size_t)j * N + r] = (T)w.q[(size_t)j * N + r];
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
   const bool dnz = w.has_delta && w.dflag[j];
@@ -1059,7 +1059,7 @@ __global__ void kf_local_solve(Ws<T> w, int count) {
   const int gl = g.gl, r = gl < N ? gl : 0;
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
   const bool dnz = w.has_delta && w.dflag[j];
-  const bool is_root = j == w.root;
+  const bool is_root = node_is_root(w, j);
   stage<T, T, N, N, LD, G>(sW, dnz ? w.W + oj : w.U + oj, gl);
   stage<T, double, N, M, MLD, G>(sB, w.B + om, gl);
   if (!is_root) stage<T, T, M, M, MLD, G>(sL, w.LG + (size_t)j * M * M, gl);
@@ -1167,7 +1167,7 @@ __global__ void kf_recover(Ws<T> w, double* x, double* u, double* y, int accumul
 #pragma unroll
   for (int t = 0; t < N; ++t) yr = fma(w.U[(size_t)j * NN + t * N + r], xv[t], yr);   // P symmetric
   bool bad = !tfinite(xr) || !tfinite(yr);
-  const bool nonroot = j != w.root;
+  const bool nonroot = !node_is_root(w, j);
   T ur = T(0);
   if (nonroot && gl < M) {
     const int par = w.parent[j];

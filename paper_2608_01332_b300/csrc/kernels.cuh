@@ -31,7 +31,7 @@ enum : int { ST_OK = 0, ST_NOT_PD = 3, ST_SINGULAR = 4, ST_NONFINITE = 5 };
 
 template <typename T>
 struct Ws {
-  int N, n, m, root;
+  int N, n, m;
   int has_M, has_delta;
   // problem data (FP64, device)
   const double *Q, *M, *R, *A, *B, *Delta;
@@ -48,6 +48,11 @@ struct Ws {
   T *h, *z, *s, *cv, *bv, *kv, *xs;
   int* status;
 };
+
+// A node is a root (of its tree in a forest) when its parent is -1.  Batched
+// primitive calls have no tree (parent == nullptr) and no roots.
+template <typename T>
+__device__ __forceinline__ bool node_is_root(const Ws<T>& w, int j) { return w.parent ? (w.parent[j] < 0) : false; }
 
 __device__ __forceinline__ void set_status(int* status, int code) {
   if (lane_id() == 0) atomicCAS(status, 0, code);
@@ -101,7 +106,7 @@ __global__ void k_condense(Ws<T> w, int warp_bytes) {
     dnz = wany(dnz);
     if (lane_id() == 0) w.dflag[i] = dnz ? 1 : 0;
   }
-  if (i == w.root) return;
+  if (node_is_root(w, i)) return;
   T *sR = sm, *sX = sm + m * m, *sB = sX + 2 * n * m, *sM = sB + n * m;
   const int nr = w.has_M ? 2 * n : n;    // X = R^{-1} [B^T | M^T]  (m x nr)
   wload(sR, w.R + (size_t)i * m * m, m * m);
@@ -257,7 +262,7 @@ __global__ void k_local_factor(Ws<T> w, int warp_bytes) {
     wgemm<T, false, false>(n, n, n, sP, n, sFi, n, sW, n, T(1), (const T*)nullptr, 0);
     wload(w.W + oj, sW, nn);
   }
-  if (j == w.root) return;
+  if (node_is_root(w, j)) return;
   const T* Wuse = dnz ? sW : sP;
   const size_t onm = (size_t)j * n * m;
   wload(sB, w.B + onm, n * m);
@@ -317,7 +322,7 @@ __global__ void k_aff_init(Ws<T> w, int warp_bytes) {
   if (j >= w.N) return;
   const int n = w.n, m = w.m, nn = n * n;
   wload(w.h + (size_t)j * n, w.q + (size_t)j * n, n);
-  if (j == w.root) return;
+  if (node_is_root(w, j)) return;
   T* sm = warp_smem<T>(warp_bytes);
   T *sWm = sm, *sA = sm + nn, *sB = sA + nn, *sK = sB + n * m, *vc = sK + m * n, *vw = vc + n,
     *vr = vw + n;
@@ -412,7 +417,7 @@ __global__ void k_local_solve(Ws<T> w, int warp_bytes) {
   __syncwarp();
   for (int a = lane_id(); a < n; a += 32) vf[a] -= (T)w.c[(size_t)j * n + a];
   __syncwarp();
-  if (j == w.root) {
+  if (node_is_root(w, j)) {
     // x_rho = -F^{-1} f
     if (dnz) {
       wload(sMat, w.Finv + oj, nn);
@@ -490,7 +495,7 @@ __global__ void k_recover(Ws<T> w, double* x, double* u, double* y, int accumula
   T *sP = sm, *sK = sm + nn, *vx = sK + m * n, *vxp = vx + n, *vo = vxp + n;
   wload(sP, w.U + (size_t)j * nn, nn);
   wload(vx, w.xs + (size_t)j * n, n);
-  const bool nonroot = j != w.root;
+  const bool nonroot = !node_is_root(w, j);
   if (nonroot) {
     wload(sK, w.K + (size_t)j * m * n, m * n);
     wload(vxp, w.xs + (size_t)w.parent[j] * n, n);
@@ -520,14 +525,14 @@ __global__ void k_recover(Ws<T> w, double* x, double* u, double* y, int accumula
 
 // Widen P (= U after the reverse pass) and K to FP64 outputs.
 template <typename T>
-__global__ void k_export_PK(int N, int n, int m, int root, const T* U, const T* K, double* P, double* Ko) {
+__global__ void k_export_PK(int N, int n, int m, const int* parent, const T* U, const T* K, double* P, double* Ko) {
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (P) for (size_t e = tid; e < (size_t)N * nn; e += stride) P[e] = (double)U[e];
   if (Ko)
     for (size_t e = tid; e < (size_t)N * mn; e += stride)
-      Ko[e] = ((int)(e / mn) == root) ? 0.0 : (double)K[e];
+      Ko[e] = (parent[e / mn] < 0) ? 0.0 : (double)K[e];
 }
 
 }  // namespace tlqr

@@ -104,7 +104,7 @@ extern "C" int tlqr_kkt_residual_noalloc(const tlqr_plan_t* plan, int32_t n, int
   if (!e) e = cudaMemsetAsync(d_maxes, 0, 4 * sizeof(unsigned long long), st);
   if (e) return TLQR_ERR_CUDA;
   tlqr::ResidualArgs a{};
-  a.N = (int)N; a.n = n; a.m = m; a.root = plan->root; a.with_knorm = 1;
+  a.N = (int)N; a.n = n; a.m = m; a.with_knorm = 1;
   a.parent = d_parent; a.child_start = d_cs; a.child_list = d_cl;
   a.Q = prob->Q; a.q = prob->q; a.M = prob->M; a.R = prob->R; a.r = prob->r; a.A = prob->A; a.B = prob->B;
   a.c = prob->c; a.Delta = prob->Delta;

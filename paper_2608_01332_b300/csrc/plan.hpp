@@ -16,7 +16,8 @@ struct tlqr_round {
 
 struct tlqr_plan_t {
   int32_t N = 0;
-  int32_t root = -1;
+  int32_t root = -1;                    // first root (the root of a single-tree plan)
+  int32_t n_trees = 1;                  // roots in the parent array (a forest is a batch)
   std::vector<int32_t> parent;          // caller's parent array
   std::vector<tlqr_round> rounds;
   // rakes (global order: round by round, segment by segment)

@@ -70,7 +70,11 @@ int readiness_level(const std::vector<int>& lv, int* n_comb) {
 
 }  // namespace
 
-extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** out) {
+namespace {
+
+// Shared builder.  allow_forest = false: exactly one root; true: one or more
+// roots, each tree contracted independently in the same rounds (a batch).
+int build_plan(const int32_t* parent, int32_t N, bool allow_forest, tlqr_plan_t** out) {
   if (!parent || !out || N < 1) return TLQR_ERR_ARG;
   *out = nullptr;
   tlqr_plan_t* P = new (std::nothrow) tlqr_plan_t;
@@ -78,12 +82,13 @@ extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** 
   try {
     P->N = N;
     P->parent.assign(parent, parent + N);
-    int root = -1;
+    int root = -1, n_roots = 0;
     for (int i = 0; i < N; ++i) {
       int p = parent[i];
       if (p == -1) {
-        if (root >= 0) { delete P; return TLQR_ERR_TOPOLOGY; }
-        root = i;
+        if (root >= 0 && !allow_forest) { delete P; return TLQR_ERR_TOPOLOGY; }
+        if (root < 0) root = i;
+        ++n_roots;
       } else if (p < 0 || p >= N || p == i) {
         delete P;
         return TLQR_ERR_TOPOLOGY;
@@ -91,21 +96,22 @@ extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** 
     }
     if (root < 0) { delete P; return TLQR_ERR_TOPOLOGY; }
     P->root = root;
+    P->n_trees = n_roots;
 
     // original children, CSR in increasing index
     std::vector<int32_t> cnt(N, 0);
     P->child_start.assign(N + 1, 0);
-    for (int j = 0; j < N; ++j) if (j != root) P->child_start[parent[j] + 1]++;
+    for (int j = 0; j < N; ++j) if (parent[j] >= 0) P->child_start[parent[j] + 1]++;
     for (int i = 0; i < N; ++i) P->child_start[i + 1] += P->child_start[i];
     P->child_list.resize(std::max(0, N - 1));
     {
       std::vector<int32_t> fill(P->child_start.begin(), P->child_start.end() - 1);
-      for (int j = 0; j < N; ++j) if (j != root) P->child_list[fill[parent[j]]++] = j;
+      for (int j = 0; j < N; ++j) if (parent[j] >= 0) P->child_list[fill[parent[j]]++] = j;
     }
     // reachability from the root (a cycle leaves nodes unreached) and height
     {
-      std::vector<int32_t> depth(N, -1), stack{root};
-      depth[root] = 0;
+      std::vector<int32_t> depth(N, -1), stack;
+      for (int i = 0; i < N; ++i) if (parent[i] < 0) { depth[i] = 0; stack.push_back(i); }
       int seen = 0;
       while (!stack.empty()) {
         int i = stack.back(); stack.pop_back(); ++seen;
@@ -125,7 +131,7 @@ extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** 
     std::vector<int32_t> cur_parent(parent, parent + N);
     std::vector<int32_t> nchild(N, 0);
     std::vector<int64_t> child_sum(N, 0);       // sum of current child ids (gives the only child)
-    for (int j = 0; j < N; ++j) if (j != root) { nchild[parent[j]]++; child_sum[parent[j]] += j; }
+    for (int j = 0; j < N; ++j) if (parent[j] >= 0) { nchild[parent[j]]++; child_sum[parent[j]] += j; }
     std::vector<char> selected(N, 0), dead(N, 0);
     std::vector<int32_t> live;
     live.reserve(N);
@@ -140,12 +146,12 @@ extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** 
 
     std::vector<int32_t> leaves, sel;
     int round_no = 0;
-    while (live.size() > 1) {
+    while ((int)live.size() > n_roots) {
       ++round_no;
       tlqr_round rd{};
       // ---- rake every nonroot leaf
       leaves.clear();
-      for (int32_t j : live) if (j != root && nchild[j] == 0) leaves.push_back(j);
+      for (int32_t j : live) if (parent[j] >= 0 && nchild[j] == 0) leaves.push_back(j);
       // group by current parent, keeping increasing leaf index inside a group
       std::stable_sort(leaves.begin(), leaves.end(),
                        [&](int a, int b) { return cur_parent[a] < cur_parent[b]; });
@@ -193,7 +199,7 @@ extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** 
       rd.comp_begin = (int32_t)P->comp_j.size();
       sel.clear();
       for (int32_t j : live) {
-        if (dead[j] || j == root || nchild[j] != 1) continue;
+        if (dead[j] || parent[j] < 0 || nchild[j] != 1) continue;
         int k = (int)child_sum[j];
         int i = cur_parent[j];
         if (selected[i] || selected[k]) continue;
@@ -236,6 +242,16 @@ extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** 
   return TLQR_OK;
 }
 
+}  // namespace
+
+extern "C" int tlqr_plan_create(const int32_t* parent, int32_t N, tlqr_plan_t** out) {
+  return build_plan(parent, N, false, out);
+}
+
+extern "C" int tlqr_plan_create_forest(const int32_t* parent, int32_t N, tlqr_plan_t** out) {
+  return build_plan(parent, N, true, out);
+}
+
 extern "C" void tlqr_plan_destroy(tlqr_plan_t* plan) { delete plan; }
 
 extern "C" int tlqr_plan_stats(const tlqr_plan_t* P, tlqr_plan_stats_t* out) {
@@ -250,6 +266,7 @@ extern "C" int tlqr_plan_stats(const tlqr_plan_t* P, tlqr_plan_stats_t* out) {
   out->levels = P->levels;
   out->height = P->height;
   out->max_degree = P->max_degree;
+  out->n_trees = P->n_trees;
   return TLQR_OK;
 }
 

@@ -20,7 +20,7 @@
 namespace tlqr {
 
 struct ResidualArgs {
-  int N, n, m, root, with_knorm;
+  int N, n, m, with_knorm;
   const int *parent, *child_start, *child_list;
   const double *Q, *q, *M, *R, *r, *A, *B, *c, *Delta;
   const double *x, *u, *y;
@@ -96,7 +96,7 @@ __global__ void k_residual(ResidualArgs a) {
     } else if (t < rows_x + rows_u) {                   // (kkt-u)
       const size_t tu = t - rows_x;
       const int i = (int)(tu / m), r = (int)(tu - (size_t)i * m);
-      if (i == a.root) { a.res_u[tu] = 0.0; continue; }
+      if (a.parent[i] < 0) { a.res_u[tu] = 0.0; continue; }
       const int p = a.parent[i];
       const double* xp = a.x + (size_t)p * n;
       const double* ui = a.u + (size_t)i * m;
@@ -124,7 +124,7 @@ __global__ void k_residual(ResidualArgs a) {
         const double* Dr = a.Delta + (size_t)i * nn + (size_t)r * n;
         for (int b = 0; b < n; ++b) { s = fma(-Dr[b], yi[b], s); if (ks) rs += fabs(Dr[b]); }
       }
-      if (i != a.root) {
+      if (a.parent[i] >= 0) {
         const int p = a.parent[i];
         const double* xp = a.x + (size_t)p * n;
         const double* ui = a.u + (size_t)i * m;
@@ -335,7 +335,7 @@ __global__ void k_residual_ff(ResidualArgs a, FFArgs f) {
     } else if (t < rows_x + rows_u) {                   // (kkt-u)
       const size_t tu = t - rows_x;
       const int i = (int)(tu / m), r = (int)(tu - (size_t)i * m);
-      if (i == a.root) { a.res_u[tu] = 0.0; continue; }
+      if (a.parent[i] < 0) { a.res_u[tu] = 0.0; continue; }
       const int p = a.parent[i];
       const size_t xo = (size_t)p * n, uo = (size_t)i * m, yo = (size_t)i * n;
       const double* Bc = a.B + (size_t)i * nm + r;
@@ -376,7 +376,7 @@ __global__ void k_residual_ff(ResidualArgs a, FFArgs f) {
           if (ks) rs += ad;
         }
       }
-      if (i != a.root) {
+      if (a.parent[i] >= 0) {
         const int p = a.parent[i];
         const size_t xo = (size_t)p * n, uo = (size_t)i * m;
         const double* Ar = a.A + (size_t)i * nn + (size_t)r * n;

@@ -237,7 +237,7 @@ struct tlqr_factor_t {
   Ws<T> ws(const tlqr_problem& p) const {
     Ws<T> w{};
     const tlqr_plan_t* P = plan;
-    w.N = P->N; w.n = opt.n; w.m = opt.m; w.root = P->root;
+    w.N = P->N; w.n = opt.n; w.m = opt.m;
     w.has_M = opt.has_M; w.has_delta = opt.has_delta;
     w.Q = p.Q; w.M = p.M; w.R = p.R; w.A = p.A; w.B = p.B; w.Delta = p.Delta;
     w.q = p.q; w.r = p.r; w.c = p.c;
@@ -572,7 +572,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
                          const double* u, const double* y, int with_knorm, cudaStream_t st, int ff = 0) {
   ResidualArgs a{};
   const tlqr_plan_t* P = f->plan;
-  a.N = P->N; a.n = f->opt.n; a.m = f->opt.m; a.root = P->root; a.with_knorm = with_knorm;
+  a.N = P->N; a.n = f->opt.n; a.m = f->opt.m; a.with_knorm = with_knorm;
   a.parent = f->dp.parent; a.child_start = f->dp.child_start; a.child_list = f->dp.child_list;
   a.Q = p.Q; a.q = p.q; a.M = f->opt.has_M ? p.M : nullptr; a.R = p.R; a.r = p.r; a.A = p.A;
   a.B = p.B; a.c = p.c; a.Delta = f->opt.has_delta ? p.Delta : nullptr;
@@ -1029,10 +1029,10 @@ int get_PK_impl(tlqr_factor_t* f, int32_t mem, double* P, double* K, cudaStream_
   }
   const int blocks = 4 * 148;
   if (f->ts == 8)
-    k_export_PK<double><<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, f->plan->root, (const double*)f->U,
+    k_export_PK<double><<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, (const int*)f->dp.parent, (const double*)f->U,
                                                 (const double*)f->K, dP, dK);
   else
-    k_export_PK<float><<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, f->plan->root, (const float*)f->U,
+    k_export_PK<float><<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, (const int*)f->dp.parent, (const float*)f->U,
                                                (const float*)f->K, dP, dK);
   if (cudaGetLastError()) return TLQR_ERR_CUDA;
   f->prof.launches[TLQR_K_EXPORT]++;
@@ -1161,7 +1161,7 @@ int batched_ops(int kind, int count, int n, int m, const double* const* in, doub
     return p;
   };
   Ws<T> w{};
-  w.N = count; w.n = n; w.m = m; w.root = -1;
+  w.N = count; w.n = n; w.m = m;
   T *U = (T*)take(S * nn, sizeof(T)), *Ea = (T*)take(S * nn, sizeof(T)), *Ec = (T*)take(S * nn, sizeof(T)),
     *Ep = (T*)take(S * nn, sizeof(T)), *contrib = (T*)take(count * nn, sizeof(T));
   int* idx = (int*)take(S, sizeof(int));

@@ -380,3 +380,41 @@ def spine_hybrid(seed: int = BASE_SEED + 3, N: int = 1 << 20, spine: int = 1 << 
     parent = spine_hybrid_tree(rng, N=N, spine=spine)
     data = problem_data(parent, n, m, rng, kappa_R=kappa_R)
     return Workload(f"spine_hybrid_N{N}_n{n}_m{m}_kR{kappa_R:g}", parent, n, m, data)
+
+
+def forest(parents, rng: np.random.Generator | None = None):
+    """Concatenate trees into one forest parent array (labels offset tree by
+    tree; optionally a random relabelling of the whole forest).  Returns
+    (parent, offsets) with offsets[t] = first label of tree t before relabelling."""
+    offs, out, base = [], [], 0
+    for p in parents:
+        p = np.asarray(p, dtype=np.int64)
+        offs.append(base)
+        out.append(np.where(p < 0, -1, p + base))
+        base += len(p)
+    par = np.concatenate(out).astype(np.int32)
+    return par, np.asarray(offs)
+
+
+def concat_data(datas: list) -> dict:
+    """Concatenate per-tree problem data in forest order."""
+    out = {}
+    for k in datas[0]:
+        if datas[0][k] is None:
+            out[k] = None
+        else:
+            out[k] = np.ascontiguousarray(np.concatenate([d[k] for d in datas]))
+    return out
+
+
+def recursive_batch(seed: int = BASE_SEED + 2, count: int = 1024, n: int = 16, m: int = 4,
+                    lo: int = 64, hi: int = 16384) -> Workload:
+    """Batch of random recursive trees (node k attaches to a uniform earlier
+    node), sizes log-uniform in [lo, hi], solved together as one forest."""
+    rng = rng_for(seed)
+    sizes = recursive_batch_sizes(rng, count, lo, hi)
+    parents = [random_recursive(int(N), rng) for N in sizes]
+    par, offs = forest(parents)
+    data = problem_data(par, n, m, rng)
+    return Workload(f"recursive_batch_{count}x_n{n}_m{m}", par, n, m, data,
+                    info=dict(sizes=sizes, offsets=offs))

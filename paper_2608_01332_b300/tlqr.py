@@ -54,7 +54,7 @@ class tlqr_solution(ctypes.Structure):
 
 class tlqr_plan_stats_t(ctypes.Structure):
     _fields_ = [(k, _i32) for k in ("N", "root", "rounds", "n_rake", "n_compress", "n_combine",
-                                    "n_absorb", "levels", "height", "max_degree")]
+                                    "n_absorb", "levels", "height", "max_degree", "n_trees")]
 
 
 class tlqr_kernel_profile(ctypes.Structure):
@@ -67,7 +67,7 @@ class tlqr_info(ctypes.Structure):
 
 
 _lib = None
-EXPORTS = ["tlqr_plan_create", "tlqr_plan_destroy", "tlqr_plan_stats", "tlqr_plan_schedule",
+EXPORTS = ["tlqr_plan_create", "tlqr_plan_create_forest", "tlqr_plan_destroy", "tlqr_plan_stats", "tlqr_plan_schedule",
            "tlqr_factor_create", "tlqr_factor_destroy", "tlqr_factor", "tlqr_solve_rhs", "tlqr_solve",
            "tlqr_get_PK", "tlqr_kkt_residual", "tlqr_last_info", "tlqr_status_string",
            "tlqr_batched_tau", "tlqr_batched_compose", "tlqr_batched_condense",
@@ -93,6 +93,7 @@ def lib():
         L.tlqr_status_string.restype = ctypes.c_char_p
         L.tlqr_status_string.argtypes = [ctypes.c_int]
         L.tlqr_plan_create.argtypes = [_ip, _i32, ctypes.POINTER(_vp)]
+        L.tlqr_plan_create_forest.argtypes = [_ip, _i32, ctypes.POINTER(_vp)]
         L.tlqr_plan_destroy.argtypes = [_vp]
         L.tlqr_plan_destroy.restype = None
         L.tlqr_plan_stats.argtypes = [_vp, ctypes.POINTER(tlqr_plan_stats_t)]
@@ -184,6 +185,13 @@ def tlqr_plan_create(parent) -> ctypes.c_void_p:
     parent = np.ascontiguousarray(parent, dtype=np.int32)
     h = _vp()
     _check(lib().tlqr_plan_create(_iptr(parent), len(parent), ctypes.byref(h)), "tlqr_plan_create")
+    return h
+
+
+def tlqr_plan_create_forest(parent) -> ctypes.c_void_p:
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    h = _vp()
+    _check(lib().tlqr_plan_create_forest(_iptr(parent), len(parent), ctypes.byref(h)), "tlqr_plan_create_forest")
     return h
 
 
@@ -363,10 +371,10 @@ def tlqr_project_lifted(N: int, n: int, m: int, lmap, lx, lu, ly):
 class TreeLQR:
     """Owns one plan and one factor object; every method is a direct C call."""
 
-    def __init__(self, parent, n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, **kw):
+    def __init__(self, parent, n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, forest=False, **kw):
         self.parent = np.ascontiguousarray(parent, dtype=np.int32)
         self.N, self.n, self.m = len(self.parent), int(n), int(m)
-        self.plan = tlqr_plan_create(self.parent)
+        self.plan = tlqr_plan_create_forest(self.parent) if forest else tlqr_plan_create(self.parent)
         self.opts = make_options(n, m, precision, has_M, has_delta, **kw)
         try:
             self.f = tlqr_factor_create(self.plan, self.opts)

@@ -128,3 +128,23 @@ def test_lifting_is_exact_through_the_oracle(seed, delta):
     # dummy controls of the uncertainty edges (children that are predecision nodes) are zero
     dummies = [j for j in range(len(p)) if p[j] >= 0]
     assert np.abs(sol["u"][dummies]).max() <= 1e-12 * scale
+
+
+def test_forest_planner_equals_schedule_oracle():
+    rng = inputs.rng_for(43)
+    trees = [inputs.random_recursive(int(rng.integers(1, 300)), rng) for _ in range(8)]
+    par, _ = inputs.forest(trees)
+    par, _ = inputs.permute_labels(par, rng)      # relabelling handles several roots
+    h = tlqr.tlqr_plan_create_forest(par)
+    try:
+        rnd, op = tlqr.tlqr_plan_schedule(h, len(par))
+        ops = oplan.node_ops(par)
+        assert [int(r) for r in rnd] == [ops[i][0] for i in range(len(par))]
+        assert [int(o) for o in op] == [OPCODE[ops[i][1]] for i in range(len(par))]
+        st = tlqr.tlqr_plan_stats(h)
+        assert st["n_trees"] == len(trees)
+        assert st["n_rake"] + st["n_compress"] == len(par) - len(trees)
+    finally:
+        tlqr.tlqr_plan_destroy(h)
+    with pytest.raises(tlqr.TLQRError):
+        tlqr.tlqr_plan_create(par)          # the single-tree entry point refuses several roots

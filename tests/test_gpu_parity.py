@@ -393,3 +393,31 @@ def test_fixed_and_runtime_dimension_kernels(n, m, generic):
     outm = gpu_solve(p, n, m, d, precision=MIXED, want_PK=False, generic_kernels=generic)
     assert outm["info"]["eta"] <= 1e-8
     check_against_oracle(p, n, m, d, outm, fwd_tol=1e-6, eta_tol=1e-8)
+
+
+# -------------------------------------------------------------------- batches (forests)
+
+@pytest.mark.parametrize("n,m", [(4, 2), (12, 4), (5, 3)])
+def test_forest_batch_equals_trees_alone(n, m):
+    """A batch of independent trees solved as one forest: in FP64 every tree's
+    x, u, y, P, K are bitwise those of the tree solved alone (same schedule, same
+    per-operation arithmetic); all match the oracle.  In mixed precision each
+    tree meets eta <= 1e-8 (the batch may take an extra refinement step)."""
+    rng = inputs.rng_for(700 + n)
+    trees = [inputs.random_recursive(int(rng.integers(1, 900)), rng) for _ in range(9)] + [inputs.chain(700)]
+    datas = [inputs.problem_data(p, n, m, rng, delta="subset", delta_value=0.05, delta_fraction=0.3) for p in trees]
+    par, offs = inputs.forest(trees)
+    data = inputs.concat_data(datas)
+    batch = gpu_solve(par, n, m, data, forest=True)
+    check_against_oracle(par, n, m, data, batch, fwd_tol=1e-8, eta_tol=1e-10, pk_tol=1e-8)
+    for t, p in enumerate(trees):
+        alone = gpu_solve(p, n, m, datas[t])
+        sl = slice(offs[t], offs[t] + len(p))
+        for k in ("x", "u", "y", "P", "K"):
+            np.testing.assert_array_equal(batch[k][sl], alone[k])
+    mixed = gpu_solve(par, n, m, data, precision=MIXED, want_PK=False, forest=True)
+    for t, p in enumerate(trees):
+        sl = slice(offs[t], offs[t] + len(p))
+        sub = {k: mixed[k][sl] for k in ("x", "u", "y")}
+        res = riccati.kkt_residual(p, n, m, datas[t], sub["x"], sub["u"], sub["y"])
+        assert res["eta"] <= 1e-8

@@ -169,7 +169,28 @@ def test_oracle_rejects_bad_topology():
     with pytest.raises(RuntimeError):
         riccati.tree_riccati(np.array([-1, 2, 1], dtype=np.int32), 2, 1, d)   # cycle 1<->2
     with pytest.raises(RuntimeError):
-        riccati.tree_riccati(np.array([-1, -1, 0], dtype=np.int32), 2, 1, d)  # two roots
+        riccati.tree_riccati(np.array([1, 2, 0], dtype=np.int32), 2, 1, d)    # no root
+
+
+def test_forest_is_a_batch_of_independent_trees():
+    """A forest's KKT system is block diagonal: its solution is exactly the
+    independent per-tree solutions (bitwise, same arithmetic per tree) and it
+    matches the dense solve of the whole block system."""
+    rng = inputs.rng_for(41)
+    n, m = 3, 2
+    trees = [inputs.random_recursive(int(rng.integers(2, 15)), rng) for _ in range(4)]
+    datas = [inputs.problem_data(p, n, m, rng, M_scale=0.2, delta="random", delta_value=0.2) for p in trees]
+    par, offs = inputs.forest(trees)
+    data = inputs.concat_data(datas)
+    sol = riccati.tree_riccati(par, n, m, data)
+    for t, p in enumerate(trees):
+        alone = riccati.tree_riccati(p, n, m, datas[t])
+        sl = slice(offs[t], offs[t] + len(p))
+        for k in ("x", "u", "y", "P", "K"):
+            np.testing.assert_array_equal(sol[k][sl], alone[k])
+    ref = dense.dense_solve(par, n, m, data)
+    assert riccati.forward_error(sol, ref, par) < 1e-11
+    assert riccati.kkt_residual(par, n, m, data, sol["x"], sol["u"], sol["y"])["eta"] < 1e-14
 
 
 # ---------------------------------------------------------------- per-op pins

@@ -115,3 +115,16 @@ def test_readiness_reduction_lemma3():
     for k in (2, 3, 5, 8, 15, 16, 17):
         final, _, _ = plan.readiness_reduction([0] * k)
         assert final == math.ceil(math.log2(k))
+
+
+def test_forest_schedule_is_each_trees_own_schedule():
+    """In a forest every tree is contracted by the same rule in the same rounds:
+    a tree's (round, operation) labels are those it gets alone."""
+    rng = inputs.rng_for(42)
+    trees = [inputs.random_recursive(int(rng.integers(1, 200)), rng) for _ in range(6)] + [inputs.chain(50)]
+    par, offs = inputs.forest(trees)
+    ops = plan.node_ops(par)
+    for t, p in enumerate(trees):
+        alone = plan.node_ops(p)
+        for i in range(len(p)):
+            assert ops[offs[t] + i] == alone[i]
