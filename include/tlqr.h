@@ -272,6 +272,13 @@ int tlqr_profile_mask(tlqr_factor_t *f, uint32_t mask);
  * reset all counters.  Host array. */
 int tlqr_profile_read(tlqr_factor_t *f, tlqr_kernel_profile *out);
 
+/* The individual timed launches since the last tlqr_profile_read, in launch
+ * order: kind, operations (warps or groups) and milliseconds.  Writes at most
+ * `max` entries to the host arrays and the total count to *count; call before
+ * tlqr_profile_read, which clears them. */
+int tlqr_profile_launches(tlqr_factor_t *f, int32_t *kind, int64_t *units, double *ms, int32_t max,
+                          int32_t *count);
+
 /* Static name of a status code. */
 const char *tlqr_status_string(int code);
 

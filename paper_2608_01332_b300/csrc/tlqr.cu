@@ -84,7 +84,7 @@ inline int warps_per_block(size_t wbytes) {
 // counts, and CUDA-event pairs around the launches of the kinds in `mask`.
 // When `capture` is set the events are recorded as external event nodes of a
 // CUDA graph (they then fire on every replay).
-struct EvPair { int kind; cudaEvent_t a, b; };
+struct EvPair { int kind; cudaEvent_t a, b; int64_t units = 0; };
 struct Recorder {
   uint32_t mask = 0;
   bool capture = false;
@@ -112,6 +112,8 @@ struct Profiler {
   std::vector<char> pending_owned;
   std::vector<cudaEvent_t> pool;
   bool event_error = false;
+  struct Launch { int kind; int64_t units; double ms; };
+  std::vector<Launch> log;             // harvested timed launches, in launch order
   void add(const Recorder& r, bool owned) {
     for (int k = 0; k < TLQR_K_COUNT; ++k) { launches[k] += r.launches[k]; units[k] += r.units[k]; }
     for (const EvPair& p : r.recs) { pending.push_back(p); pending_owned.push_back(owned); }
@@ -124,6 +126,7 @@ struct Profiler {
       if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&v, p.a, p.b) == cudaSuccess) {
         ms[p.kind] += v;
         timed[p.kind]++;
+        if (log.size() < (1u << 20)) log.push_back(Launch{p.kind, p.units, (double)v});
       } else {
         event_error = true;
         cudaGetLastError();
@@ -153,7 +156,7 @@ cudaError_t launch_warps(Recorder* rc, int kind, Kernel kernel, int count, size_
   }
   const int blocks = (count + wpb - 1) / wpb;
   const bool timed = rc && (rc->mask >> kind) & 1u;
-  EvPair ev{kind, nullptr, nullptr};
+  EvPair ev{kind, nullptr, nullptr, count};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
   kernel<<<blocks, 32 * wpb, smem, st>>>(args...);
   cudaError_t e = cudaGetLastError();
@@ -350,7 +353,7 @@ cudaError_t launch_groups(Recorder* rc, int kind, Kernel kernel, int count, int 
   }
   const int blocks = (count + gpb - 1) / gpb;
   const bool timed = rc && (rc->mask >> kind) & 1u;
-  EvPair ev{kind, nullptr, nullptr};
+  EvPair ev{kind, nullptr, nullptr, count};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
   kernel<<<blocks, threads, smem, st>>>(args...);
   cudaError_t e = cudaGetLastError();
@@ -363,7 +366,7 @@ cudaError_t launch_groups(Recorder* rc, int kind, Kernel kernel, int count, int 
 template <typename Kernel, typename... Args>
 cudaError_t launch_tail(Recorder* rc, int kind, Kernel kernel, cudaStream_t st, Args... args) {
   const bool timed = rc && (rc->mask >> kind) & 1u;
-  EvPair ev{kind, nullptr, nullptr};
+  EvPair ev{kind, nullptr, nullptr, 1};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
   kernel<<<1, kTailThreads, 0, st>>>(args...);
   cudaError_t e = cudaGetLastError();
@@ -604,7 +607,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   const int threads = 256;
   const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 32);
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
-  EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr};
+  EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr, P->N};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
   if (ff) k_residual_ff<<<blocks, threads, 0, st>>>(a, fa);
   else k_residual<<<blocks, threads, 0, st>>>(a);
@@ -1285,5 +1288,20 @@ extern "C" int tlqr_profile_read(tlqr_factor_t* f, tlqr_kernel_profile* out) {
   }
   const bool bad = f->prof.event_error;
   f->prof.event_error = false;
+  f->prof.log.clear();
   return bad ? TLQR_ERR_CUDA : TLQR_OK;
+}
+
+extern "C" int tlqr_profile_launches(tlqr_factor_t* f, int32_t* kind, int64_t* units, double* ms, int32_t max,
+                                     int32_t* count) {
+  if (!f || !count || max < 0) return TLQR_ERR_ARG;
+  f->prof.harvest();
+  const int32_t n = (int32_t)f->prof.log.size();
+  *count = n;
+  for (int32_t t = 0; t < n && t < max; ++t) {
+    if (kind) kind[t] = f->prof.log[t].kind;
+    if (units) units[t] = f->prof.log[t].units;
+    if (ms) ms[t] = f->prof.log[t].ms;
+  }
+  return TLQR_OK;
 }

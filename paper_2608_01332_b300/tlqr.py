@@ -72,7 +72,7 @@ EXPORTS = ["tlqr_plan_create", "tlqr_plan_create_forest", "tlqr_plan_destroy", "
            "tlqr_get_PK", "tlqr_kkt_residual", "tlqr_last_info", "tlqr_status_string",
            "tlqr_batched_tau", "tlqr_batched_compose", "tlqr_batched_condense",
            "tlqr_lift_node_controls", "tlqr_project_lifted", "tlqr_profile_mask", "tlqr_profile_read",
-           "tlqr_kkt_residual_noalloc"]
+           "tlqr_kkt_residual_noalloc", "tlqr_profile_launches"]
 
 KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
                 "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
@@ -114,6 +114,7 @@ def lib():
         L.tlqr_project_lifted.argtypes = [_i32, _i32, _i32, _ip] + [_dp] * 6
         L.tlqr_profile_mask.argtypes = [_vp, ctypes.c_uint32]
         L.tlqr_profile_read.argtypes = [_vp, ctypes.POINTER(tlqr_kernel_profile)]
+        L.tlqr_profile_launches.argtypes = [_vp, _ip, ctypes.POINTER(ctypes.c_int64), _dp, _i32, _ip]
         L.tlqr_kkt_residual_noalloc.argtypes = [_vp, _i32, _i32, ctypes.POINTER(tlqr_problem), _dp, _dp, _dp, _dp, _vp]
         _lib = L
     return _lib
@@ -302,6 +303,18 @@ def tlqr_profile_mask(f, kinds) -> None:
     for k in kinds:
         mask |= 1 << KERNEL_KINDS.index(k)
     _check(lib().tlqr_profile_mask(f, mask), "tlqr_profile_mask")
+
+
+def tlqr_profile_launches(f, max_records: int = 1 << 16):
+    """Timed launches since the last read, in launch order: list of (kind, units, ms)."""
+    kind = np.zeros(max_records, dtype=np.int32)
+    units = np.zeros(max_records, dtype=np.int64)
+    ms = np.zeros(max_records)
+    cnt = _i32(0)
+    _check(lib().tlqr_profile_launches(f, _iptr(kind), units.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       _ptr(ms), max_records, ctypes.byref(cnt)), "tlqr_profile_launches")
+    k = min(cnt.value, max_records)
+    return [(KERNEL_KINDS[kind[t]], int(units[t]), float(ms[t])) for t in range(k)]
 
 
 def tlqr_profile_read(f) -> dict:
