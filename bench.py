@@ -9,6 +9,12 @@ mixed-precision solver at eta <= 1e-8; the plain FP64 contraction on the same
 GPU is measured in the same run for comparison.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode mixed|fp64]
+                    [--workload long_trunk|batch|spine]
+
+The other workloads (a batch of 1,024 random recursive trees solved as one
+forest; the N = 2^20 spine hybrid at n = 32, m = 8) print the same line with
+their own config, a per-round roofline of the factorisation and no e2e leg
+unless asked (their host copies are 15-20 GB).
 
 Multi-GPU (torchrun): the single-tree path has no sharded form here, so every
 rank solves its own replica of the workload (weak scaling, no collective on the
@@ -46,15 +52,181 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--total", type=int, default=65536, help="tree size (default: the benchmark workload)")
+    ap.add_argument("--workload", default="long_trunk", choices=list(WORKLOADS),
+                    help="long_trunk: the headline tree (N=65,536, n=12, m=4); batch: 1,024 random recursive "
+                         "trees (n=16, m=4) solved as one forest; spine: N=2^20 spine hybrid (n=32, m=8)")
+    ap.add_argument("--total", type=int, default=None, help="tree size (default: the workload's own)")
+    ap.add_argument("--count", type=int, default=1024, help="batch: number of trees")
+    ap.add_argument("--kappa", type=float, default=1e2, help="spine: condition number of R")
+    ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests")
+    ap.add_argument("--requests", type=int, default=32, help="serve: requests per arrival rate")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--ref-seconds", type=float, default=180.0,
+                    help="reference arm: CPU seconds for warm-up + timed steps together")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
+    ap.add_argument("--e2e", action="store_true", help="run the end-to-end leg for the 10^6-node workloads too")
     ap.add_argument("--quick", action="store_true",
                     help="time the headline mode only (no FP64 comparison, e2e or CPU legs); for profiler runs")
     return ap.parse_args()
 
 
-def workload(total):
-    return inputs.long_trunk(total=total)
+WORKLOADS = {
+    "long_trunk": "trunk 4,096 + random side branches, N=65,536, n=12, m=4, Delta=1e-6 I on 10% of edges",
+    "serve": "Poisson arrivals of driving-style scenario trees (N in [500, 50000], n=6, m=2), 20 interior-point "
+             "solves per request with fresh data each, continuous batching over slots",
+    "batch": "1,024 random recursive trees, N log-uniform in [64, 16384], n=16, m=4, one forest",
+    "spine": "2^16-node spine + random recursive subtrees of mean size 16, N=2^20, n=32, m=8, kappa(R) swept",
+}
+
+
+# ----------------------------------------------------------------- serving workload
+class ServeTraffic:
+    """Requests of the serving workload: a pool of driving-style topologies
+    (N uniform in [500, 50000]); a request picks one, draws its base data on
+    the device, and each of its solves perturbs the barrier-like diagonal of Q
+    and R and draws a fresh gradient (q, r) -- in place, so that the buffers
+    (and the factor's captured graphs) stay the same across its solves."""
+
+    def __init__(self, device, seed=inputs.BASE_SEED + 4, topologies=16, n=6, m=2, iterations=20,
+                 lo=500, hi=50000):
+        rng = inputs.rng_for(seed)
+        self.device, self.seed, self.n, self.m, self.iterations = device, seed, n, m, iterations
+        self.trees = [inputs.driving_tree(rng, int(rng.integers(lo, hi + 1))) for _ in range(topologies)]
+        self.rng = rng
+
+    def request(self, k, precision, t=None):
+        """Request k (its data are a function of k alone) on topology t (drawn when None)."""
+        import torch
+        from paper_2608_01332_b300 import serve
+        if t is None:
+            t = int(self.rng.integers(len(self.trees)))
+        parent = self.trees[t]
+        base = inputs.problem_data_device(parent, self.n, self.m, self.seed * 1000 + k, self.device)
+        live = {kk: (None if v is None else v.clone()) for kk, v in base.items()}
+        g = torch.Generator(device=self.device)
+        g.manual_seed(self.seed * 7919 + k)
+        N, n, m = len(parent), self.n, self.m
+        nr = torch.from_numpy(parent >= 0).to(self.device)
+
+        def data(it, stream):
+            with torch.cuda.stream(stream):
+                sq = torch.rand((N, n), generator=g, dtype=torch.float64, device=self.device)
+                sr = torch.rand((N, m), generator=g, dtype=torch.float64, device=self.device) * nr[:, None]
+                live["Q"].copy_(base["Q"]).diagonal(dim1=1, dim2=2).add_(sq)
+                live["R"].copy_(base["R"]).diagonal(dim1=1, dim2=2).add_(sr)
+                live["q"].normal_(generator=g)
+                live["r"].normal_(generator=g).mul_(nr[:, None])
+            return live
+        return serve.Request(parent=parent, n=n, m=m, iterations=self.iterations, data=data, precision=precision,
+                             tag=(k, t))
+
+
+def run_serve(args, rank, world, dist):
+    """Closed-loop capacity, then Poisson arrivals at 0.25 ... 1.1 x capacity."""
+    import torch
+    from paper_2608_01332_b300 import serve, tlqr
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = tlqr.TLQR_PREC_MIXED if args.mode == "mixed" else tlqr.TLQR_PREC_FP64
+    traffic = ServeTraffic(dev)
+    slots = args.slots
+    srv = serve.Server(slots=slots)
+    k = 0
+    # warm-up: every topology once (plans, factors, graphs)
+    warm = []
+    for t in range(len(traffic.trees)):
+        r = traffic.request(k, prec)
+        k += 1
+        warm.append(srv.submit(r))
+    srv.drain()
+    # capacity: a closed burst of requests
+    burst = [traffic.request(k + i, prec) for i in range(args.requests)]
+    k += args.requests
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for r in burst:
+        srv.submit(r)
+    srv.drain()
+    span = time.perf_counter() - t0
+    errors = [repr(r.error) for r in warm + burst if r.error is not None]
+    nodes = sum(r.N * r.iterations for r in burst)
+    capacity_rps = len(burst) / span
+    value = nodes / span
+    rates = []
+    for fct in (0.25, 0.5, 0.75, 0.9, 1.1):
+        lam = fct * capacity_rps
+        reqs = [traffic.request(k + i, prec) for i in range(args.requests)]
+        k += args.requests
+        gaps = traffic.rng.exponential(1.0 / lam, size=len(reqs))
+        torch.cuda.synchronize(dev)
+        t_start = time.perf_counter()
+        at = t_start
+        for r, gap in zip(reqs, gaps):
+            at += gap
+            now = time.perf_counter()
+            if at > now:
+                time.sleep(at - now)
+            srv.submit(r, arrival=at)
+        srv.drain()
+        t_end = max(r.finished for r in reqs)
+        errors += [repr(r.error) for r in reqs if r.error is not None]
+        summ = serve.latency_summary(reqs)
+        summ.update({"rate_factor": fct, "rate_rps": lam,
+                     "throughput_nodes_s": sum(r.N * r.iterations for r in reqs) / (t_end - t_start),
+                     "max_eta": max((i["eta"] for r in reqs for i in r.infos), default=None)})
+        rates.append(summ)
+    stats = dict(srv.stats)
+    peak = srv.peak
+    srv.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": len(burst),
+        "warmup": len(warm), "ms_per_step": 1e3 * span / len(burst), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == tlqr.TLQR_PREC_MIXED else "f64",
+        "data": "synthetic (seeded; drawn on the device)",
+        "config": {"workload": "serve_driving_trees_n6_m2", "description": WORKLOADS["serve"], "slots": slots,
+                   "requests_per_rate": args.requests, "iterations_per_request": traffic.iterations,
+                   "topologies": len(traffic.trees), "precision": args.mode,
+                   "step": "one request (20 solves, each factor + solve + refinement to eta <= 1e-8)"},
+        "capacity_rps": capacity_rps, "burst_latency": serve.latency_summary(burst),
+        "serving": rates, "server_stats": stats, "peak_admitted_bytes": peak, "errors": errors[:5],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload(args, device=None):
+    """(Workload, forest?) -- host numpy data for the headline tree, device data
+    (drawn on the GPU) for the 10^6-node workloads."""
+    if args.workload == "long_trunk":
+        return inputs.long_trunk(total=args.total or 65536), False
+    if args.workload == "serve":                    # the oracle's view: the topology pool as one batch
+        rng = inputs.rng_for(inputs.BASE_SEED + 4)
+        trees = [inputs.driving_tree(rng, int(rng.integers(500, 50001))) for _ in range(16)]
+        par, offs = inputs.forest(trees)
+        return inputs.Workload("serve_driving_trees_n6_m2", par, 6, 2, inputs.problem_data(par, 6, 2, rng),
+                               info=dict(offsets=offs)), True
+    if device is None:
+        import torch
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    if args.workload == "batch":
+        return inputs.recursive_batch_device(device, count=args.count), True
+    return inputs.spine_hybrid_device(device, N=args.total or (1 << 20), kappa_R=args.kappa), False
+
+
+def host_slice(w, a, b):
+    """Problem data of nodes [a, b) as host numpy arrays."""
+    out = {}
+    for k, v in w.data.items():
+        if v is None:
+            out[k] = None
+        elif isinstance(v, np.ndarray):
+            out[k] = np.ascontiguousarray(v[a:b])
+        else:
+            out[k] = v[a:b].cpu().numpy()
+    return out
 
 
 def load_peaks():
@@ -178,62 +350,180 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle legs
-def oracle_leg(w, budget_s=12.0, min_reps=1, max_reps=50):
-    """Time the FP64 oracle (single thread) on the full workload for about budget_s."""
+def oracle_units(w, forest):
+    """Independent pieces the oracle can time: whole trees of a batch, else the
+    tree itself (a prefix of the labels when it is too large; every parent label
+    is below its child's, so a prefix is a connected subtree)."""
+    if forest:
+        offs = [int(v) for v in w.info["offsets"]] + [len(w.parent)]
+        return [(offs[t], offs[t + 1]) for t in range(len(offs) - 1)]
+    return [(0, len(w.parent))]
+
+
+def oracle_leg(w, forest, budget_s=12.0, max_reps=50):
+    """Time the FP64 oracle (single thread) for about budget_s on the workload:
+    the full tree (repeated), consecutive trees of a batch, or a prefix of a tree
+    too large for the budget.  Returns (nodes/s, description, solution of the
+    full tree or None)."""
     from oracle import riccati
     riccati.build()
-    times = []
-    sol = None
-    t_start = time.perf_counter()
-    while len(times) < max_reps and (len(times) < min_reps or time.perf_counter() - t_start < budget_s):
+    units = oracle_units(w, forest)
+    N = len(w.parent)
+    if not forest and N > 200_000:                      # too large: a timed prefix
+        probe = 4096
+        d = host_slice(w, 0, probe)
         t0 = time.perf_counter()
-        sol = riccati.tree_riccati(w.parent, w.n, w.m, w.data)
-        times.append(time.perf_counter() - t0)
-    return times, sol
+        riccati.tree_riccati(w.parent[:probe], w.n, w.m, d)
+        per_node = (time.perf_counter() - t0) / probe
+        k = int(min(N, max(probe, budget_s / 2 / per_node)))
+        d = host_slice(w, 0, k)
+        times = []
+        t_start = time.perf_counter()
+        while len(times) < 2 and (not times or time.perf_counter() - t_start < budget_s):
+            t0 = time.perf_counter()
+            riccati.tree_riccati(w.parent[:k], w.n, w.m, d)
+            times.append(time.perf_counter() - t0)
+        return k / float(np.median(times)), f"prefix of {k} of {N} nodes (labels 0..{k - 1}) x {len(times)}", None
+    nodes, secs, sol, done = 0, 0.0, None, 0
+    t_start = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t_start < budget_s and reps < max_reps:
+        for a, b in units:
+            p = w.parent[a:b] - np.where(w.parent[a:b] >= 0, a, 0)
+            d = host_slice(w, a, b)
+            t0 = time.perf_counter()
+            out = riccati.tree_riccati(p.astype(np.int32), w.n, w.m, d)
+            secs += time.perf_counter() - t0
+            nodes += b - a
+            done += 1
+            if len(units) == 1:
+                sol = out
+            if time.perf_counter() - t_start > budget_s:
+                break
+        reps += 1
+    if forest:
+        desc = f"{done} trees of the batch ({nodes} nodes), one at a time"
+    else:
+        desc = f"full workload ({N} nodes) x {reps} runs"
+    return nodes / secs, desc, sol
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    w = workload(args.total)
+    w, forest = workload(args)
     N = len(w.parent)
     steps, warm = args.steps, args.warmup
     from oracle import riccati
     riccati.build()
-    # each step is the full tree unless that would exceed ~3 minutes in total
-    est = None
+    units = oracle_units(w, forest)
+    # one step = the oracle over a bounded sample of the workload, sized so
+    # that warm-up + timed steps take about three minutes in total
+    a0, b0 = units[0]
+    probe_b = min(b0, a0 + 4096)
+    p = (w.parent[a0:probe_b] - np.where(w.parent[a0:probe_b] >= 0, a0, 0)).astype(np.int32)
+    d = host_slice(w, a0, probe_b)
     t0 = time.perf_counter()
-    riccati.tree_riccati(w.parent, w.n, w.m, w.data)
-    est = time.perf_counter() - t0
-    sub = N
-    if est * (steps + warm) > 180:
-        sub = max(1024, int(N * 180 / (est * (steps + warm))))
-    wp = w
-    if sub < N:      # breadth-first prefix of the tree: a connected subtree
-        keep = np.arange(sub)
-        wp = inputs.Workload(w.name + f"_prefix{sub}", w.parent[:sub].copy(), w.n, w.m,
-                             {k: (None if v is None else v[:sub].copy()) for k, v in w.data.items()})
+    riccati.tree_riccati(p, w.n, w.m, d)
+    per_node = (time.perf_counter() - t0) / (probe_b - a0)
+    budget_nodes = max(256, int(args.ref_seconds / (steps + warm) / per_node))
+    sample = []
+    tot = 0
+    for a, b in units:
+        if tot >= budget_nodes:
+            break
+        b = min(b, a + budget_nodes - tot)     # a label prefix of a tree is a subtree
+        pp = (w.parent[a:b] - np.where(w.parent[a:b] >= 0, a, 0)).astype(np.int32)
+        sample.append((pp, host_slice(w, a, b)))
+        tot += int(b - a)
     for _ in range(warm):
-        riccati.tree_riccati(wp.parent, wp.n, wp.m, wp.data)
+        for pp, dd in sample:
+            riccati.tree_riccati(pp, w.n, w.m, dd)
     ts = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        riccati.tree_riccati(wp.parent, wp.n, wp.m, wp.data)
+        for pp, dd in sample:
+            riccati.tree_riccati(pp, w.n, w.m, dd)
         ts.append(time.perf_counter() - t0)
-    tot = sum(ts)
-    value = len(wp.parent) * steps / tot
+    total_s = sum(ts)
+    value = tot * steps / total_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": args.gpus,
-        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * tot / steps, "higher_is_better": True,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * total_s / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "N": N, "n": w.n, "m": w.m, "sample_nodes": len(wp.parent)},
+        "config": {"workload": w.name, "N": N, "n": w.n, "m": w.m, "sample_nodes": tot},
         "p50_ms": 1e3 * float(np.percentile(ts, 50)), "p99_ms": 1e3 * float(np.percentile(ts, 99)),
         "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{len(wp.parent)} of {N} nodes per step, single-threaded C FP64 "
-                                   f"sequential tree Riccati"},
+                         "sample": f"{tot} of {N} nodes per step ({len(sample)} tree(s) or label prefixes), "
+                                   f"single-threaded C FP64 sequential tree Riccati"},
         "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- per-round roofline
+ROUND_KINDS = ("rake", "absorb", "compress", "expand", "compose_T")
+
+
+def round_roofline(launches, rnd, op, n, m, wbytes, hbm_gbs, alu_tflops, rake_code, comp_code):
+    """Per structural round of the factorisation: algorithmic flops and bytes of
+    its rake, absorb and compress launches (and of the reverse expansion and
+    T-composite launches of the same round), the measured time, and the
+    roofline time max(bytes / HBM, flops / ALU peak)."""
+    R = int(rnd.max()) if len(rnd) else 0
+    nr = np.bincount(rnd[op == rake_code], minlength=R + 1)
+    nc = np.bincount(rnd[op == comp_code], minlength=R + 1)
+    by_kind = {k: [rec for rec in launches if rec[0] == k] for k in ROUND_KINDS}
+    it = {k: iter(v) for k, v in by_kind.items()}
+    s = n * (n + 1) / 2
+    rows = {r: dict(round=r, rakes=int(nr[r]), compresses=int(nc[r]), flops=0.0, bytes=0.0, ms=0.0)
+            for r in range(1, R + 1)}
+
+    def take(kind, r, units_expected=None):
+        rec = next(it[kind], None)
+        if rec is None:
+            return None
+        _, units, ms = rec
+        if units_expected is not None and units != units_expected:
+            raise RuntimeError(f"round {r}: {kind} launch of {units} operations, plan has {units_expected}")
+        return units, ms
+
+    def add(r, kind, units, ms, n_contrib=0):
+        if kind == "absorb":                       # sum contributions into U_i: reads nr + 2 ns packed blocks
+            fl, by = n * n * n_contrib, (n_contrib + 2 * units) * s * wbytes
+        else:
+            fl1, by1 = per_unit(kind, n, m, wbytes)
+            fl, by = fl1 * units, by1 * units
+        rows[r]["flops"] += fl
+        rows[r]["bytes"] += by
+        rows[r]["ms"] += ms
+
+    for r in range(1, R + 1):                       # launch order of the forward rounds
+        if nr[r]:
+            u, ms = take("rake", r, int(nr[r]))
+            add(r, "rake", u, ms)
+            u, ms = take("absorb", r)
+            add(r, "absorb", u, ms, int(nr[r]))
+        if nc[r]:
+            u, ms = take("compress", r, int(nc[r]))
+            add(r, "compress", u, ms)
+    for r in range(R, 0, -1):                       # reverse expansion
+        if nc[r]:
+            u, ms = take("expand", r, int(nc[r]))
+            add(r, "expand", u, ms)
+    for r in range(1, R + 1):                       # T composites of the compressions
+        if nc[r]:
+            u, ms = take("compose_T", r, int(nc[r]))
+            add(r, "compose_T", u, ms)
+    out = []
+    for r in range(1, R + 1):
+        row = rows[r]
+        t_roof = max(row["bytes"] / (hbm_gbs * 1e9), row["flops"] / (alu_tflops * 1e12))
+        row["roof_ms"] = 1e3 * t_roof
+        row["frac"] = (1e3 * t_roof / row["ms"]) if row["ms"] > 0 else None
+        row["bound"] = "hbm" if row["bytes"] / (hbm_gbs * 1e9) >= row["flops"] / (alu_tflops * 1e12) else "alu"
+        out.append(row)
+    return out
 
 
 # ----------------------------------------------------------------- our arm
@@ -244,12 +534,13 @@ def run_ours(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload(args.total)
+    w, forest = workload(args, dev)
     N, n, m = len(w.parent), w.n, w.m
     mixed = args.mode == "mixed"
     prec = tlqr.TLQR_PREC_MIXED if mixed else tlqr.TLQR_PREC_FP64
     has_delta = w.data["Delta"] is not None
-    dd = {k: (None if v is None else torch.from_numpy(v).to(dev)) for k, v in w.data.items()}
+    dd = {k: (None if v is None else (torch.from_numpy(v).to(dev) if isinstance(v, np.ndarray) else v))
+          for k, v in w.data.items()}
     x = torch.zeros((N, n), dtype=torch.float64, device=dev)
     u = torch.zeros((N, m), dtype=torch.float64, device=dev)
     y = torch.zeros((N, n), dtype=torch.float64, device=dev)
@@ -261,17 +552,17 @@ def run_ours(args, rank, world, dist):
         if dist is not None:
             dist.barrier()
 
-    def timed_steps(solver, K, profile_kinds=()):
+    def timed(solver, K, call, profile_kinds=()):
         tlqr.tlqr_profile_mask(solver.f, profile_kinds)
-        tlqr.tlqr_solve(solver.f, dd, x, u, y, stream=stream)   # (re)capture graphs outside the timing
-        tlqr.tlqr_profile_read(solver.f)                     # reset counters
+        call()                                       # (re)capture graphs outside the timing
+        tlqr.tlqr_profile_read(solver.f)             # reset counters
         ts = []
         barrier()
         for _ in range(K):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            tlqr.tlqr_solve(solver.f, dd, x, u, y, stream=stream)
+            call()
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
@@ -279,15 +570,19 @@ def run_ours(args, rank, world, dist):
         tlqr.tlqr_profile_mask(solver.f, ())
         return ts, tlqr.tlqr_profile_read(solver.f)
 
-    solver = tlqr.TreeLQR(w.parent, n, m, prec, has_delta=has_delta)
+    solver = tlqr.TreeLQR(w.parent, n, m, prec, has_delta=has_delta, forest=forest)
     stats = solver.stats()
+
+    def solve():
+        tlqr.tlqr_solve(solver.f, dd, x, u, y, stream=stream)
+
     # warm-up, and one fully profiled step to find the dominant kernel
     for _ in range(max(3, args.warmup)):
-        tlqr.tlqr_solve(solver.f, dd, x, u, y, stream=stream)
-    _, prof_all = timed_steps(solver, 1, tlqr.KERNEL_KINDS)
+        solve()
+    _, prof_all = timed(solver, 1, solve, tlqr.KERNEL_KINDS)
     dominant = max(prof_all, key=lambda k: prof_all[k]["ms"])
     with ClockSampler(local) as clk:
-        ts, prof = timed_steps(solver, args.steps, (dominant,))
+        ts, prof = timed(solver, args.steps, solve, (dominant,))
     info = tlqr.tlqr_last_info(solver.f)
     tot_ms = sum(ts)
     if dist is not None:
@@ -297,63 +592,97 @@ def run_ours(args, rank, world, dist):
     ms_per_step = tot_ms / args.steps
     value = world * N / (ms_per_step / 1e3)
     gpu_launches = int(sum(p["launches"] for p in prof.values()))
-    # accuracy of the last timed solution
+    # accuracy of the last timed solution (per tree for a batch)
     res = tlqr.tlqr_kkt_residual(solver.f, dd, x, u, y)
-    sol_dev = dict(x=x.cpu().numpy(), u=u.cpu().numpy(), y=y.cpu().numpy())
+    tree_eta = tlqr.tlqr_tree_residuals(solver.f, stats["n_trees"])[1]
 
-    # plain FP64 contraction on the same GPU (the comparison of the metric)
-    fp64 = None
-    if mixed and not args.quick:
-        s64 = tlqr.TreeLQR(w.parent, n, m, tlqr.TLQR_PREC_FP64, has_delta=has_delta)
-        for _ in range(2):
-            tlqr.tlqr_solve(s64.f, dd, x, u, y, stream=stream)
-        ts64, _ = timed_steps(s64, max(3, min(args.steps, 10)))
-        r64 = tlqr.tlqr_kkt_residual(s64.f, dd, x, u, y)
-        ms64 = sum(ts64) / len(ts64)
-        fp64 = {"value": N / (ms64 / 1e3), "unit": "nodes/s", "ms_per_step": ms64, "eta": r64["eta"],
-                "p50_ms": float(np.percentile(ts64, 50)), "p99_ms": float(np.percentile(ts64, 99))}
-        s64.close()
-
-    # end to end through the public API with pinned host buffers
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "nodes/s", "ms_per_step": ms_per_step,
-                              "steps": args.steps, "eta": res["eta"], "quick": True,
+                              "steps": args.steps, "eta": res["eta"], "quick": True, "workload": w.name,
                               "kernel_ms_per_step": {k: v["ms"] for k, v in prof_all.items() if v["ms"] > 0}}),
                   flush=True)
         solver.close()
         return
-    hd = {k: (None if v is None else torch.from_numpy(v).pin_memory()) for k, v in w.data.items()}
-    hx = torch.zeros((N, n), dtype=torch.float64).pin_memory()
-    hu = torch.zeros((N, m), dtype=torch.float64).pin_memory()
-    hy = torch.zeros((N, n), dtype=torch.float64).pin_memory()
-    tlqr.tlqr_solve(solver.f, hd, hx, hu, hy, stream=stream)
-    h2d = sum(v.numel() * 8 for v in hd.values() if v is not None)
-    d2h = (hx.numel() + hu.numel() + hy.numel()) * 8
-    barrier()
-    e2e_t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
+    sol_dev = dict(x=x.cpu().numpy(), u=u.cpu().numpy(), y=y.cpu().numpy()) if N <= 200_000 else None
+
+    # factor and solve separately (factor; one FP32/FP64 pass through the factors, no refinement)
+    K_split = max(3, min(args.steps, 20))
+    ts_f, _ = timed(solver, K_split, lambda: tlqr.tlqr_factor(solver.f, dd, stream=stream))
+    xs, us, ys = torch.empty_like(x), torch.empty_like(u), torch.empty_like(y)
+    ts_s, _ = timed(solver, K_split, lambda: tlqr.tlqr_solve_rhs(solver.f, dd["q"], dd["r"], dd["c"], xs, us, ys,
+                                                                  stream=stream))
+    split = {"factor_ms": float(np.median(ts_f)), "solve_rhs_ms": float(np.median(ts_s)),
+             "note": "medians; solve_rhs = one pass through the factors without refinement"}
+
+    # per-round roofline of the factorisation (one profiled step, launches timed one by one)
+    wbytes = 4 if mixed else 8
+    hbm, hbm_src = load_peaks()
+    alu = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    solve()
+    tlqr.tlqr_profile_mask(solver.f, ROUND_KINDS)
+    solve()
+    solve()
+    torch.cuda.synchronize(dev)
+    launches = tlqr.tlqr_profile_launches(solver.f)
+    tlqr.tlqr_profile_mask(solver.f, ())
+    tlqr.tlqr_profile_read(solver.f)
+    rnd, op = tlqr.tlqr_plan_schedule(solver.plan, N)
+    per_round = None
+    try:
+        half = len(launches) // 2                  # two identical steps were recorded: keep the second
+        per_round = round_roofline(launches[half:], rnd, op, n, m, wbytes, hbm, alu,
+                                   tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)
+    except (RuntimeError, StopIteration, TypeError) as e:
+        per_round = {"error": str(e)}
+
+    # plain FP64 contraction on the same GPU (the comparison of the metric)
+    fp64 = None
+    if mixed:
+        s64 = tlqr.TreeLQR(w.parent, n, m, tlqr.TLQR_PREC_FP64, has_delta=has_delta, forest=forest)
+        call64 = lambda: tlqr.tlqr_solve(s64.f, dd, x, u, y, stream=stream)  # noqa: E731
+        for _ in range(2):
+            call64()
+        ts64, _ = timed(s64, max(3, min(args.steps, 10)), call64)
+        r64 = tlqr.tlqr_kkt_residual(s64.f, dd, x, u, y)
+        ms64 = sum(ts64) / len(ts64)
+        fp64 = {"value": world * N / (ms64 / 1e3), "unit": "nodes/s", "ms_per_step": ms64, "eta": r64["eta"],
+                "p50_ms": float(np.percentile(ts64, 50)), "p99_ms": float(np.percentile(ts64, 99))}
+        s64.close()
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e and (args.workload == "long_trunk" or args.e2e):
+        hd = {k: (None if v is None else v.cpu().pin_memory()) for k, v in dd.items()}
+        hx = torch.zeros((N, n), dtype=torch.float64).pin_memory()
+        hu = torch.zeros((N, m), dtype=torch.float64).pin_memory()
+        hy = torch.zeros((N, n), dtype=torch.float64).pin_memory()
         tlqr.tlqr_solve(solver.f, hd, hx, hu, hy, stream=stream)
-        e2e_t.append(time.perf_counter() - t0)
-    barrier()
-    e2e_tot = sum(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = world * N * args.steps / e2e_tot
+        h2d = sum(v.numel() * 8 for v in hd.values() if v is not None)
+        d2h = (hx.numel() + hu.numel() + hy.numel()) * 8
+        barrier()
+        e2e_t = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            tlqr.tlqr_solve(solver.f, hd, hx, hu, hy, stream=stream)
+            e2e_t.append(time.perf_counter() - t0)
+        barrier()
+        e2e_tot = sum(e2e_t)
+        if dist is not None:
+            t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_tot = float(t.item())
+        e2e = {"value": world * N * args.steps / e2e_tot, "unit": "nodes/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     if rank != 0:
         solver.close()
         return
     # roofline of the dominant kernel
-    wbytes = 4 if mixed else 8
-    dfrac = float((w.data["Delta"].reshape(N, -1) != 0).any(axis=1).mean()) if has_delta else 0.0
+    dfrac = float((dd["Delta"].reshape(N, -1) != 0).any(dim=1).double().mean()) if has_delta else 0.0
     fl, by = per_unit(dominant, n, m, wbytes, dfrac)
     pd = prof[dominant]
     roof = None
-    hbm, hbm_src = load_peaks()
     if fl is not None and pd["timed"] > 0 and pd["ms"] > 0:
         sec = pd["ms"] / 1e3
         flops = fl * pd["units"] / sec
@@ -373,30 +702,45 @@ def run_ours(args, rank, world, dist):
         roof.update({"kernel": f"k_{dominant}", "launches": pd["timed"], "units": pd["units"],
                      "avg_launch_ms": pd["ms"] / pd["timed"], "flops_per_unit": fl, "bytes_per_unit": by})
 
+    cfg = {"workload": w.name, "N": N, "n": n, "m": m, "precision": args.mode, "rounds": stats["rounds"],
+           "height": stats["height"], "trees": stats["n_trees"], "description": WORKLOADS[args.workload],
+           "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"}
+    if args.workload == "spine":
+        cfg["kappa_R"] = args.kappa
     line = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": w.name, "N": N, "n": n, "m": m, "trunk": 4096, "delta_fraction": 0.1,
-                   "precision": args.mode, "rounds": stats["rounds"], "height": stats["height"],
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+        "data": "synthetic (seeded; host numpy)" if args.workload == "long_trunk"
+        else "synthetic (seeded; drawn on the device)",
+        "config": cfg,
         "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
         "eta": res["eta"], "refine_steps": info["refine_steps"] if mixed else 0,
+        "tree_eta": {"max": float(tree_eta.max()), "p50": float(np.percentile(tree_eta, 50))} if forest else None,
+        "factor_solve": split,
         "plain_fp64": fp64,
-        "e2e": {"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
         "roofline": roof,
         "kernel_ms_per_step": {k: v["ms"] for k, v in prof_all.items() if v["ms"] > 0},
     }
+    if isinstance(per_round, list):
+        tot_meas = sum(r["ms"] for r in per_round)
+        tot_roof = sum(r["roof_ms"] for r in per_round)
+        line["round_roofline"] = {
+            "frac": tot_roof / tot_meas if tot_meas > 0 else None, "measured_ms": tot_meas, "roof_ms": tot_roof,
+            "alu_peak_tflops": alu, "hbm_gbs": hbm,
+            "rounds": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in r.items()} for r in per_round]}
+    else:
+        line["round_roofline"] = per_round
     if not args.no_baseline:
-        times, ref = oracle_leg(w)
-        from oracle import riccati
-        line["cpu_baseline"] = {"value": N / float(np.median(times)), "unit": "nodes/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"full workload ({N} nodes) x {len(times)} runs, single-threaded "
-                                          f"C FP64 sequential tree Riccati, median"}
-        line["forward_error_vs_oracle"] = riccati.forward_error(sol_dev, ref, w.parent)
+        v_cpu, desc, ref = oracle_leg(w, forest)
+        line["cpu_baseline"] = {"value": v_cpu, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+                                "sample": desc + ", single-threaded C FP64 sequential tree Riccati"}
+        if ref is not None and sol_dev is not None:
+            from oracle import riccati
+            line["forward_error_vs_oracle"] = riccati.forward_error(sol_dev, ref, w.parent)
     solver.close()
     print(json.dumps(line), flush=True)
 
@@ -417,6 +761,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, rank)
+        elif args.workload == "serve":
+            run_serve(args, rank, world, dist)
         else:
             run_ours(args, rank, world, dist)
     finally:

@@ -42,6 +42,7 @@
 #ifndef TLQR_H
 #define TLQR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -167,10 +168,20 @@ int tlqr_plan_schedule(const tlqr_plan_t *plan, int32_t *round_of_node, int32_t 
 /* ---------------------------------------------------------------- factor */
 
 /* Allocate the device workspace of a factorisation for this plan and
- * dimensions on the current CUDA device.  The options are copied.  Errors:
- * TLQR_ERR_ARG (dimensions out of range, bad precision), TLQR_ERR_OOM,
- * TLQR_ERR_CUDA. */
+ * dimensions on the current CUDA device: one device allocation holding the
+ * plan's arrays and the workspace, plus a few pinned host words.  The options
+ * are copied; the plan must outlive the factor.  Errors: TLQR_ERR_ARG
+ * (dimensions out of range, bad precision), TLQR_ERR_OOM, TLQR_ERR_CUDA. */
 int tlqr_factor_create(const tlqr_plan_t *plan, const tlqr_options *opts, tlqr_factor_t **out);
+
+/* Device bytes tlqr_factor_create would allocate for this plan and options
+ * (host only, nothing is allocated) -- for admission control by device
+ * memory.  Calls with host-memory problems add a lazily allocated FP64
+ * staging area of the problem's size. */
+int tlqr_factor_workspace_bytes(const tlqr_plan_t *plan, const tlqr_options *opts, size_t *bytes);
+
+/* Device bytes a factor object holds now (workspace + staging, if any). */
+int tlqr_factor_bytes(const tlqr_factor_t *f, size_t *bytes);
 
 /* Free a factor object and its device memory (NULL is ignored). */
 void tlqr_factor_destroy(tlqr_factor_t *f);
@@ -213,7 +224,10 @@ int tlqr_get_PK(tlqr_factor_t *f, int32_t mem, double *P, double *K, void *strea
 /* FP64 KKT residual of eq. (kkt) for a given (x, u, y) on the GPU.
  * stats[0] = ||K z - b||_inf, stats[1] = eta = ||K z - b||_inf /
  * (||K||_inf ||z||_inf + ||b||_inf) (normwise backward error), written to the
- * host array stats[2].  Synchronises `stream`. */
+ * host array stats[2].  For a forest plan the norms are taken tree by tree:
+ * stats[0] is the largest residual and stats[1] the largest eta over the trees
+ * (a batch meets a tolerance when each of its trees does; the refinement of
+ * tlqr_solve stops on the same per-tree eta).  Synchronises `stream`. */
 int tlqr_kkt_residual(tlqr_factor_t *f, const tlqr_problem *prob, int32_t mem, const double *x,
                       const double *u, const double *y, double *stats, void *stream);
 
@@ -242,6 +256,12 @@ int tlqr_kkt_residual(tlqr_factor_t *f, const tlqr_problem *prob, int32_t mem, c
 int tlqr_kkt_residual_noalloc(const tlqr_plan_t *plan, int32_t n, int32_t m, const tlqr_problem *prob,
                               const double *x, const double *u, const double *y, double *stats,
                               void *stream);
+
+/* Per-tree ||K z - b||_inf and eta of the last residual evaluation (the last
+ * refinement check of tlqr_solve, or tlqr_kkt_residual), for the first
+ * min(max_trees, number of trees) trees in increasing root label.  Host
+ * arrays; either may be NULL.  A single tree has one entry. */
+int tlqr_tree_residuals(const tlqr_factor_t *f, double *abs_res, double *eta, int32_t max_trees);
 
 /* Refinement steps and backward error of the last tlqr_solve. */
 int tlqr_last_info(const tlqr_factor_t *f, tlqr_info *out);

@@ -695,6 +695,52 @@ __device__ __forceinline__ bool chol_reg(T (&g)[M][M]) {
   }
   return ok;
 }
+// FP64 fallback of chol_reg (see kCholRatio): when a group's FP32 factor of
+// S = S64 + S32 failed or is ill-conditioned, the group's first lane
+// refactors S in FP64 in `scratch` (M*M doubles of the group's shared memory)
+// and writes the rounded L to lout (M rows of stride ldo); every lane of the
+// group then reloads L from there.  s32 (shared, stride lds) may be null.
+// Called by all lanes of the warp (warp-uniform); skip = this group has no
+// block to factor (a root's empty edge slot).
+template <typename T, int M, int G>
+__device__ __forceinline__ bool chol_reg_checked(T (&l)[M][M], bool ok, bool skip, int gl, const double* s64,
+                                                 const T* s32, int lds, double* scratch, T* lout, int ldo) {
+  if constexpr (sizeof(T) == 8) {
+    return ok;
+  } else {
+    float dmin = INFINITY, dmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) { dmin = fminf(dmin, l[k][k]); dmax = fmaxf(dmax, l[k][k]); }
+    const bool ill = !skip && (!ok || dmax > kCholRatio * dmin);
+    if (!__any_sync(TLQR_FULL_MASK, ill)) return ok;
+    bool ok64 = true;
+    if (ill && gl == 0) {
+      for (int e = 0; e < M * M; ++e) {
+        const int i = e / M, j = e - (e / M) * M;
+        scratch[e] = s64[e] + (s32 ? (double)s32[i * lds + j] : 0.0);
+      }
+      ok64 = chol64_serial(scratch, M, M);
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) lout[i * ldo + j] = j <= i ? (T)scratch[i * M + j] : T(0);
+    }
+    const int leader = (threadIdx.x & 31) & ~(G - 1);
+    ok64 = __shfl_sync(TLQR_FULL_MASK, ok64, leader);
+    __syncwarp();
+    if (ill) {
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        T row[M];
+        row_load<T, M>(row, lout + a * ldo);
+#pragma unroll
+        for (int b = 0; b < M; ++b) l[a][b] = row[b];
+      }
+      ok = ok64;
+    }
+    __syncwarp();
+    return ok;
+  }
+}
+
 // Solve L L^T x = b in registers.
 template <typename T, int M>
 __device__ __forceinline__ void chol_solve_reg(const T (&l)[M][M], T (&b)[M]) {
@@ -785,7 +831,11 @@ __global__ void kf_condense(Ws<T> w, int count) {
 #pragma unroll
     for (int b = 0; b < M; ++b) Rl[a][b] = row[b];
   }
-  const bool ok = chol_reg<T, M>(Rl);
+  bool ok = chol_reg<T, M>(Rl);
+  static_assert(2 * N * CondSmem<T, N, M>::MLD * sizeof(T) >= 8 * M * M, "FP64 scratch does not fit");
+  __syncwarp();
+  ok = chol_reg_checked<T, M, G>(Rl, ok, is_root || !g.valid, gl, w.R + (size_t)i * M * M, (const T*)nullptr, 0,
+                                 reinterpret_cast<double*>(sBR), sR, MLD);
   T br[M];
   row_load<T, M>(br, sB + r * MLD);
   chol_solve_reg<T, M>(Rl, br);                 // row r of B R^{-1}
@@ -903,14 +953,27 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
   row_mm<T, N, M, MLD>(wb, wrow, sB);
   if (gl < N) row_store<T, M>(sWB + r * MLD, wb);
   __syncwarp();
-  // G = R + B^T (W B): entry (a, b) by lane a*M + b, then factored in every lane
+  // G = R + B^T (W B): entry (a, b) by lane a*M + b, then factored in every
+  // lane; in FP32, B^T W B is also kept apart (in the Delta tile, free by now)
+  // for the FP64 fallback of the factorisation
+  T* sBWB = sD;
+  double* scratch = reinterpret_cast<double*>(sD + M * M);
+  static_assert(MAT * sizeof(T) >= 4 * M * M + 8 * M * M, "FP64 scratch does not fit");
 #pragma unroll
   for (int e2 = gl; e2 < M * M; e2 += G) {
     const int a = e2 / M, b = e2 - (e2 / M) * M;
-    T v = (T)w.R[(size_t)j * M * M + e2];
+    if constexpr (sizeof(T) == 8) {
+      T v = (T)w.R[(size_t)j * M * M + e2];
 #pragma unroll
-    for (int t = 0; t < N; ++t) v = fma(sB[t * MLD + a], sWB[t * MLD + b], v);
-    sG[a * MLD + b] = v;
+      for (int t = 0; t < N; ++t) v = fma(sB[t * MLD + a], sWB[t * MLD + b], v);
+      sG[a * MLD + b] = v;
+    } else {
+      T v = T(0);
+#pragma unroll
+      for (int t = 0; t < N; ++t) v = fma(sB[t * MLD + a], sWB[t * MLD + b], v);
+      sBWB[e2] = v;
+      sG[a * MLD + b] = (T)w.R[(size_t)j * M * M + e2] + v;
+    }
   }
   __syncwarp();
   T Gl[M][M];
@@ -921,7 +984,10 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
 #pragma unroll
     for (int b = 0; b < M; ++b) Gl[a][b] = row[b];
   }
-  const bool okg = chol_reg<T, M>(Gl);
+  bool okg = chol_reg<T, M>(Gl);
+  __syncwarp();
+  okg = chol_reg_checked<T, M, G>(Gl, okg, is_root || !g.valid, gl, w.R + (size_t)j * M * M, (const T*)sBWB, M,
+                                  scratch, sG, MLD);
   // column r of H = (W B)^T A + M^T;  K(:, r) = -G^{-1} H(:, r)
   T hc[M];
   if (w.has_M) row_load<T, M>(hc, sMm + r * MLD);

@@ -108,6 +108,8 @@ __global__ void k_condense(Ws<T> w, int warp_bytes) {
   }
   if (node_is_root(w, i)) return;
   T *sR = sm, *sX = sm + m * m, *sB = sX + 2 * n * m, *sM = sB + n * m;
+  double* scratch = reinterpret_cast<double*>(
+      reinterpret_cast<unsigned char*>(sm) + ((sizeof(T) * (m * m + 4 * n * m) + 15) / 16) * 16);
   const int nr = w.has_M ? 2 * n : n;    // X = R^{-1} [B^T | M^T]  (m x nr)
   wload(sR, w.R + (size_t)i * m * m, m * m);
   const double* Bg = w.B + (size_t)i * n * m;
@@ -125,7 +127,10 @@ __global__ void k_condense(Ws<T> w, int warp_bytes) {
     }
   }
   __syncwarp();
-  if (!wchol(sR, m, m)) { set_status(w.status, ST_NOT_PD); return; }
+  if (!wchol_checked(sR, m, m, w.R + (size_t)i * m * m, (const T*)nullptr, 0, scratch)) {
+    set_status(w.status, ST_NOT_PD);
+    return;
+  }
   wchol_solve(sR, m, m, sX, nr, nr);
   T* Ec = w.Ec + (size_t)i * nn;
   const double* Dg = (w.has_delta && dnz) ? w.Delta + (size_t)i * nn : nullptr;
@@ -230,8 +235,8 @@ __global__ void k_expand(Ws<T> w, int begin, int count, int warp_bytes) {
 }
 
 // ---------------------------------------------------------------- local factors
-// eq. (FW), (factor-local).  sm: 5 n^2 + 3 n m + m^2 T + n ints (n^2 >= n m assumed
-// by the carve-out below only through the explicit sizes).
+// eq. (FW), (factor-local).  sm: 5 n^2 + 3 n m + m^2 T + n ints, then (FP32)
+// B^T W B (m^2 T) and m^2 doubles for the FP64 fallback of the G Cholesky.
 template <typename T>
 __global__ void k_local_factor(Ws<T> w, int warp_bytes) {
   const int j = warp_op();
@@ -241,6 +246,9 @@ __global__ void k_local_factor(Ws<T> w, int warp_bytes) {
   T *sP = sm, *sF = sm + nn, *sFi = sm + 2 * nn, *sW = sm + 3 * nn, *sAcl = sm + 4 * nn;
   T *sB = sm + 5 * nn, *sWB = sB + n * m, *sH = sWB + n * m, *sG = sH + n * m;
   int* piv = reinterpret_cast<int*>(sG + m * m);
+  unsigned char* tail = reinterpret_cast<unsigned char*>(sm) + ((sizeof(T) * (5 * nn + 3 * n * m + m * m) + 4 * n + 15) / 16) * 16;
+  T* sBWB = reinterpret_cast<T*>(tail);
+  double* scratch = reinterpret_cast<double*>(tail + ((sizeof(T) * m * m + 15) / 16) * 16);
   const size_t oj = (size_t)j * nn;
   wload(sP, w.U + oj, nn);
   const bool dnz = w.has_delta && w.dflag[j];
@@ -270,7 +278,14 @@ __global__ void k_local_factor(Ws<T> w, int warp_bytes) {
   wload(sG, w.R + (size_t)j * m * m, m * m);
   __syncwarp();
   wgemm<T, false, false>(n, m, n, Wuse, n, sB, m, sWB, m, T(1), (const T*)nullptr, 0);    // W B
-  wgemm<T, true, false>(m, m, n, sB, m, sWB, m, sG, m, T(1), sG, m);                     // G = R + B^T W B
+  if constexpr (sizeof(T) == 8) {
+    wgemm<T, true, false>(m, m, n, sB, m, sWB, m, sG, m, T(1), sG, m);                   // G = R + B^T W B
+  } else {
+    // keep B^T W B apart from R for a possible FP64 refactorisation of G
+    wgemm<T, true, false>(m, m, n, sB, m, sWB, m, sBWB, m, T(1), (const T*)nullptr, 0);
+    for (int e = lane_id(); e < m * m; e += 32) sG[e] += sBWB[e];
+    __syncwarp();
+  }
   // H = (W B)^T A + M^T  (B^T W A with W symmetric)
   wgemm<T, true, false>(m, n, n, sWB, m, sAcl, n, sH, n, T(1), (const T*)nullptr, 0);
   if (w.has_M) {
@@ -281,7 +296,10 @@ __global__ void k_local_factor(Ws<T> w, int warp_bytes) {
     }
     __syncwarp();
   }
-  if (!wchol(sG, m, m)) { set_status(w.status, ST_NOT_PD); return; }
+  if (!wchol_checked(sG, m, m, w.R + (size_t)j * m * m, (const T*)sBWB, m, scratch)) {
+    set_status(w.status, ST_NOT_PD);
+    return;
+  }
   wload(w.LG + (size_t)j * m * m, sG, m * m);
   wchol_solve(sG, m, m, sH, n, n);                 // G^{-1} H ; K = -G^{-1} H
   for (int e = lane_id(); e < m * n; e += 32) {

@@ -30,6 +30,7 @@ struct tlqr_plan_t {
   std::vector<int32_t> comp_j, comp_i, comp_k;   // centre, current parent, current child
   // original-tree children (CSR), increasing index; for the KKT residual
   std::vector<int32_t> child_start, child_list;
+  std::vector<int32_t> tree_of;         // forest: tree ordinal of each node (roots in increasing label)
   // per-node schedule (Fig. 2 labels)
   std::vector<int32_t> round_of_node, op_of_node;
   // statistics

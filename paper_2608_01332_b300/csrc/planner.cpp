@@ -111,7 +111,9 @@ int build_plan(const int32_t* parent, int32_t N, bool allow_forest, tlqr_plan_t*
     // reachability from the root (a cycle leaves nodes unreached) and height
     {
       std::vector<int32_t> depth(N, -1), stack;
-      for (int i = 0; i < N; ++i) if (parent[i] < 0) { depth[i] = 0; stack.push_back(i); }
+      P->tree_of.assign(N, 0);
+      for (int i = 0, t = 0; i < N; ++i)
+        if (parent[i] < 0) { depth[i] = 0; P->tree_of[i] = t++; stack.push_back(i); }
       int seen = 0;
       while (!stack.empty()) {
         int i = stack.back(); stack.pop_back(); ++seen;
@@ -120,6 +122,7 @@ int build_plan(const int32_t* parent, int32_t N, bool allow_forest, tlqr_plan_t*
         for (int t = P->child_start[i]; t < P->child_start[i + 1]; ++t) {
           int j = P->child_list[t];
           depth[j] = depth[i] + 1;
+          P->tree_of[j] = P->tree_of[i];
           P->height = std::max(P->height, depth[j]);
           stack.push_back(j);
         }

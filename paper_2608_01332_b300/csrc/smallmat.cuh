@@ -172,6 +172,84 @@ __device__ bool wchol(T* a, int m, int lda) {
   return true;
 }
 
+// ------------------------------------------------------------ FP64 fallback
+// In mixed precision the SPD blocks R_e and G_e = R_e + B_e^T W B_e are
+// factored in FP32 first.  An FP32 Cholesky has a backward error of about
+// eps_32 ||S||, i.e. a relative error ~ kappa(S) eps_32 in the directions of
+// the small eigenvalues: beyond kappa ~ 1e5 the factors stop being a usable
+// preconditioner for the FP64 refinement (and the factorisation may break
+// down).  Such blocks are refactored in FP64 and the FP64 factor L is rounded
+// to FP32; the rounding perturbs the preconditioned operator only by
+// ~ kappa(L) eps_32 = sqrt(kappa(S)) eps_32, so FP32 triangular solves with the
+// rounded L stay accurate to ~1e-3 up to kappa(S) ~ 1e8.
+// A block counts as ill-conditioned when the FP32 factorisation fails or its
+// largest diagonal entry of L exceeds kCholRatio times its smallest (pivot
+// ratio > 1e4, a lower bound on kappa(S)).
+constexpr float kCholRatio = 100.0f;
+
+// In-place Cholesky of an m x m SPD matrix (row-major, lda) in FP64 by one
+// thread, left-looking (row by row); the lower triangle receives L.  False
+// when a pivot is not positive and finite.
+__device__ inline bool chol64_serial(double* a, int m, int lda) {
+  for (int k = 0; k < m; ++k) {
+    for (int i = 0; i <= k; ++i) {
+      double v = a[k * lda + i];
+      for (int t = 0; t < i; ++t) v = fma(-a[k * lda + t], a[i * lda + t], v);
+      if (i < k) {
+        a[k * lda + i] = v / a[i * lda + i];
+      } else {
+        if (!(v > 0.0) || !isfinite(v)) return false;
+        a[k * lda + k] = sqrt(v);
+      }
+    }
+  }
+  return true;
+}
+
+// Warp-cooperative Cholesky with the FP64 fallback.  On entry a (working
+// precision) holds S = S64 + S32 rounded, where s64 (global, FP64, m x m
+// row-major) and s32 (shared, working precision, lds; may be null) are the
+// two parts of S kept separately; scratch holds m*m doubles of shared memory.
+// On return a holds L (in the working precision).  False when S is not
+// numerically PD even in FP64.
+template <typename T>
+__device__ bool wchol_checked(T* a, int m, int lda, const double* s64, const T* s32, int lds, double* scratch) {
+  bool ok = wchol(a, m, lda);
+  if constexpr (sizeof(T) == 8) {
+    return ok;
+  } else {
+    float dmin = INFINITY, dmax = 0.f;
+    if (ok) {
+      for (int k = lane_id(); k < m; k += 32) {
+        const float d = (float)a[k * lda + k];
+        dmin = fminf(dmin, d);
+        dmax = fmaxf(dmax, d);
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        dmin = fminf(dmin, __shfl_xor_sync(TLQR_FULL_MASK, dmin, off));
+        dmax = fmaxf(dmax, __shfl_xor_sync(TLQR_FULL_MASK, dmax, off));
+      }
+    }
+    if (ok && dmax <= kCholRatio * dmin) return true;
+    for (int e = lane_id(); e < m * m; e += 32) {
+      const int i = e / m, j = e - (e / m) * m;
+      scratch[e] = s64[e] + (s32 ? (double)s32[i * lds + j] : 0.0);
+    }
+    __syncwarp();
+    bool ok64 = true;
+    if (lane_id() == 0) ok64 = chol64_serial(scratch, m, m);
+    ok64 = __shfl_sync(TLQR_FULL_MASK, ok64, 0);
+    __syncwarp();
+    for (int e = lane_id(); e < m * m; e += 32) {
+      const int i = e / m, j = e - (e / m) * m;
+      if (j <= i) a[i * lda + j] = (T)scratch[e];
+    }
+    __syncwarp();
+    return ok64;
+  }
+}
+
 // Solve L L^T X = B in place (L from wchol); B is m x nrhs, leading dim ldb.
 template <typename T>
 __device__ void wchol_solve(const T* l, int m, int lda, T* b, int nrhs, int ldb) {

@@ -48,10 +48,10 @@ struct WarpBytes {
 WarpBytes warp_bytes(int n, int m, size_t ts) {
   const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
   WarpBytes w;
-  w.condense = align16(ts * (mm + 4 * nm));
+  w.condense = align16(ts * (mm + 4 * nm)) + align16(8 * mm);                 // + FP64 Cholesky scratch
   w.tau = align16(ts * 5 * nn + 4 * n);
   w.compress = align16(ts * 7 * nn + 4 * n);
-  w.local_factor = align16(ts * (5 * nn + 3 * nm + mm) + 4 * n);
+  w.local_factor = align16(ts * (5 * nn + 3 * nm + mm) + 4 * n) + align16(ts * mm) + align16(8 * mm);
   w.compose_T = align16(ts * 2 * nn);
   w.aff_init = align16(ts * (2 * nn + 2 * nm + 2 * n + m));
   w.vec1 = align16(ts * (nn + n));
@@ -193,6 +193,7 @@ struct DevPlan {
   int *rake_leaf = nullptr, *rake_parent = nullptr, *seg_parent = nullptr, *seg_start = nullptr;
   int *comp_j = nullptr, *comp_i = nullptr, *comp_k = nullptr;
   int *parent = nullptr, *child_start = nullptr, *child_list = nullptr;
+  int* tree = nullptr;           // forest only: tree ordinal of each node
 };
 
 }  // namespace
@@ -218,6 +219,7 @@ struct tlqr_factor_t {
   unsigned long long* h_maxes = nullptr;   // pinned mirror
   int* h_status = nullptr;                  // pinned mirror
   double* stage = nullptr;                  // FP64 staging (host-memory calls), lazily allocated
+  size_t arena_bytes = 0;                   // the one device allocation holding plan arrays + workspace
   size_t stage_elems = 0;
   // problem pointers of the last factorisation (device), for refinement/residual
   tlqr_problem dprob{};
@@ -298,33 +300,89 @@ int map_status(int st) {
   }
 }
 
+// Device memory of a factor object: the plan's arrays and the whole workspace
+// are carved from one allocation (one cudaMalloc and one cudaFree per factor,
+// so that creating and destroying factors does not fragment memory or
+// serialise the device more than once).  A pass with base == nullptr only
+// sizes the layout.
+struct Carve {
+  unsigned char* base = nullptr;
+  size_t off = 0;
+  void* take(size_t bytes) {
+    const size_t o = (off + 255) & ~size_t(255);
+    off = o + std::max<size_t>(bytes, 1);
+    return base ? base + o : nullptr;
+  }
+  template <typename T>
+  T* take(size_t elems, size_t es) { return reinterpret_cast<T*>(take(elems * es)); }
+};
+
+std::vector<int32_t> round_table(const tlqr_plan_t* P) {
+  std::vector<int32_t> rd;
+  for (const tlqr_round& r : P->rounds)
+    rd.insert(rd.end(), {r.rake_begin, r.rake_end, r.seg_begin, r.seg_end, r.comp_begin, r.comp_end});
+  return rd;
+}
+
+// Assign (or size) every device pointer of f.
+void carve_factor(tlqr_factor_t* f, Carve& c) {
+  const tlqr_plan_t* P = f->plan;
+  auto ints = [&](const std::vector<int32_t>& v) { return c.take<int>(v.size(), sizeof(int)); };
+  f->dp.rake_leaf = ints(P->rake_leaf);
+  f->dp.rake_parent = ints(P->rake_parent);
+  f->dp.seg_parent = ints(P->seg_parent);
+  f->dp.seg_start = ints(P->seg_start);
+  f->dp.comp_j = ints(P->comp_j);
+  f->dp.comp_i = ints(P->comp_i);
+  f->dp.comp_k = ints(P->comp_k);
+  f->dp.parent = ints(P->parent);
+  f->dp.child_start = ints(P->child_start);
+  f->dp.child_list = ints(P->child_list);
+  f->dp.tree = P->n_trees > 1 ? ints(P->tree_of) : nullptr;
+  f->d_rounds = reinterpret_cast<fx::RoundDesc*>(c.take<int>(6 * P->rounds.size(), sizeof(int)));
+  const size_t N = P->N, n = f->opt.n, m = f->opt.m, nn = n * n, nm = n * m, mm = m * m;
+  const size_t nrake = std::max<size_t>(1, P->rake_leaf.size());
+  const size_t ts = f->ts;
+  f->U = c.take(N * nn * ts); f->Ea = c.take(N * nn * ts); f->Ec = c.take(N * nn * ts); f->Ep = c.take(N * nn * ts);
+  f->contrib = c.take(nrake * nn * ts);
+  f->K = c.take(N * nm * ts); f->Tm = c.take(N * nn * ts); f->Tr = c.take(N * nn * ts);
+  f->LG = c.take(N * mm * ts);
+  f->W = f->Finv = nullptr;
+  if (f->opt.has_delta) { f->W = c.take(N * nn * ts); f->Finv = c.take(N * nn * ts); }
+  f->h = c.take(N * n * ts); f->z = c.take(N * n * ts); f->s = c.take(N * n * ts); f->cv = c.take(nrake * n * ts);
+  f->bv = c.take(N * n * ts); f->kv = c.take(N * m * ts); f->xs = c.take(N * n * ts);
+  f->dflag = c.take<unsigned char>(N, 1);
+  f->status = c.take<int>(1, sizeof(int));
+  f->res_x = c.take<double>(N * n, 8); f->res_u = c.take<double>(N * m, 8); f->res_c = c.take<double>(N * n, 8);
+  f->maxes = c.take<unsigned long long>(4 * (size_t)P->n_trees, 8);
+  f->xh = f->xl = f->uh = f->ul = f->yh = f->yl = nullptr;
+  if (f->opt.precision == TLQR_PREC_MIXED) {
+    f->xh = c.take<float>(N * n, 4); f->xl = c.take<float>(N * n, 4);
+    f->uh = c.take<float>(N * m, 4); f->ul = c.take<float>(N * m, 4);
+    f->yh = c.take<float>(N * n, 4); f->yl = c.take<float>(N * n, 4);
+  }
+}
+
+// Copy the plan's arrays into their carved slots and pick the tail rounds.
 int upload_plan(tlqr_factor_t* f) {
   const tlqr_plan_t* P = f->plan;
   cudaError_t err = cudaSuccess;
-  auto up = [&](const std::vector<int32_t>& v, int** dst) {
-    *dst = dalloc<int>(v.size(), &err);
-    if (*dst) f->allocs.push_back(*dst);
-    if (err == cudaSuccess && !v.empty())
-      err = cudaMemcpy(*dst, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice);
+  auto up = [&](const std::vector<int32_t>& v, int* dst) {
+    if (err == cudaSuccess && !v.empty() && dst)
+      err = cudaMemcpy(dst, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice);
   };
-  up(P->rake_leaf, &f->dp.rake_leaf);
-  up(P->rake_parent, &f->dp.rake_parent);
-  up(P->seg_parent, &f->dp.seg_parent);
-  up(P->seg_start, &f->dp.seg_start);
-  up(P->comp_j, &f->dp.comp_j);
-  up(P->comp_i, &f->dp.comp_i);
-  up(P->comp_k, &f->dp.comp_k);
-  up(P->parent, &f->dp.parent);
-  up(P->child_start, &f->dp.child_start);
-  up(P->child_list, &f->dp.child_list);
-  {
-    std::vector<int32_t> rd;
-    for (const tlqr_round& r : P->rounds)
-      rd.insert(rd.end(), {r.rake_begin, r.rake_end, r.seg_begin, r.seg_end, r.comp_begin, r.comp_end});
-    int* d = nullptr;
-    up(rd, &d);
-    f->d_rounds = reinterpret_cast<fx::RoundDesc*>(d);
-  }
+  up(P->rake_leaf, f->dp.rake_leaf);
+  up(P->rake_parent, f->dp.rake_parent);
+  up(P->seg_parent, f->dp.seg_parent);
+  up(P->seg_start, f->dp.seg_start);
+  up(P->comp_j, f->dp.comp_j);
+  up(P->comp_i, f->dp.comp_i);
+  up(P->comp_k, f->dp.comp_k);
+  up(P->parent, f->dp.parent);
+  up(P->child_start, f->dp.child_start);
+  up(P->child_list, f->dp.child_list);
+  if (P->n_trees > 1) up(P->tree_of, f->dp.tree);
+  up(round_table(P), reinterpret_cast<int*>(f->d_rounds));
   // tail: the longest suffix of rounds whose phases each hold at most kTailOps operations
   const int R = (int)P->rounds.size();
   f->tail_r0 = R;
@@ -334,7 +392,7 @@ int upload_plan(tlqr_factor_t* f) {
     if (mx > kTailOps) break;
     --f->tail_r0;
   }
-  if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? TLQR_ERR_OOM : TLQR_ERR_CUDA;
+  if (err != cudaSuccess) return TLQR_ERR_CUDA;
   return TLQR_OK;
 }
 
@@ -543,14 +601,21 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
   return launch_warps(rc, TLQR_K_RECOVER, k_recover<T>, P->N, wb.recover, st, w, x, u, y, accumulate, (int)wb.recover);
 }
 
+// FP64 keeps the run-time-n kernels at n = 32 (a row of 32 doubles per lane
+// does not fit the register file), so those are not instantiated.
+template <typename T>
+constexpr bool fixed_for(int n) { return !(sizeof(T) == 8 && n == 32); }
+
 // Dimension dispatch.  fixed_n: compile-time n of the n x n kernels (0 = run time);
 // fixed_m: compile-time m of the (n, m) kernels for that n (0 = run time).
 #define TLQR_FIXED_CASES(X)                                                     \
-  X(4, 0) X(4, 2) X(6, 0) X(6, 2) X(8, 0) X(8, 2) X(12, 0) X(12, 4) X(16, 0) X(16, 4)
+  X(4, 0) X(4, 2) X(6, 0) X(6, 2) X(8, 0) X(8, 2) X(12, 0) X(12, 4) X(16, 0) X(16, 4) X(32, 0) X(32, 8)
 
 template <typename T>
 cudaError_t dispatch_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cudaStream_t st) {
-#define X(n_, m_) if (f->fixed_n == n_ && f->fixed_m == m_) return run_factor<T, n_, m_>(f, rc, p, st);
+#define X(n_, m_)                                                   \
+  if constexpr (fixed_for<T>(n_))                                   \
+    if (f->fixed_n == n_ && f->fixed_m == m_) return run_factor<T, n_, m_>(f, rc, p, st);
   TLQR_FIXED_CASES(X)
 #undef X
   return run_factor<T, 0, 0>(f, rc, p, st);
@@ -558,16 +623,17 @@ cudaError_t dispatch_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& 
 template <typename T>
 cudaError_t dispatch_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const double* r, const double* c,
                            double* x, double* u, double* y, int accumulate, cudaStream_t st) {
-#define X(n_, m_) \
-  if (f->fixed_n == n_ && f->fixed_m == m_) return run_solve<T, n_, m_>(f, rc, q, r, c, x, u, y, accumulate, st);
+#define X(n_, m_)                                                   \
+  if constexpr (fixed_for<T>(n_))                                   \
+    if (f->fixed_n == n_ && f->fixed_m == m_) return run_solve<T, n_, m_>(f, rc, q, r, c, x, u, y, accumulate, st);
   TLQR_FIXED_CASES(X)
 #undef X
   return run_solve<T, 0, 0>(f, rc, q, r, c, x, u, y, accumulate, st);
 }
 
-bool has_fixed_kernels(int n) { return n == 4 || n == 6 || n == 8 || n == 12 || n == 16; }
+bool has_fixed_kernels(int n) { return n == 4 || n == 6 || n == 8 || n == 12 || n == 16 || n == 32; }
 bool has_fixed_pair(int n, int m) {
-  return (m == 2 && (n == 4 || n == 6 || n == 8)) || (m == 4 && (n == 12 || n == 16));
+  return (m == 2 && (n == 4 || n == 6 || n == 8)) || (m == 4 && (n == 12 || n == 16)) || (m == 8 && n == 32);
 }
 
 // ff = 1: float-float kernel on the FP32 pipe (refinement); ff = 0: plain FP64 kernel.
@@ -582,23 +648,30 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   a.x = x; a.u = u; a.y = y;
   a.res_x = f->res_x; a.res_u = f->res_u; a.res_c = f->res_c;
   a.maxes = f->maxes;
-  cudaError_t e = cudaMemsetAsync(f->maxes, 0, (with_knorm ? 4 : 3) * sizeof(unsigned long long), st);
+  a.T = P->n_trees;
+  a.tree = a.T > 1 ? f->dp.tree : nullptr;
+  // slot-major [4][T]: the ||K|| slot (last) is kept from an earlier call unless with_knorm
+  cudaError_t e = cudaMemsetAsync(f->maxes, 0, (with_knorm ? 4 : 3) * (size_t)a.T * sizeof(unsigned long long), st);
   if (e) return e;
   FFArgs fa{};
   if (ff) {
-    // split x, u, y once per call; ||z|| and ||b|| maxima come from the same pass
+    // split x, u, y once per call; for one tree ||z|| and ||b|| maxima come
+    // from the same pass (a forest forms them per tree in the residual kernel)
     const size_t N = P->N, n = f->opt.n, m = f->opt.m;
+    const int zs = a.tree ? -1 : 1, bs = a.tree ? -1 : 2;
     SplitList L{};
     auto add = [&](const double* src, float* hi, float* lo, size_t len, int slot) {
       L.src[L.count] = src; L.hi[L.count] = hi; L.lo[L.count] = lo; L.len[L.count] = len; L.slot[L.count] = slot;
       ++L.count;
     };
-    add(x, f->xh, f->xl, N * n, 1);
-    add(u, f->uh, f->ul, N * m, 1);
-    add(y, f->yh, f->yl, N * n, 1);
-    add(p.q, nullptr, nullptr, N * n, 2);
-    add(p.r, nullptr, nullptr, N * m, 2);
-    add(p.c, nullptr, nullptr, N * n, 2);
+    add(x, f->xh, f->xl, N * n, zs);
+    add(u, f->uh, f->ul, N * m, zs);
+    add(y, f->yh, f->yl, N * n, zs);
+    if (!a.tree) {
+      add(p.q, nullptr, nullptr, N * n, bs);
+      add(p.r, nullptr, nullptr, N * m, bs);
+      add(p.c, nullptr, nullptr, N * n, bs);
+    }
     L.maxes = f->maxes;
     if ((e = launch_split(rc, L, st))) return e;
     fa = FFArgs{f->xh, f->xl, f->uh, f->ul, f->yh, f->yl};
@@ -609,12 +682,19 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
   EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr, P->N};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  if (ff) k_residual_ff<<<blocks, threads, 0, st>>>(a, fa);
-  else k_residual<<<blocks, threads, 0, st>>>(a);
+  if (a.tree) {
+    if (ff) k_residual_ff_trees<<<blocks, threads, 0, st>>>(a, fa);
+    else k_residual_trees<<<blocks, threads, 0, st>>>(a);
+  } else {
+    if (ff) k_residual_ff<<<blocks, threads, 0, st>>>(a, fa);
+    else k_residual<<<blocks, threads, 0, st>>>(a);
+  }
   if ((e = cudaGetLastError())) return e;
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[TLQR_K_RESIDUAL]++; rc->units[TLQR_K_RESIDUAL] += P->N; }
-  if ((e = cudaMemcpyAsync(f->h_maxes, f->maxes, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(f->h_maxes, f->maxes, 4 * (size_t)a.T * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, st)))
+    return e;
   return cudaMemcpyAsync(f->h_status, f->status, sizeof(int), cudaMemcpyDeviceToHost, st);
 }
 
@@ -674,13 +754,28 @@ GraphCache* solve_cache(tlqr_factor_t* f, const std::vector<uintptr_t>& key) {
   return g;
 }
 
-void residual_stats(const tlqr_factor_t* f, double* abs_res, double* eta) {
+// ||K z - b|| and eta of tree t from the slot-major maxima [4][T].
+void tree_stats(const tlqr_factor_t* f, int t, double* abs_res, double* eta) {
+  const int T = f->plan->n_trees;
   double v[4];
-  for (int t = 0; t < 4; ++t) std::memcpy(&v[t], &f->h_maxes[t], sizeof(double));
+  for (int q = 0; q < 4; ++q) std::memcpy(&v[q], &f->h_maxes[(size_t)q * T + t], sizeof(double));
   *abs_res = v[0];
   const double den = v[3] * v[1] + v[2];
   *eta = den > 0 ? v[0] / den : v[0];
   if (!std::isfinite(v[0])) *eta = INFINITY;
+}
+
+// Whole problem: the largest residual, and the largest eta over the trees
+// (for one tree, the plain eta).
+void residual_stats(const tlqr_factor_t* f, double* abs_res, double* eta) {
+  *abs_res = 0.0;
+  *eta = 0.0;
+  for (int t = 0; t < f->plan->n_trees; ++t) {
+    double a, e;
+    tree_stats(f, t, &a, &e);
+    if (!(a <= *abs_res)) *abs_res = a;
+    if (!(e <= *eta)) *eta = e;
+  }
 }
 
 size_t problem_elems(int N, int n, int m) {
@@ -824,7 +919,8 @@ cudaError_t configure_fixed_nm() {
 }
 template <typename T>
 cudaError_t configure_fixed_pair(int n, int m) {
-#define X(n_, m_) if constexpr (m_ > 0) { if (n == n_ && m == m_) return configure_fixed_nm<T, n_, m_>(); }
+#define X(n_, m_) \
+  if constexpr (m_ > 0 && fixed_for<T>(n_)) { if (n == n_ && m == m_) return configure_fixed_nm<T, n_, m_>(); }
   TLQR_FIXED_CASES(X)
 #undef X
   return cudaSuccess;
@@ -837,6 +933,9 @@ cudaError_t configure_fixed_n(int n) {
     case 8: return configure_fixed<T, 8>();
     case 12: return configure_fixed<T, 12>();
     case 16: return configure_fixed<T, 16>();
+    case 32:
+      if constexpr (fixed_for<T>(32)) return configure_fixed<T, 32>();
+      return cudaSuccess;
     default: return cudaSuccess;
   }
 }
@@ -928,7 +1027,7 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   f->fixed_n = (has_fixed_kernels(n) && !opts->generic_kernels) ? n : 0;
   // FP64: groups of 8 / 16 lanes for n = 6 / 12 leave lanes idle, which costs FP64 issue slots;
   // the run-time-n kernels keep all 32 lanes busy and are faster there.
-  if (f->ts == 8 && (n == 6 || n == 12)) f->fixed_n = 0;
+  if (f->ts == 8 && (n == 6 || n == 12 || n == 32)) f->fixed_n = 0;
   f->fixed_m = (f->fixed_n && has_fixed_pair(n, m)) ? m : 0;
   if ((f->ts == 8 ? configure_kernels<double>(n, m) : configure_kernels<float>(n, m)) != cudaSuccess ||
       (f->ts == 8 ? configure_fixed_n<double>(f->fixed_n) : configure_fixed_n<float>(f->fixed_n)) != cudaSuccess ||
@@ -937,36 +1036,24 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
     delete f;
     return TLQR_ERR_CUDA;
   }
+  Carve sizing;
+  carve_factor(f, sizing);
+  void* arena = nullptr;
+  cudaError_t err = cudaMalloc(&arena, sizing.off);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    delete f;
+    return err == cudaErrorMemoryAllocation ? TLQR_ERR_OOM : TLQR_ERR_CUDA;
+  }
+  f->allocs.push_back(arena);
+  f->arena_bytes = sizing.off;
+  Carve c;
+  c.base = static_cast<unsigned char*>(arena);
+  carve_factor(f, c);
   int rc = upload_plan(f);
   if (rc) { delete f; return rc; }
-  const size_t N = plan->N, nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
-  const size_t nrake = std::max<size_t>(1, plan->rake_leaf.size());
-  cudaError_t err = cudaSuccess;
-  auto take = [&](size_t elems, size_t es) -> void* {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(1, elems) * es);
-    if (e != cudaSuccess) { if (err == cudaSuccess) err = e; return nullptr; }
-    f->allocs.push_back(p);
-    return p;
-  };
-  const size_t ts = f->ts;
-  f->U = take(N * nn, ts); f->Ea = take(N * nn, ts); f->Ec = take(N * nn, ts); f->Ep = take(N * nn, ts);
-  f->contrib = take(nrake * nn, ts);
-  f->K = take(N * nm, ts); f->Tm = take(N * nn, ts); f->Tr = take(N * nn, ts);
-  f->LG = take(N * mm, ts);
-  if (opts->has_delta) { f->W = take(N * nn, ts); f->Finv = take(N * nn, ts); }
-  f->h = take(N * n, ts); f->z = take(N * n, ts); f->s = take(N * n, ts); f->cv = take(nrake * n, ts);
-  f->bv = take(N * n, ts); f->kv = take(N * m, ts); f->xs = take(N * n, ts);
-  f->dflag = (unsigned char*)take(N, 1);
-  f->status = (int*)take(1, sizeof(int));
-  f->res_x = (double*)take(N * n, 8); f->res_u = (double*)take(N * m, 8); f->res_c = (double*)take(N * n, 8);
-  f->maxes = (unsigned long long*)take(4, 8);
-  if (opts->precision == TLQR_PREC_MIXED) {
-    f->xh = (float*)take(N * n, 4); f->xl = (float*)take(N * n, 4);
-    f->uh = (float*)take(N * m, 4); f->ul = (float*)take(N * m, 4);
-    f->yh = (float*)take(N * n, 4); f->yl = (float*)take(N * n, 4);
-  }
-  if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_maxes, 4 * sizeof(unsigned long long));
+  const size_t N = plan->N, T = (size_t)plan->n_trees;
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_maxes, 4 * T * sizeof(unsigned long long));
   if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_status, sizeof(int));
   if (err == cudaSuccess && f->dflag) err = cudaMemset(f->dflag, 0, N);
   if (err != cudaSuccess) {
@@ -974,6 +1061,26 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
     return err == cudaErrorMemoryAllocation ? TLQR_ERR_OOM : TLQR_ERR_CUDA;
   }
   *out = f;
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_factor_workspace_bytes(const tlqr_plan_t* plan, const tlqr_options* opts, size_t* bytes) {
+  if (!plan || !opts || !bytes) return TLQR_ERR_ARG;
+  if (opts->n < 1 || opts->m < 1 || opts->n > TLQR_MAX_DIM || opts->m > TLQR_MAX_DIM) return TLQR_ERR_ARG;
+  if (opts->precision != TLQR_PREC_FP64 && opts->precision != TLQR_PREC_MIXED) return TLQR_ERR_ARG;
+  tlqr_factor_t tmp;                       // host-side shell: no CUDA resources
+  tmp.plan = plan;
+  tmp.opt = *opts;
+  tmp.ts = opts->precision == TLQR_PREC_FP64 ? 8 : 4;
+  Carve c;
+  carve_factor(&tmp, c);
+  *bytes = c.off;
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_factor_bytes(const tlqr_factor_t* f, size_t* bytes) {
+  if (!f || !bytes) return TLQR_ERR_ARG;
+  *bytes = f->arena_bytes + f->stage_elems * sizeof(double);
   return TLQR_OK;
 }
 
@@ -1136,6 +1243,18 @@ extern "C" int tlqr_kkt_residual(tlqr_factor_t* f, const tlqr_problem* prob, int
   }
   if (run_residual(f, nullptr, dp, dx, du, dy, 1, st) || cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
   residual_stats(f, &stats[0], &stats[1]);
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_tree_residuals(const tlqr_factor_t* f, double* abs_res, double* eta, int32_t max_trees) {
+  if (!f || max_trees < 0) return TLQR_ERR_ARG;
+  const int T = std::min<int>(f->plan->n_trees, max_trees);
+  for (int t = 0; t < T; ++t) {
+    double a, e;
+    tree_stats(f, t, &a, &e);
+    if (abs_res) abs_res[t] = a;
+    if (eta) eta[t] = e;
+  }
   return TLQR_OK;
 }
 

@@ -6,7 +6,7 @@ the solver's arithmetic.  Both the CPU oracle and the CUDA path are fed from it.
 
 Conventions (shared by every consumer):
   * ``parent`` is an int32 array of length N with exactly one entry equal to -1
-    (the root).  Edge e=(i,j) is identified with its child j, so every edge
+    (the root); a batch of trees is a forest with one -1 per tree.  Edge e=(i,j) is identified with its child j, so every edge
     array is indexed by the child node and the root slot is unused (zeros).
   * Node arrays: Q (N,n,n), q (N,n), c (N,n), Delta (N,n,n) or None.
     Edge arrays (child-indexed): M (N,n,m) or None, R (N,m,m), r (N,m),
@@ -416,5 +416,90 @@ def recursive_batch(seed: int = BASE_SEED + 2, count: int = 1024, n: int = 16, m
     parents = [random_recursive(int(N), rng) for N in sizes]
     par, offs = forest(parents)
     data = problem_data(par, n, m, rng)
+    return Workload(f"recursive_batch_{count}x_n{n}_m{m}", par, n, m, data,
+                    info=dict(sizes=sizes, offsets=offs))
+
+
+# --------------------------------------------------------------------------
+# Device-side generation for the largest workloads
+# --------------------------------------------------------------------------
+
+def problem_data_device(parent: np.ndarray, n: int, m: int, seed: int, device, *,
+                        kappa_R: float | None = None, delta_fraction: float = 0.0,
+                        delta_value: float = 1e-6, A_scale: float = 0.95, chunk: int = 1 << 16) -> dict:
+    """The distributions of ``problem_data`` (M = 0) drawn on a CUDA device with
+    torch's seeded generator, chunk by chunk -- for workloads of 10^6 nodes and
+    n = 16..32 whose host generation would take minutes and tens of GB of host
+    memory.  Returns float64 device tensors keyed like ``problem_data``.  The
+    values are a deterministic function of (parent, n, m, seed, device type),
+    not the same numbers ``problem_data`` draws."""
+    import torch
+
+    N = len(parent)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = dict(dtype=torch.float64, device=device)
+    nonroot = torch.from_numpy(np.asarray(parent) >= 0).to(device)
+    A = torch.empty((N, n, n), **f64)
+    B = torch.empty((N, n, m), **f64)
+    Q = torch.empty((N, n, n), **f64)
+    R = torch.empty((N, m, m), **f64)
+    eye_n = torch.eye(n, **f64)
+    eye_m = torch.eye(m, **f64)
+    ev = None
+    if kappa_R is not None:
+        ev = torch.logspace(0.0, math.log10(kappa_R), m, **f64)
+
+    def haar(cnt, k):
+        q, r = torch.linalg.qr(torch.randn((cnt, k, k), generator=g, **f64))
+        d = torch.sign(torch.diagonal(r, dim1=1, dim2=2))
+        d[d == 0] = 1.0
+        return q * d[:, None, :]
+
+    for b in range(0, N, chunk):
+        e = min(N, b + chunk)
+        cnt = e - b
+        nr = nonroot[b:e]
+        A[b:e] = torch.where(nr[:, None, None], A_scale * haar(cnt, n), 0.0)
+        B[b:e] = torch.where(nr[:, None, None], torch.randn((cnt, n, m), generator=g, **f64) / math.sqrt(n), 0.0)
+        G = torch.randn((cnt, n, n), generator=g, **f64)
+        Q[b:e] = G @ G.transpose(1, 2) + 0.1 * eye_n
+        if ev is None:
+            H = torch.randn((cnt, m, m), generator=g, **f64)
+            Rc = eye_m + H @ H.transpose(1, 2)
+        else:
+            U = haar(cnt, m)
+            Rc = (U * ev[None, None, :]) @ U.transpose(1, 2)
+        R[b:e] = torch.where(nr[:, None, None], Rc, 0.0)
+    c = torch.randn((N, n), generator=g, **f64) * math.sqrt(0.1)
+    q = torch.randn((N, n), generator=g, **f64)
+    r = torch.randn((N, m), generator=g, **f64) * nonroot[:, None]
+    Delta = None
+    if delta_fraction > 0:
+        pick = (torch.rand((N,), generator=g, **f64) < delta_fraction) & nonroot
+        Delta = torch.zeros((N, n, n), **f64)
+        Delta[pick] = delta_value * eye_n
+    return dict(Q=Q, q=q, M=None, R=R, r=r, A=A, B=B, c=c, Delta=Delta)
+
+
+def spine_hybrid_device(device, seed: int = BASE_SEED + 3, N: int = 1 << 20, spine: int = 1 << 16,
+                        n: int = 32, m: int = 8, kappa_R: float = 1e2) -> Workload:
+    """The spine-plus-random-recursive-subtrees tree (N = 2^20, n = 32, m = 8)
+    with its data drawn on the device (R = U diag(logspace(0, log10 kappa, m)) U^T)."""
+    rng = rng_for(seed)
+    parent = spine_hybrid_tree(rng, N=N, spine=spine)
+    data = problem_data_device(parent, n, m, seed, device, kappa_R=kappa_R)
+    return Workload(f"spine_hybrid_N{N}_n{n}_m{m}_kR{kappa_R:g}", parent, n, m, data)
+
+
+def recursive_batch_device(device, seed: int = BASE_SEED + 2, count: int = 1024, n: int = 16, m: int = 4,
+                           lo: int = 64, hi: int = 16384) -> Workload:
+    """``recursive_batch`` (1,024 random recursive trees, sizes log-uniform in
+    [64, 16384], n = 16, m = 4) with its data drawn on the device."""
+    rng = rng_for(seed)
+    sizes = recursive_batch_sizes(rng, count, lo, hi)
+    parents = [random_recursive(int(k), rng) for k in sizes]
+    par, offs = forest(parents)
+    data = problem_data_device(par, n, m, seed, device)
     return Workload(f"recursive_batch_{count}x_n{n}_m{m}", par, n, m, data,
                     info=dict(sizes=sizes, offsets=offs))

@@ -72,7 +72,8 @@ EXPORTS = ["tlqr_plan_create", "tlqr_plan_create_forest", "tlqr_plan_destroy", "
            "tlqr_get_PK", "tlqr_kkt_residual", "tlqr_last_info", "tlqr_status_string",
            "tlqr_batched_tau", "tlqr_batched_compose", "tlqr_batched_condense",
            "tlqr_lift_node_controls", "tlqr_project_lifted", "tlqr_profile_mask", "tlqr_profile_read",
-           "tlqr_kkt_residual_noalloc", "tlqr_profile_launches"]
+           "tlqr_kkt_residual_noalloc", "tlqr_profile_launches", "tlqr_tree_residuals",
+           "tlqr_factor_workspace_bytes", "tlqr_factor_bytes"]
 
 KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
                 "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
@@ -114,6 +115,9 @@ def lib():
         L.tlqr_project_lifted.argtypes = [_i32, _i32, _i32, _ip] + [_dp] * 6
         L.tlqr_profile_mask.argtypes = [_vp, ctypes.c_uint32]
         L.tlqr_profile_read.argtypes = [_vp, ctypes.POINTER(tlqr_kernel_profile)]
+        L.tlqr_factor_workspace_bytes.argtypes = [_vp, ctypes.POINTER(tlqr_options), ctypes.POINTER(ctypes.c_size_t)]
+        L.tlqr_factor_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.tlqr_tree_residuals.argtypes = [_vp, _dp, _dp, _i32]
         L.tlqr_profile_launches.argtypes = [_vp, _ip, ctypes.POINTER(ctypes.c_int64), _dp, _i32, _ip]
         L.tlqr_kkt_residual_noalloc.argtypes = [_vp, _i32, _i32, ctypes.POINTER(tlqr_problem), _dp, _dp, _dp, _dp, _vp]
         _lib = L
@@ -231,6 +235,18 @@ def tlqr_factor_create(plan, opts: tlqr_options) -> ctypes.c_void_p:
     return h
 
 
+def tlqr_factor_workspace_bytes(plan, opts: tlqr_options) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().tlqr_factor_workspace_bytes(plan, ctypes.byref(opts), ctypes.byref(b)), "tlqr_factor_workspace_bytes")
+    return int(b.value)
+
+
+def tlqr_factor_bytes(f) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().tlqr_factor_bytes(f, ctypes.byref(b)), "tlqr_factor_bytes")
+    return int(b.value)
+
+
 def tlqr_factor_destroy(f) -> None:
     lib().tlqr_factor_destroy(f)
 
@@ -295,6 +311,14 @@ def tlqr_last_info(f) -> dict:
     i = tlqr_info()
     _check(lib().tlqr_last_info(f, ctypes.byref(i)), "tlqr_last_info")
     return dict(refine_steps=i.refine_steps, eta=i.eta, abs_residual=i.abs_residual)
+
+
+def tlqr_tree_residuals(f, n_trees: int):
+    """Per-tree (||K z - b||, eta) of the last residual evaluation, as two arrays."""
+    a = np.zeros(max(1, n_trees))
+    e = np.zeros(max(1, n_trees))
+    _check(lib().tlqr_tree_residuals(f, _ptr(a), _ptr(e), n_trees), "tlqr_tree_residuals")
+    return a[:n_trees], e[:n_trees]
 
 
 def tlqr_profile_mask(f, kinds) -> None:

@@ -1,0 +1,101 @@
+"""CPU tests of the benchmark harness: the reference arm (the oracle timed on
+host cores) prints one well-formed JSON line, also as rank 0 of a two-rank
+gloo job whose other rank exits without work; and the per-round roofline
+bookkeeping matches launches to the plan's rounds exactly."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2608_01332_b300 import inputs, tlqr
+from tests.conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+        "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"}
+
+
+def _run(args, env=None, timeout=600):
+    out = subprocess.run([sys.executable, *args], cwd=ROOT, capture_output=True, text=True, timeout=timeout,
+                         env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    return out.stdout
+
+
+def test_reference_arm_line():
+    line = _run(["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1", "--total", "2048",
+                 "--ref-seconds", "2"])
+    rows = [json.loads(s) for s in line.splitlines() if s.startswith("{")]
+    assert len(rows) == 1
+    d = rows[0]
+    assert KEYS <= set(d) and d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["config"]["N"] == 2048
+
+
+def test_reference_arm_two_rank_gloo():
+    """torchrun with two CPU ranks: rank 0 alone prints; the job exits 0."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    line = _run(["-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2", "--master-addr=127.0.0.1",
+                 "--master-port=29517", "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                 "--warmup", "1", "--total", "1024", "--ref-seconds", "1"], env=env)
+    rows = [json.loads(s) for s in line.splitlines() if s.startswith("{")]
+    assert len(rows) == 1 and rows[0]["n_gpus"] == 2
+
+
+def _fake_launches(parent, seed=0):
+    """The launch sequence run_factor issues for this plan (kinds, operation
+    counts in the order of the rounds), with made-up durations."""
+    h = tlqr.tlqr_plan_create(parent)
+    try:
+        rnd, op = tlqr.tlqr_plan_schedule(h, len(parent))
+    finally:
+        tlqr.tlqr_plan_destroy(h)
+    R = int(rnd.max())
+    nr = np.bincount(rnd[op == tlqr.TLQR_OP_RAKE], minlength=R + 1)
+    nc = np.bincount(rnd[op == tlqr.TLQR_OP_COMPRESS], minlength=R + 1)
+    rng = np.random.default_rng(seed)
+    L = []
+    for r in range(1, R + 1):
+        if nr[r]:
+            L.append(("rake", int(nr[r]), float(rng.uniform(0.01, 0.02))))
+            L.append(("absorb", max(1, int(nr[r]) // 2), 0.005))
+        if nc[r]:
+            L.append(("compress", int(nc[r]), float(rng.uniform(0.01, 0.03))))
+    for r in range(R, 0, -1):
+        if nc[r]:
+            L.append(("expand", int(nc[r]), 0.01))
+    for r in range(1, R + 1):
+        if nc[r]:
+            L.append(("compose_T", int(nc[r]), 0.004))
+    return L, rnd, op, nr, nc
+
+
+@pytest.mark.parametrize("tree", ["long_trunk", "recursive", "chain"])
+def test_round_roofline_bookkeeping(tree):
+    rng = inputs.rng_for(90)
+    parent = {"long_trunk": lambda: inputs.long_trunk_tree(rng, trunk=300, total=3000),
+              "recursive": lambda: inputs.random_recursive(2000, rng),
+              "chain": lambda: inputs.chain(500)}[tree]()
+    L, rnd, op, nr, nc = _fake_launches(parent)
+    n, m = 12, 4
+    rows = bench.round_roofline(L, rnd, op, n, m, 4, 6500.0, 76.9, tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)
+    assert [r["round"] for r in rows] == list(range(1, int(rnd.max()) + 1))
+    assert abs(sum(r["ms"] for r in rows) - sum(x[2] for x in L)) < 1e-12
+    fr, br = bench.per_unit("rake", n, m, 4)
+    fc, bc = bench.per_unit("compress", n, m, 4)
+    for r in rows:
+        k = r["round"]
+        assert r["rakes"] == nr[k] and r["compresses"] == nc[k]
+        assert r["flops"] >= fr * nr[k] + fc * nc[k]
+        assert r["roof_ms"] > 0 and r["bound"] in ("hbm", "alu")
+    # a launch list that disagrees with the plan is refused
+    bad = [(k, u + 1, t) if k == "compress" else (k, u, t) for k, u, t in L]
+    if any(k == "compress" for k, _, _ in L):
+        with pytest.raises(RuntimeError):
+            bench.round_roofline(bad, rnd, op, n, m, 4, 6500.0, 76.9, tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)

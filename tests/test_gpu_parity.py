@@ -51,6 +51,8 @@ def gpu_solve(parent, n, m, data, precision=FP64, host=False, want_PK=True, **kw
             out = dict(x=x.cpu().numpy(), u=u.cpu().numpy(), y=y.cpu().numpy(),
                        P=None if P is None else P.cpu().numpy(), K=None if K is None else K.cpu().numpy())
         out["info"] = tlqr.tlqr_last_info(s.f)
+        if kw.get("forest"):
+            out["tree_eta"] = tlqr.tlqr_tree_residuals(s.f, s.stats()["n_trees"])[1]
         return out
     finally:
         s.close()
@@ -416,8 +418,51 @@ def test_forest_batch_equals_trees_alone(n, m):
         for k in ("x", "u", "y", "P", "K"):
             np.testing.assert_array_equal(batch[k][sl], alone[k])
     mixed = gpu_solve(par, n, m, data, precision=MIXED, want_PK=False, forest=True)
+    assert len(mixed["tree_eta"]) == len(trees)
     for t, p in enumerate(trees):
         sl = slice(offs[t], offs[t] + len(p))
         sub = {k: mixed[k][sl] for k in ("x", "u", "y")}
         res = riccati.kkt_residual(p, n, m, datas[t], sub["x"], sub["u"], sub["y"])
         assert res["eta"] <= 1e-8
+        # the refinement's own per-tree eta (float-float residual, FP32 row sums of |K|)
+        assert abs(mixed["tree_eta"][t] - res["eta"]) <= 1e-3 * res["eta"] + 1e-15
+    assert mixed["info"]["eta"] == mixed["tree_eta"].max()
+
+
+@pytest.mark.parametrize("permute", [False, True])
+def test_forest_residual_is_per_tree(permute):
+    """tlqr_kkt_residual on a forest: per-tree ||K z - b|| and eta equal the
+    oracle's residual of each tree on its own (FP64 kernel), also when the
+    forest's labels are permuted so that trees interleave in memory."""
+    n, m = 5, 2
+    rng = inputs.rng_for(720 + permute)
+    trees = [inputs.random_recursive(int(rng.integers(1, 400)), rng) for _ in range(12)]
+    datas = [inputs.problem_data(p, n, m, rng, delta="subset", delta_value=0.05) for p in trees]
+    par, offs = inputs.forest(trees)
+    data = inputs.concat_data(datas)
+    # a perturbed solution so that the residual is well above rounding
+    x = rng.standard_normal((len(par), n)); u = rng.standard_normal((len(par), m)); y = rng.standard_normal((len(par), n))
+    owner = np.concatenate([np.full(len(p), t) for t, p in enumerate(trees)])
+    if permute:
+        par2, perm = inputs.permute_labels(par, rng)
+        data = inputs.permute_data(data, perm)
+        inv = np.argsort(perm)
+        x, u, y, owner = x[inv], u[inv], y[inv], owner[inv]
+        par = par2
+    s = tlqr.TreeLQR(par, n, m, FP64, has_delta=True, forest=True)
+    try:
+        stats = tlqr.tlqr_kkt_residual(s.f, {k: dev(v) for k, v in data.items()}, dev(x), dev(u), dev(y))
+        absr, eta = tlqr.tlqr_tree_residuals(s.f, len(trees))
+    finally:
+        s.close()
+    roots = np.nonzero(np.asarray(par) < 0)[0]          # tree ordinals follow increasing root label
+    for t, rt in enumerate(roots):
+        sel = np.nonzero(owner == owner[rt])[0]
+        pos = np.full(len(par), -1)
+        pos[sel] = np.arange(len(sel))
+        sub = np.where(par[sel] < 0, -1, pos[par[sel]]).astype(np.int32)
+        d_t = {k: (None if v is None else v[sel]) for k, v in data.items()}
+        ref = riccati.kkt_residual(sub, n, m, d_t, x[sel], u[sel], y[sel])
+        assert abs(absr[t] - ref["abs"]) <= 1e-12 * ref["abs"]
+        assert abs(eta[t] - ref["eta"]) <= 1e-12 * ref["eta"]
+    assert stats["eta"] == eta.max()
