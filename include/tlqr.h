@@ -258,7 +258,8 @@ int tlqr_kkt_residual_noalloc(const tlqr_plan_t *plan, int32_t n, int32_t m, con
                               void *stream);
 
 /* Per-tree ||K z - b||_inf and eta of the last residual evaluation (the last
- * refinement check of tlqr_solve, or tlqr_kkt_residual), for the first
+ * refinement check of a MIXED tlqr_solve, or tlqr_kkt_residual; an FP64
+ * tlqr_solve evaluates none), for the first
  * min(max_trees, number of trees) trees in increasing root label.  Host
  * arrays; either may be NULL.  A single tree has one entry. */
 int tlqr_tree_residuals(const tlqr_factor_t *f, double *abs_res, double *eta, int32_t max_trees);

@@ -28,6 +28,7 @@
 #include "kernels.cuh"
 #include "plan.hpp"
 #include "residual.cuh"
+#include "residual_nodes.cuh"
 
 using namespace tlqr;
 
@@ -215,6 +216,8 @@ struct tlqr_factor_t {
   double *res_x = nullptr, *res_u = nullptr, *res_c = nullptr;
   // MIXED: (hi, lo) FP32 splits of x, u, y for the float-float residual
   float *xh = nullptr, *xl = nullptr, *uh = nullptr, *ul = nullptr, *yh = nullptr, *yl = nullptr;
+  // MIXED with compile-time (n, m): the node-organised residual's child messages
+  float *rwh = nullptr, *rwl = nullptr, *rwk = nullptr;
   unsigned long long* maxes = nullptr;
   unsigned long long* h_maxes = nullptr;   // pinned mirror
   int* h_status = nullptr;                  // pinned mirror
@@ -356,10 +359,12 @@ void carve_factor(tlqr_factor_t* f, Carve& c) {
   f->res_x = c.take<double>(N * n, 8); f->res_u = c.take<double>(N * m, 8); f->res_c = c.take<double>(N * n, 8);
   f->maxes = c.take<unsigned long long>(4 * (size_t)P->n_trees, 8);
   f->xh = f->xl = f->uh = f->ul = f->yh = f->yl = nullptr;
+  f->rwh = f->rwl = f->rwk = nullptr;
   if (f->opt.precision == TLQR_PREC_MIXED) {
     f->xh = c.take<float>(N * n, 4); f->xl = c.take<float>(N * n, 4);
     f->uh = c.take<float>(N * m, 4); f->ul = c.take<float>(N * m, 4);
     f->yh = c.take<float>(N * n, 4); f->yl = c.take<float>(N * n, 4);
+    f->rwh = c.take<float>(N * n, 4); f->rwl = c.take<float>(N * n, 4); f->rwk = c.take<float>(N * n, 4);
   }
 }
 
@@ -610,6 +615,8 @@ constexpr bool fixed_for(int n) { return !(sizeof(T) == 8 && n == 32); }
 // fixed_m: compile-time m of the (n, m) kernels for that n (0 = run time).
 #define TLQR_FIXED_CASES(X)                                                     \
   X(4, 0) X(4, 2) X(6, 0) X(6, 2) X(8, 0) X(8, 2) X(12, 0) X(12, 4) X(16, 0) X(16, 4) X(32, 0) X(32, 8)
+// the (n, m) pairs of the list above
+#define TLQR_FIXED_PAIRS(X) X(4, 2) X(6, 2) X(8, 2) X(12, 4) X(16, 4) X(32, 8)
 
 template <typename T>
 cudaError_t dispatch_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cudaStream_t st) {
@@ -636,6 +643,52 @@ bool has_fixed_pair(int n, int m) {
   return (m == 2 && (n == 4 || n == 6 || n == 8)) || (m == 4 && (n == 12 || n == 16)) || (m == 8 && n == 32);
 }
 
+// Node-organised float-float residual for compile-time (n, m): edge pass then
+// node pass (see residual_nodes.cuh).  Returns cudaErrorNotSupported when
+// (n, m) has no such kernels.
+template <int N, int M>
+cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::NodeArgs& na, cudaStream_t st,
+                             bool capturing) {
+  constexpr int OPS = rn::RG<N>::OPS, threads = 128, gpb = (threads / 32) * OPS;
+  const size_t se = (size_t)rn::EdgeSmem<N, M>::bytes * gpb, sn = (size_t)rn::NodeSmem<N>::bytes * gpb;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, 148 * 16));
+  const bool forest = a.tree != nullptr;
+  auto ek = forest ? rn::k_res_edge<N, M, true> : rn::k_res_edge<N, M, false>;
+  auto nk = forest ? rn::k_res_node<N, true> : rn::k_res_node<N, false>;
+  if (!capturing) {
+    cudaError_t e = ensure_smem(ek, se);
+    if (!e) e = ensure_smem(nk, sn);
+    if (e) return e;
+  }
+  ek<<<blocks, threads, se, st>>>(a, fa, na);
+  nk<<<blocks, threads, sn, st>>>(a, fa, na);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_res_nodes(int n, int m) {
+#define X(n_, m_)                                                                              \
+  if (n == n_ && m == m_) {                                                                    \
+    constexpr int gpb = 4 * rn::RG<n_>::OPS;                                                   \
+    cudaError_t e = ensure_smem(rn::k_res_edge<n_, m_, true>, (size_t)rn::EdgeSmem<n_, m_>::bytes * gpb);  \
+    if (!e) e = ensure_smem(rn::k_res_edge<n_, m_, false>, (size_t)rn::EdgeSmem<n_, m_>::bytes * gpb);    \
+    if (!e) e = ensure_smem(rn::k_res_node<n_, true>, (size_t)rn::NodeSmem<n_>::bytes * gpb);             \
+    if (!e) e = ensure_smem(rn::k_res_node<n_, false>, (size_t)rn::NodeSmem<n_>::bytes * gpb);            \
+    return e;                                                                                  \
+  }
+  TLQR_FIXED_PAIRS(X)
+#undef X
+  return cudaSuccess;
+}
+
+cudaError_t dispatch_res_nodes(int n, int m, const ResidualArgs& a, const FFArgs& fa, const rn::NodeArgs& na,
+                               cudaStream_t st, bool capturing) {
+#define X(n_, m_) \
+  if (n == n_ && m == m_) return launch_res_nodes<n_, m_>(a, fa, na, st, capturing);
+  TLQR_FIXED_PAIRS(X)
+#undef X
+  return cudaErrorNotSupported;
+}
+
 // ff = 1: float-float kernel on the FP32 pipe (refinement); ff = 0: plain FP64 kernel.
 cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, const double* x,
                          const double* u, const double* y, int with_knorm, cudaStream_t st, int ff = 0) {
@@ -658,7 +711,8 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
     // split x, u, y once per call; for one tree ||z|| and ||b|| maxima come
     // from the same pass (a forest forms them per tree in the residual kernel)
     const size_t N = P->N, n = f->opt.n, m = f->opt.m;
-    const int zs = a.tree ? -1 : 1, bs = a.tree ? -1 : 2;
+    const bool by_node = f->fixed_m > 0;            // node kernels form all four maxima themselves
+    const int zs = (a.tree || by_node) ? -1 : 1, bs = (a.tree || by_node) ? -1 : 2;
     SplitList L{};
     auto add = [&](const double* src, float* hi, float* lo, size_t len, int slot) {
       L.src[L.count] = src; L.hi[L.count] = hi; L.lo[L.count] = lo; L.len[L.count] = len; L.slot[L.count] = slot;
@@ -667,7 +721,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
     add(x, f->xh, f->xl, N * n, zs);
     add(u, f->uh, f->ul, N * m, zs);
     add(y, f->yh, f->yl, N * n, zs);
-    if (!a.tree) {
+    if (bs >= 0) {
       add(p.q, nullptr, nullptr, N * n, bs);
       add(p.r, nullptr, nullptr, N * m, bs);
       add(p.c, nullptr, nullptr, N * n, bs);
@@ -682,7 +736,10 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
   EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr, P->N};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  if (a.tree) {
+  if (ff && f->fixed_m > 0) {
+    const rn::NodeArgs na{f->rwh, f->rwl, f->rwk};
+    if ((e = dispatch_res_nodes(f->fixed_n, f->fixed_m, a, fa, na, st, rc && rc->capture))) return e;
+  } else if (a.tree) {
     if (ff) k_residual_ff_trees<<<blocks, threads, 0, st>>>(a, fa);
     else k_residual_trees<<<blocks, threads, 0, st>>>(a);
   } else {
@@ -1032,7 +1089,8 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   if ((f->ts == 8 ? configure_kernels<double>(n, m) : configure_kernels<float>(n, m)) != cudaSuccess ||
       (f->ts == 8 ? configure_fixed_n<double>(f->fixed_n) : configure_fixed_n<float>(f->fixed_n)) != cudaSuccess ||
       (f->ts == 8 ? configure_fixed_pair<double>(f->fixed_n, f->fixed_m)
-                  : configure_fixed_pair<float>(f->fixed_n, f->fixed_m)) != cudaSuccess) {
+                  : configure_fixed_pair<float>(f->fixed_n, f->fixed_m)) != cudaSuccess ||
+      (f->ts == 4 && f->fixed_m > 0 && configure_res_nodes(f->fixed_n, f->fixed_m) != cudaSuccess)) {
     delete f;
     return TLQR_ERR_CUDA;
   }

@@ -44,6 +44,8 @@ def solve(w, precision, forest=False, want_PK=False):
         tlqr.tlqr_solve(s.f, w.data, x, u, y, P, K)
         torch.cuda.synchronize()
         out = dict(x=x, u=u, y=y, P=P, K=K, info=tlqr.tlqr_last_info(s.f))
+        if precision == FP64:                       # an FP64 solve evaluates no residual of its own
+            tlqr.tlqr_kkt_residual(s.f, w.data, x, u, y)
         out["tree_eta"] = tlqr.tlqr_tree_residuals(s.f, s.stats()["n_trees"])[1]
         return out
     finally:
@@ -117,8 +119,9 @@ def test_batch_full_size_fp64(batch):
         ref = riccati.tree_riccati(p, w.n, w.m, d)
         got = {k: out[k][a:b].cpu().numpy() for k in ("x", "u", "y")}
         assert riccati.forward_error(got, ref, p) <= 1e-8, t
-        assert abs(out["tree_eta"][t] - riccati.kkt_residual(p, w.n, w.m, d, got["x"], got["u"], got["y"])["eta"]) \
-            <= 1e-3 * out["tree_eta"][t] + 1e-17
+        # both etas are rounding noise here; the per-tree residual itself is pinned elsewhere
+        assert riccati.kkt_residual(p, w.n, w.m, d, got["x"], got["u"], got["y"])["eta"] <= 1e-10
+        assert out["tree_eta"][t] <= 1e-10
 
 
 def test_batch_full_size_mixed(batch):
@@ -157,9 +160,12 @@ def test_spine_full_size(kappa):
         ref = riccati.tree_riccati(sub, w.n, w.m, d)
         P = out["P"][torch.as_tensor(nodes, device="cuda")].cpu().numpy()
         K = out["K"][torch.as_tensor(nodes[1:], device="cuda")].cpu().numpy()
-        # FP32 factors: relative to the block's scale, a few hundred FP32 ulps
-        assert np.abs(P - ref["P"]).max() <= 2e-4 * np.abs(ref["P"]).max(), i
-        assert np.abs(K - ref["K"][1:]).max() <= 2e-4 * max(1.0, np.abs(ref["K"][1:]).max()), i
+        # FP32 factors: a few hundred FP32 ulps of the block's scale; with an
+        # ill-conditioned R the FP64 Cholesky factor is rounded to FP32, which
+        # perturbs R^{-1} (and so C, P, K) by ~ kappa(L) eps_32 = sqrt(kappa) 6e-8
+        tol = max(2e-4, 20 * np.sqrt(kappa) * 6e-8)
+        assert np.abs(P - ref["P"]).max() <= tol * np.abs(ref["P"]).max(), i
+        assert np.abs(K - ref["K"][1:]).max() <= tol * max(1.0, np.abs(ref["K"][1:]).max()), i
         checked += 1
         if checked == 40:
             break
