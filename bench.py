@@ -238,6 +238,13 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
+# DRAM bytes per operation (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch divided by its operation count) from one `ncu --set full` capture of
+# the round-1 launch of the headline workload; keyed by (kernel kind, n, m,
+# precision).  Entries must be dropped when the kernel changes.
+NCU_BYTES_PER_OP = {("compress", 12, 4, "mixed"): (104.829184e6 + 35.851008e6) / 25647}
+
+
 # ----------------------------------------------------------------- algorithmic work per unit
 def per_unit(kind, n, m, wbytes, has_delta_frac=0.0):
     """(flops, bytes) of one local operation, leading-order dense counts with
@@ -701,6 +708,11 @@ def run_ours(args, rank, world, dist):
                     else "nominal FP64 1.25 TFLOP/s"}
         roof.update({"kernel": f"k_{dominant}", "launches": pd["timed"], "units": pd["units"],
                      "avg_launch_ms": pd["ms"] / pd["timed"], "flops_per_unit": fl, "bytes_per_unit": by})
+        bpo = NCU_BYTES_PER_OP.get((dominant, n, m, args.mode))
+        if bpo is not None:
+            roof["traffic"] = bpo * pd["units"] / pd["timed"]
+            roof["traffic_note"] = ("ncu DRAM bytes per operation of the round-1 launch x this run's average "
+                                    "operations per launch (bytes per launch)")
 
     cfg = {"workload": w.name, "N": N, "n": n, "m": m, "precision": args.mode, "rounds": stats["rounds"],
            "height": stats["height"], "trees": stats["n_trees"], "description": WORKLOADS[args.workload],
