@@ -469,43 +469,55 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------- per-round roofline
-ROUND_KINDS = ("rake", "absorb", "compress", "expand", "compose_T")
+ROUND_KINDS = ("rake", "absorb", "compress", "expand", "compose_T", "factor_tail")
 
 
 def round_roofline(launches, rnd, op, n, m, wbytes, hbm_gbs, alu_tflops, rake_code, comp_code):
     """Per structural round of the factorisation: algorithmic flops and bytes of
     its rake, absorb and compress launches (and of the reverse expansion and
     T-composite launches of the same round), the measured time, and the
-    roofline time max(bytes / HBM, flops / ALU peak)."""
+    roofline time max(bytes / HBM, flops / ALU peak).  The late rounds that the
+    library runs in one block (its factor tail kernel and composite tail
+    kernel) form one row together.
+
+    launches: (kind, operations, ms) in launch order for one factorisation."""
     R = int(rnd.max()) if len(rnd) else 0
     nr = np.bincount(rnd[op == rake_code], minlength=R + 1)
     nc = np.bincount(rnd[op == comp_code], minlength=R + 1)
-    by_kind = {k: [rec for rec in launches if rec[0] == k] for k in ROUND_KINDS}
-    it = {k: iter(v) for k, v in by_kind.items()}
+    seq = [rec for rec in launches if rec[0] in ROUND_KINDS]
+    pos = 0
     s = n * (n + 1) / 2
     rows = {r: dict(round=r, rakes=int(nr[r]), compresses=int(nc[r]), flops=0.0, bytes=0.0, ms=0.0)
             for r in range(1, R + 1)}
 
     def take(kind, r, units_expected=None):
-        rec = next(it[kind], None)
-        if rec is None:
-            return None
-        _, units, ms = rec
+        nonlocal pos
+        if pos >= len(seq) or seq[pos][0] != kind:
+            got = seq[pos][0] if pos < len(seq) else "end"
+            raise RuntimeError(f"round {r}: expected a {kind} launch, found {got}")
+        _, units, ms = seq[pos]
+        pos += 1
         if units_expected is not None and units != units_expected:
             raise RuntimeError(f"round {r}: {kind} launch of {units} operations, plan has {units_expected}")
         return units, ms
 
-    def add(r, kind, units, ms, n_contrib=0):
+    def work(kind, units, n_contrib=0):
         if kind == "absorb":                       # sum contributions into U_i: reads nr + 2 ns packed blocks
-            fl, by = n * n * n_contrib, (n_contrib + 2 * units) * s * wbytes
-        else:
-            fl1, by1 = per_unit(kind, n, m, wbytes)
-            fl, by = fl1 * units, by1 * units
+            return n * n * n_contrib, (n_contrib + 2 * units) * s * wbytes
+        fl1, by1 = per_unit(kind, n, m, wbytes)
+        return fl1 * units, by1 * units
+
+    def add(r, kind, units, ms, n_contrib=0):
+        fl, by = work(kind, units, n_contrib)
         rows[r]["flops"] += fl
         rows[r]["bytes"] += by
         rows[r]["ms"] += ms
 
-    for r in range(1, R + 1):                       # launch order of the forward rounds
+    r0 = R + 1                                      # first round of the tail (none: R + 1)
+    for r in range(1, R + 1):                       # forward rounds
+        if pos < len(seq) and seq[pos][0] == "factor_tail":
+            r0 = r
+            break
         if nr[r]:
             u, ms = take("rake", r, int(nr[r]))
             add(r, "rake", u, ms)
@@ -514,22 +526,36 @@ def round_roofline(launches, rnd, op, n, m, wbytes, hbm_gbs, alu_tflops, rake_co
         if nc[r]:
             u, ms = take("compress", r, int(nc[r]))
             add(r, "compress", u, ms)
-    for r in range(R, 0, -1):                       # reverse expansion
+    tail_ms = 0.0
+    if r0 <= R:
+        tail_ms += take("factor_tail", r0)[1]
+    for r in range(min(R, r0 - 1), 0, -1):          # reverse expansion of the head rounds
         if nc[r]:
             u, ms = take("expand", r, int(nc[r]))
             add(r, "expand", u, ms)
-    for r in range(1, R + 1):                       # T composites of the compressions
+    for r in range(1, min(R, r0 - 1) + 1):          # T composites of the head rounds
         if nc[r]:
             u, ms = take("compose_T", r, int(nc[r]))
             add(r, "compose_T", u, ms)
+    if r0 <= R:
+        tail_ms += take("factor_tail", r0)[1]
     out = []
-    for r in range(1, R + 1):
-        row = rows[r]
+    for r in range(1, min(R, r0 - 1) + 1):
+        out.append(rows[r])
+    if r0 <= R:
+        t = dict(round=f"{r0}-{R} (tail)", rakes=int(nr[r0:].sum()), compresses=int(nc[r0:].sum()),
+                 flops=0.0, bytes=0.0, ms=tail_ms)
+        for r in range(r0, R + 1):
+            for kind, cnt in (("rake", nr[r]), ("compress", nc[r]), ("expand", nc[r]), ("compose_T", nc[r])):
+                fl, by = work(kind, int(cnt))
+                t["flops"] += fl
+                t["bytes"] += by
+        out.append(t)
+    for row in out:
         t_roof = max(row["bytes"] / (hbm_gbs * 1e9), row["flops"] / (alu_tflops * 1e12))
         row["roof_ms"] = 1e3 * t_roof
         row["frac"] = (1e3 * t_roof / row["ms"]) if row["ms"] > 0 else None
         row["bound"] = "hbm" if row["bytes"] / (hbm_gbs * 1e9) >= row["flops"] / (alu_tflops * 1e12) else "alu"
-        out.append(row)
     return out
 
 
@@ -640,7 +666,7 @@ def run_ours(args, rank, world, dist):
         half = len(launches) // 2                  # two identical steps were recorded: keep the second
         per_round = round_roofline(launches[half:], rnd, op, n, m, wbytes, hbm, alu,
                                    tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)
-    except (RuntimeError, StopIteration, TypeError) as e:
+    except RuntimeError as e:
         per_round = {"error": str(e)}
 
     # plain FP64 contraction on the same GPU (the comparison of the metric)

@@ -1,7 +1,8 @@
 // Float-float KKT residual of eq. (kkt), organised by node for compile-time
-// (n, m): one group of G lanes per node, the node's FP64 blocks staged once
-// into shared memory with coalesced loads and split into (hi, lo) FP32 pairs
-// there, lane r owning row r.  Every FP64 matrix entry is read from HBM
+// (n, m): one group of G lanes per node, lane r owning row r.  Each node's
+// FP64 blocks are copied into shared memory with asynchronous 8-byte copies
+// (cp.async), double-buffered so that the next node's blocks are in flight
+// while the current node is computed; every FP64 matrix entry is read from HBM
 // exactly once per evaluation (the row-per-thread kernels of residual.cuh read
 // A_j and B_j twice and walk Q by strided rows).
 //
@@ -26,20 +27,24 @@ template <int N>
 struct RG {
   static constexpr int G = N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
   static constexpr int OPS = 32 / G;          // nodes per warp
-  static constexpr int LDP = N + 1;           // padded row stride (conflict-free rows and columns)
 };
 
-// Stage an R x C FP64 block (row-major, contiguous) as (hi, lo) FP32 planes
-// with row stride LDS; entries are read coalesced by the group.
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+// Asynchronous copy of an R x C FP64 block (contiguous rows) into shared rows
+// of stride LDS, by the G lanes of a group.
 template <int R, int C, int LDS, int G>
-__device__ __forceinline__ void stage_split(float* h, float* l, const double* src, int gl) {
+__device__ __forceinline__ void stage_async(double* dst, const double* src, int gl) {
 #pragma unroll 4
   for (int e = gl; e < R * C; e += G) {
     const int a = e / C, b = e - (e / C) * C;
-    float hh, ll;
-    dsplit(src[e], hh, ll);
-    h[a * LDS + b] = hh;
-    l[a * LDS + b] = ll;
+    cp_async8(dst + a * LDS + b, src + e);
   }
 }
 
@@ -64,7 +69,6 @@ struct NodeArgs {
   float* wk;          // [N][n] absolute column sums of [A_j^T | M_j] (when with_knorm)
 };
 
-// Per-lane maxima: one tree (block fold at the end) or per tree (TreeAcc).
 struct Maxima {
   unsigned long long v[4] = {0ull, 0ull, 0ull, 0ull};
   __device__ __forceinline__ void take(const unsigned long long (&r)[4]) {
@@ -73,46 +77,66 @@ struct Maxima {
   }
 };
 
+// Shared-memory layout of one edge-pass buffer (doubles): A, [Delta], B, [M], R.
 template <int N, int M>
-struct EdgeSmem {
-  static constexpr int LDP = RG<N>::LDP, MLD = M + 1;
-  // A (hi, lo), Delta (hi, lo): N x LDP; B (hi, lo): N x MLD; M (hi, lo): N x MLD; R (hi, lo): M x MLD;
-  // vectors x_p, y_j (hi, lo): N; u_j (hi, lo): M
-  static constexpr int floats = 4 * N * LDP + 4 * N * MLD + 2 * M * MLD + 4 * N + 2 * M;
-  static constexpr int bytes = ((floats * 4 + 15) / 16) * 16;
+struct EdgeBuf {
+  static constexpr int LDA = N + 1, LDB = M + 1;
+  __host__ __device__ static constexpr int doubles(bool has_delta, bool has_M) {
+    return N * LDA * (has_delta ? 2 : 1) + N * LDB * (has_M ? 2 : 1) + M * LDB;
+  }
+  // per group: two buffers + the float-float vectors x_p, y_j (N each), u_j (M), hi and lo
+  __host__ __device__ static constexpr int group_bytes(bool has_delta, bool has_M) {
+    return ((2 * doubles(has_delta, has_M) * 8 + (4 * N + 2 * M) * 4) + 15) / 16 * 16;
+  }
 };
 
 // Edge pass.  FOREST: fold maxima per tree.
 template <int N, int M, bool FOREST>
 __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, NodeArgs na) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using R_ = RG<N>;
-  constexpr int G = R_::G, OPS = R_::OPS, LDP = R_::LDP, MLD = M + 1;
+  using EB = EdgeBuf<N, M>;
+  constexpr int G = RG<N>::G, OPS = RG<N>::OPS, LDA = EB::LDA, LDB = EB::LDB;
+  const bool hd = a.Delta != nullptr, hm = a.M != nullptr, ks = a.with_knorm;
   const int gl = threadIdx.x & (G - 1), gid = (threadIdx.x & 31) / G;
-  float* sm = reinterpret_cast<float*>(smem_raw + ((threadIdx.x >> 5) * OPS + gid) * EdgeSmem<N, M>::bytes);
-  float *sAh = sm, *sAl = sAh + N * LDP, *sDh = sAl + N * LDP, *sDl = sDh + N * LDP;
-  float *sBh = sDl + N * LDP, *sBl = sBh + N * MLD, *sMh = sBl + N * MLD, *sMl = sMh + N * MLD;
-  float *sRh = sMl + N * MLD, *sRl = sRh + M * MLD;
-  float *vxh = sRl + M * MLD, *vxl = vxh + N, *vyh = vxl + N, *vyl = vyh + N, *vuh = vyl + N, *vul = vuh + M;
-  const bool ks = a.with_knorm;
+  const int nd = EB::doubles(hd, hm);
+  unsigned char* gbase = smem_raw + (size_t)((threadIdx.x >> 5) * OPS + gid) * EB::group_bytes(hd, hm);
+  double* buf0 = reinterpret_cast<double*>(gbase);
+  float* vxh = reinterpret_cast<float*>(gbase + 2 * (size_t)nd * 8);
+  float *vxl = vxh + N, *vyh = vxl + N, *vyl = vyh + N, *vuh = vyl + N, *vul = vuh + M;
+  const size_t nn = (size_t)N * N, nm = (size_t)N * M;
+  auto issue = [&](int j, double* b) {
+    double* sA = b;
+    double* sD = sA + N * LDA;
+    double* sB = sD + (hd ? N * LDA : 0);
+    double* sM = sB + N * LDB;
+    double* sR = sM + (hm ? N * LDB : 0);
+    if (a.parent[j] >= 0) {
+      stage_async<N, N, LDA, G>(sA, a.A + (size_t)j * nn, gl);
+      stage_async<N, M, LDB, G>(sB, a.B + (size_t)j * nm, gl);
+      stage_async<M, M, LDB, G>(sR, a.R + (size_t)j * M * M, gl);
+      if (hm) stage_async<N, M, LDB, G>(sM, a.M + (size_t)j * nm, gl);
+    }
+    if (hd) stage_async<N, N, LDA, G>(sD, a.Delta + (size_t)j * nn, gl);
+  };
   const NodeRange nr = warp_nodes<OPS>(a.N);
   Maxima mx;
   TreeAcc acc;
-  for (int base = nr.begin; base < nr.end; base += OPS) {
+  if (nr.begin < nr.end) issue(nr.begin + gid < nr.end ? nr.begin + gid : nr.end - 1, buf0);
+  cp_async_commit();
+  int t = 0;
+  for (int base = nr.begin; base < nr.end; base += OPS, ++t) {
     const int j0 = base + gid;
     const bool valid = j0 < nr.end;
     const int j = valid ? j0 : nr.end - 1;
+    double* cur = buf0 + (t & 1) * nd;
+    if (base + OPS < nr.end) {                           // prefetch this group's next node
+      const int jn = base + OPS + gid < nr.end ? base + OPS + gid : nr.end - 1;
+      issue(jn, buf0 + ((t + 1) & 1) * nd);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
     const int p = a.parent[j];
     const bool has_p = p >= 0;
-    const size_t nn = (size_t)N * N, nm = (size_t)N * M;
-    // stage this node's blocks
-    if (has_p) {
-      stage_split<N, N, LDP, G>(sAh, sAl, a.A + (size_t)j * nn, gl);
-      stage_split<N, M, MLD, G>(sBh, sBl, a.B + (size_t)j * nm, gl);
-      stage_split<M, M, MLD, G>(sRh, sRl, a.R + (size_t)j * M * M, gl);
-      if (a.M) stage_split<N, M, MLD, G>(sMh, sMl, a.M + (size_t)j * nm, gl);
-    }
-    if (a.Delta) stage_split<N, N, LDP, G>(sDh, sDl, a.Delta + (size_t)j * nn, gl);
     if (gl < N) {
       vyh[gl] = f.yh[(size_t)j * N + gl];
       vyl[gl] = f.yl[(size_t)j * N + gl];
@@ -124,104 +148,84 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
       vul[gl] = f.ul[(size_t)j * M + gl];
     }
     __syncwarp();
+    const double* sA = cur;
+    const double* sD = sA + N * LDA;
+    const double* sB = sD + (hd ? N * LDA : 0);
+    const double* sM = sB + N * LDB;
+    const double* sR = sM + (hm ? N * LDB : 0);
     const int r = gl < N ? gl : 0;
     unsigned long long row[4] = {0ull, 0ull, 0ull, 0ull};
     // constraint row r entering j
     {
-      const size_t t = (size_t)j * N + r;
+      const size_t tr = (size_t)j * N + r;
       FF s{0.f, 0.f};
-      ff_add(s, a.c[t]);
-      ff_add2(s, -f.xh[t], -f.xl[t]);
+      ff_add(s, a.c[tr]);
+      ff_add2(s, -f.xh[tr], -f.xl[tr]);
       float rs = 1.f;
-      if (a.Delta) {
+      if (hd) {
 #pragma unroll 8
-        for (int b = 0; b < N; ++b) {
-          ff_fma2(s, sDh[r * LDP + b], sDl[r * LDP + b], -vyh[b], -vyl[b]);
-          rs += fabsf(sDh[r * LDP + b]);
-        }
+        for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sD[r * LDA + b], -vyh[b], -vyl[b]);
       }
       if (has_p) {
 #pragma unroll 8
-        for (int b = 0; b < N; ++b) {
-          ff_fma2(s, sAh[r * LDP + b], sAl[r * LDP + b], vxh[b], vxl[b]);
-          rs += fabsf(sAh[r * LDP + b]);
-        }
+        for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sA[r * LDA + b], vxh[b], vxl[b]);
 #pragma unroll
-        for (int c = 0; c < M; ++c) {
-          ff_fma2(s, sBh[r * MLD + c], sBl[r * MLD + c], vuh[c], vul[c]);
-          rs += fabsf(sBh[r * MLD + c]);
-        }
+        for (int c = 0; c < M; ++c) rs += ff_fma_d(s, sB[r * LDB + c], vuh[c], vul[c]);
       }
       const double out = ff_value(s);
-      if (valid && gl < N) a.res_c[t] = out;
+      if (valid && gl < N) a.res_c[tr] = out;
       if (gl < N) {
         row[0] = abits(out);
         row[3] = ks ? abits(f2d_bits(rs)) : 0ull;
       }
     }
-    // control row gl of the edge into j (lanes gl < M), and the message w_j
-    {
-      unsigned long long ur = 0ull, uk = 0ull;
-      if (has_p && gl < M) {
-        const size_t tu = (size_t)j * M + gl;
+    // control row gl of the edge into j (lanes gl < M)
+    if (gl < M) {
+      const size_t tu = (size_t)j * M + gl;
+      if (has_p) {
         FF s{0.f, 0.f};
         ff_add(s, a.r[tu]);
         float rs = 0.f;
-        if (a.M) {
+        if (hm) {
 #pragma unroll 8
-          for (int b = 0; b < N; ++b) {
-            ff_fma2(s, sMh[b * MLD + gl], sMl[b * MLD + gl], vxh[b], vxl[b]);
-            rs += fabsf(sMh[b * MLD + gl]);
-          }
+          for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sM[b * LDB + gl], vxh[b], vxl[b]);
         }
 #pragma unroll
-        for (int c = 0; c < M; ++c) {
-          ff_fma2(s, sRh[gl * MLD + c], sRl[gl * MLD + c], vuh[c], vul[c]);
-          rs += fabsf(sRh[gl * MLD + c]);
-        }
+        for (int c = 0; c < M; ++c) rs += ff_fma_d(s, sR[gl * LDB + c], vuh[c], vul[c]);
 #pragma unroll 8
-        for (int b = 0; b < N; ++b) {
-          ff_fma2(s, sBh[b * MLD + gl], sBl[b * MLD + gl], vyh[b], vyl[b]);
-          rs += fabsf(sBh[b * MLD + gl]);
-        }
+        for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sB[b * LDB + gl], vyh[b], vyl[b]);
         const double out = ff_value(s);
         if (valid) a.res_u[tu] = out;
-        ur = abits(out);
-        uk = ks ? abits(f2d_bits(rs)) : 0ull;
-      } else if (!has_p && gl < M && valid) {
-        a.res_u[(size_t)j * M + gl] = 0.0;
+        const unsigned long long ob = abits(out), kb = ks ? abits(f2d_bits(rs)) : 0ull;
+        row[0] = ob > row[0] ? ob : row[0];
+        row[3] = kb > row[3] ? kb : row[3];
+      } else if (valid) {
+        a.res_u[tu] = 0.0;
       }
-      row[0] = ur > row[0] ? ur : row[0];
-      row[3] = uk > row[3] ? uk : row[3];
-      if (has_p && gl < N) {
-        FF wv{0.f, 0.f};
-        float wk = 0.f;
+    }
+    // message w_j = A_j^T y_j + M_j u_j to the parent's stationarity rows
+    if (has_p && gl < N) {
+      FF wv{0.f, 0.f};
+      float wk = 0.f;
 #pragma unroll 8
-        for (int b = 0; b < N; ++b) {
-          ff_fma2(wv, sAh[b * LDP + r], sAl[b * LDP + r], vyh[b], vyl[b]);
-          wk += fabsf(sAh[b * LDP + r]);
-        }
-        if (a.M) {
+      for (int b = 0; b < N; ++b) wk += ff_fma_d(wv, sA[b * LDA + r], vyh[b], vyl[b]);
+      if (hm) {
 #pragma unroll
-          for (int c = 0; c < M; ++c) {
-            ff_fma2(wv, sMh[r * MLD + c], sMl[r * MLD + c], vuh[c], vul[c]);
-            wk += fabsf(sMh[r * MLD + c]);
-          }
-        }
-        if (valid) {
-          na.wh[(size_t)j * N + r] = wv.h;
-          na.wl[(size_t)j * N + r] = wv.l;
-          if (ks) na.wk[(size_t)j * N + r] = wk;
-        }
+        for (int c = 0; c < M; ++c) wk += ff_fma_d(wv, sM[r * LDB + c], vuh[c], vul[c]);
+      }
+      if (valid) {
+        na.wh[(size_t)j * N + r] = wv.h;
+        na.wl[(size_t)j * N + r] = wv.l;
+        if (ks) na.wk[(size_t)j * N + r] = wk;
       }
     }
     // ||z|| and ||b||: u_j, r_j (edge) and x_j, y_j, q_j, c_j (node) entries of this node
     {
       double zv = 0.0, bv = 0.0;
       if (gl < N) {
-        const size_t t = (size_t)j * N + gl;
-        zv = amax(amax(0.0, a.x[t]), a.y[t]);
-        bv = fmax(fabs(a.q[t]), fabs(a.c[t]));
+        const size_t tr = (size_t)j * N + gl;
+        zv = amax(amax(0.0, a.x[tr]), a.y[tr]);
+        bv = fmax(fabs(a.q[tr]), fabs(a.c[tr]));
       }
       if (has_p && gl < M) {
         zv = amax(zv, a.u[(size_t)j * M + gl]);
@@ -235,8 +239,9 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
     } else if (valid) {
       mx.take(row);
     }
-    __syncwarp();
+    __syncwarp();                                        // buffer and vectors free for reuse
   }
+  cp_async_wait<0>();
   if constexpr (FOREST) {
     acc.flush(a, ks ? 4 : 3);
   } else {
@@ -247,53 +252,64 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
 }
 
 template <int N>
-struct NodeSmem {
-  static constexpr int LDP = RG<N>::LDP;
-  static constexpr int floats = 2 * N * LDP + 2 * N;      // Q (hi, lo), x_i (hi, lo)
-  static constexpr int bytes = ((floats * 4 + 15) / 16) * 16;
+struct NodeBuf {
+  static constexpr int LDQ = N + 1;
+  static constexpr int doubles = N * LDQ;
+  static constexpr int group_bytes = ((2 * doubles * 8 + 2 * N * 4) + 15) / 16 * 16;
 };
 
 // Node pass: stationarity rows Q_i x_i + q_i - y_i + sum_children w_j.
 template <int N, bool FOREST>
 __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, NodeArgs na) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using R_ = RG<N>;
-  constexpr int G = R_::G, OPS = R_::OPS, LDP = R_::LDP;
+  using NB = NodeBuf<N>;
+  constexpr int G = RG<N>::G, OPS = RG<N>::OPS, LDQ = NB::LDQ;
   const int gl = threadIdx.x & (G - 1), gid = (threadIdx.x & 31) / G;
-  float* sm = reinterpret_cast<float*>(smem_raw + ((threadIdx.x >> 5) * OPS + gid) * NodeSmem<N>::bytes);
-  float *sQh = sm, *sQl = sQh + N * LDP, *vxh = sQl + N * LDP, *vxl = vxh + N;
+  unsigned char* gbase = smem_raw + (size_t)((threadIdx.x >> 5) * OPS + gid) * NB::group_bytes;
+  double* buf0 = reinterpret_cast<double*>(gbase);
+  float* vxh = reinterpret_cast<float*>(gbase + 2 * (size_t)NB::doubles * 8);
+  float* vxl = vxh + N;
   const bool ks = a.with_knorm;
   const NodeRange nr = warp_nodes<OPS>(a.N);
   Maxima mx;
   TreeAcc acc;
-  for (int base = nr.begin; base < nr.end; base += OPS) {
+  if (nr.begin < nr.end) {
+    const int i0 = nr.begin + gid < nr.end ? nr.begin + gid : nr.end - 1;
+    stage_async<N, N, LDQ, G>(buf0, a.Q + (size_t)i0 * N * N, gl);
+  }
+  cp_async_commit();
+  int t = 0;
+  for (int base = nr.begin; base < nr.end; base += OPS, ++t) {
     const int i0 = base + gid;
     const bool valid = i0 < nr.end;
     const int i = valid ? i0 : nr.end - 1;
-    stage_split<N, N, LDP, G>(sQh, sQl, a.Q + (size_t)i * N * N, gl);
+    const double* sQ = buf0 + (t & 1) * NB::doubles;
+    if (base + OPS < nr.end) {
+      const int in = base + OPS + gid < nr.end ? base + OPS + gid : nr.end - 1;
+      stage_async<N, N, LDQ, G>(buf0 + ((t + 1) & 1) * NB::doubles, a.Q + (size_t)in * N * N, gl);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
     if (gl < N) {
       vxh[gl] = f.xh[(size_t)i * N + gl];
       vxl[gl] = f.xl[(size_t)i * N + gl];
     }
     __syncwarp();
     const int r = gl < N ? gl : 0;
-    const size_t t = (size_t)i * N + r;
+    const size_t tr = (size_t)i * N + r;
     FF s{0.f, 0.f};
-    ff_add(s, a.q[t]);
-    ff_add2(s, -f.yh[t], -f.yl[t]);
+    ff_add(s, a.q[tr]);
+    ff_add2(s, -f.yh[tr], -f.yl[tr]);
     float rs = 1.f;
 #pragma unroll 8
-    for (int b = 0; b < N; ++b) {
-      ff_fma2(s, sQh[r * LDP + b], sQl[r * LDP + b], vxh[b], vxl[b]);
-      rs += fabsf(sQh[r * LDP + b]);
-    }
+    for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sQ[r * LDQ + b], vxh[b], vxl[b]);
     for (int k = a.child_start[i]; k < a.child_start[i + 1]; ++k) {
       const int jc = a.child_list[k];
       ff_add2(s, na.wh[(size_t)jc * N + r], na.wl[(size_t)jc * N + r]);
       if (ks) rs += na.wk[(size_t)jc * N + r];
     }
     const double out = ff_value(s);
-    if (valid && gl < N) a.res_x[t] = out;
+    if (valid && gl < N) a.res_x[tr] = out;
     unsigned long long row[4] = {0ull, 0ull, 0ull, 0ull};
     if (gl < N) {
       row[0] = abits(out);
@@ -306,6 +322,7 @@ __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, Node
     }
     __syncwarp();
   }
+  cp_async_wait<0>();
   if constexpr (FOREST) {
     acc.flush(a, ks ? 4 : 3);
   } else {

@@ -190,10 +190,15 @@ constexpr float kCholRatio = 100.0f;
 // In-place Cholesky of an m x m SPD matrix (row-major, lda) in FP64 by one
 // thread, left-looking (row by row); the lower triangle receives L.  False
 // when a pivot is not positive and finite.
-__device__ inline bool chol64_serial(double* a, int m, int lda) {
+// Not inlined: it runs rarely, on shared memory, and must not add registers to
+// the kernels that call it.
+__device__ __noinline__ bool chol64_serial(double* a, int m, int lda) {
+#pragma unroll 1
   for (int k = 0; k < m; ++k) {
+#pragma unroll 1
     for (int i = 0; i <= k; ++i) {
       double v = a[k * lda + i];
+#pragma unroll 1
       for (int t = 0; t < i; ++t) v = fma(-a[k * lda + t], a[i * lda + t], v);
       if (i < k) {
         a[k * lda + i] = v / a[i * lda + i];

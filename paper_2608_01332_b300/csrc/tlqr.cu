@@ -438,6 +438,38 @@ cudaError_t launch_tail(Recorder* rc, int kind, Kernel kernel, cudaStream_t st, 
   return e;
 }
 
+// One block of `threads` threads with `smem` bytes of dynamic shared memory.
+template <typename Kernel, typename... Args>
+cudaError_t launch_block(Recorder* rc, int kind, Kernel kernel, int threads, size_t smem, cudaStream_t st,
+                         Args... args) {
+  if (!(rc && rc->capture)) {
+    cudaError_t e = ensure_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
+  }
+  const bool timed = rc && (rc->mask >> kind) & 1u;
+  EvPair ev{kind, nullptr, nullptr, 1};
+  if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
+  kernel<<<1, threads, smem, st>>>(args...);
+  cudaError_t e = cudaGetLastError();
+  if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
+  if (rc) { rc->launches[kind]++; rc->units[kind] += 1; }
+  return e;
+}
+
+// First round of the factorisation's tail: the longest suffix of rounds whose
+// phases each hold at most three block-loads of operations.
+template <typename T, int N>
+int factor_tail_start(const tlqr_plan_t* P) {
+  const int lim = 3 * fx::FactorTail<T, N>::gpb;
+  int r0 = (int)P->rounds.size();
+  while (r0 > 0) {
+    const tlqr_round& r = P->rounds[r0 - 1];
+    if (std::max({r.rake_end - r.rake_begin, r.seg_end - r.seg_begin, r.comp_end - r.comp_begin}) > lim) break;
+    --r0;
+  }
+  return r0;
+}
+
 cudaError_t launch_split(Recorder* rc, const SplitList& L, cudaStream_t st) {
   const int blocks = 148 * 4, threads = 256;
   k_split_ff<<<blocks, threads, 0, st>>>(L);
@@ -464,7 +496,11 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
   } else if ((e = launch_warps(rc, TLQR_K_CONDENSE, k_condense<T>, P->N, wb.condense, st, w, (int)wb.condense))) {
     return e;
   }
-  for (const tlqr_round& rd : P->rounds) {
+  const int R = (int)P->rounds.size();
+  int ft0 = R;                                  // rounds ft0..R-1 run in the factor tail kernel
+  if constexpr (NF > 0) ft0 = factor_tail_start<T, NX>(P);
+  for (int ri = 0; ri < ft0; ++ri) {
+    const tlqr_round& rd = P->rounds[ri];
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
     if constexpr (NF > 0) {
       if ((e = launch_groups(rc, TLQR_K_RAKE, fx::kf_rake<T, NX>, nr, G, fx::TauSmem<T, NX>::bytes, st, w,
@@ -481,7 +517,14 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
       return e;
     }
   }
-  for (auto it = P->rounds.rbegin(); it != P->rounds.rend(); ++it) {
+  if constexpr (NF > 0) {
+    using FT = fx::FactorTail<T, NX>;
+    if (ft0 < R && (e = launch_block(rc, TLQR_K_FACTOR_TAIL, fx::kf_factor_tail<T, NX>, FT::threads,
+                                     (size_t)FT::smem, st, w, f->d_rounds, ft0, R)))
+      return e;
+  }
+  for (int ri = ft0 - 1; ri >= 0; --ri) {
+    const tlqr_round* it = &P->rounds[ri];
     const int nc = it->comp_end - it->comp_begin;
     if constexpr (NF > 0) {
       if ((e = launch_groups(rc, TLQR_K_EXPAND, fx::kf_expand<T, NX>, nc, G, fx::TauSmem<T, NX>::bytes, st, w,
@@ -497,7 +540,8 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
                                (int)wb.local_factor))) {
     return e;
   }
-  for (const tlqr_round& rd : P->rounds) {
+  for (int ri = 0; ri < ft0; ++ri) {
+    const tlqr_round& rd = P->rounds[ri];
     const int nc = rd.comp_end - rd.comp_begin;
     if constexpr (NF > 0) {
       if ((e = launch_groups(rc, TLQR_K_COMPOSE_T, fx::kf_compose_T<T, NX>, nc, G, fx::ComposeSmem<T, NX>::bytes, st,
@@ -506,6 +550,12 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
                                  (int)wb.compose_T))) {
       return e;
     }
+  }
+  if constexpr (NF > 0) {
+    using FT = fx::FactorTail<T, NX>;
+    if (ft0 < R && (e = launch_block(rc, TLQR_K_FACTOR_TAIL, fx::kf_compose_tail<T, NX>, FT::threads,
+                                     (size_t)FT::gpb * fx::ComposeSmem<T, NX>::bytes, st, w, f->d_rounds, ft0, R)))
+      return e;
   }
   return cudaSuccess;
 }
@@ -650,7 +700,8 @@ template <int N, int M>
 cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::NodeArgs& na, cudaStream_t st,
                              bool capturing) {
   constexpr int OPS = rn::RG<N>::OPS, threads = 128, gpb = (threads / 32) * OPS;
-  const size_t se = (size_t)rn::EdgeSmem<N, M>::bytes * gpb, sn = (size_t)rn::NodeSmem<N>::bytes * gpb;
+  const size_t se = (size_t)rn::EdgeBuf<N, M>::group_bytes(a.Delta != nullptr, a.M != nullptr) * gpb;
+  const size_t sn = (size_t)rn::NodeBuf<N>::group_bytes * gpb;
   const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, 148 * 16));
   const bool forest = a.tree != nullptr;
   auto ek = forest ? rn::k_res_edge<N, M, true> : rn::k_res_edge<N, M, false>;
@@ -669,10 +720,12 @@ cudaError_t configure_res_nodes(int n, int m) {
 #define X(n_, m_)                                                                              \
   if (n == n_ && m == m_) {                                                                    \
     constexpr int gpb = 4 * rn::RG<n_>::OPS;                                                   \
-    cudaError_t e = ensure_smem(rn::k_res_edge<n_, m_, true>, (size_t)rn::EdgeSmem<n_, m_>::bytes * gpb);  \
-    if (!e) e = ensure_smem(rn::k_res_edge<n_, m_, false>, (size_t)rn::EdgeSmem<n_, m_>::bytes * gpb);    \
-    if (!e) e = ensure_smem(rn::k_res_node<n_, true>, (size_t)rn::NodeSmem<n_>::bytes * gpb);             \
-    if (!e) e = ensure_smem(rn::k_res_node<n_, false>, (size_t)rn::NodeSmem<n_>::bytes * gpb);            \
+    const size_t se = (size_t)rn::EdgeBuf<n_, m_>::group_bytes(true, true) * gpb;                \
+    const size_t sn = (size_t)rn::NodeBuf<n_>::group_bytes * gpb;                                 \
+    cudaError_t e = ensure_smem(rn::k_res_edge<n_, m_, true>, se);                                \
+    if (!e) e = ensure_smem(rn::k_res_edge<n_, m_, false>, se);                                   \
+    if (!e) e = ensure_smem(rn::k_res_node<n_, true>, sn);                                        \
+    if (!e) e = ensure_smem(rn::k_res_node<n_, false>, sn);                                       \
     return e;                                                                                  \
   }
   TLQR_FIXED_PAIRS(X)
@@ -962,6 +1015,8 @@ cudaError_t configure_fixed() {
   cudaError_t e = ensure_smem(fx::kf_rake<T, N>, (size_t)fx::TauSmem<T, N>::bytes * gpb);
   if (!e) e = ensure_smem(fx::kf_expand<T, N>, (size_t)fx::TauSmem<T, N>::bytes * gpb);
   if (!e) e = ensure_smem(fx::kf_compress<T, N>, (size_t)fx::CompSmem<T, N>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_factor_tail<T, N>, (size_t)fx::FactorTail<T, N>::smem);
+  if (!e) e = ensure_smem(fx::kf_compose_tail<T, N>, (size_t)fx::FactorTail<T, N>::gpb * fx::ComposeSmem<T, N>::bytes);
   if (!e) e = ensure_smem(fx::kf_compose_T<T, N>, (size_t)fx::ComposeSmem<T, N>::bytes * gpb);
   return e;
 }

@@ -48,9 +48,10 @@ def test_reference_arm_two_rank_gloo():
     assert len(rows) == 1 and rows[0]["n_gpus"] == 2
 
 
-def _fake_launches(parent, seed=0):
+def _fake_launches(parent, seed=0, tail_from=None):
     """The launch sequence run_factor issues for this plan (kinds, operation
-    counts in the order of the rounds), with made-up durations."""
+    counts in the order of the rounds; rounds >= tail_from in the tail
+    kernels), with made-up durations."""
     h = tlqr.tlqr_plan_create(parent)
     try:
         rnd, op = tlqr.tlqr_plan_schedule(h, len(parent))
@@ -60,19 +61,24 @@ def _fake_launches(parent, seed=0):
     nr = np.bincount(rnd[op == tlqr.TLQR_OP_RAKE], minlength=R + 1)
     nc = np.bincount(rnd[op == tlqr.TLQR_OP_COMPRESS], minlength=R + 1)
     rng = np.random.default_rng(seed)
+    head = R if tail_from is None else tail_from - 1
     L = []
-    for r in range(1, R + 1):
+    for r in range(1, head + 1):
         if nr[r]:
             L.append(("rake", int(nr[r]), float(rng.uniform(0.01, 0.02))))
             L.append(("absorb", max(1, int(nr[r]) // 2), 0.005))
         if nc[r]:
             L.append(("compress", int(nc[r]), float(rng.uniform(0.01, 0.03))))
-    for r in range(R, 0, -1):
+    if head < R:
+        L.append(("factor_tail", 1, 0.05))
+    for r in range(head, 0, -1):
         if nc[r]:
             L.append(("expand", int(nc[r]), 0.01))
-    for r in range(1, R + 1):
+    for r in range(1, head + 1):
         if nc[r]:
             L.append(("compose_T", int(nc[r]), 0.004))
+    if head < R:
+        L.append(("factor_tail", 1, 0.02))
     return L, rnd, op, nr, nc
 
 
@@ -99,3 +105,15 @@ def test_round_roofline_bookkeeping(tree):
     if any(k == "compress" for k, _, _ in L):
         with pytest.raises(RuntimeError):
             bench.round_roofline(bad, rnd, op, n, m, 4, 6500.0, 76.9, tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)
+
+
+def test_round_roofline_with_tail_rounds():
+    rng = inputs.rng_for(91)
+    parent = inputs.long_trunk_tree(rng, trunk=300, total=3000)
+    L, rnd, op, nr, nc = _fake_launches(parent, tail_from=6)
+    rows = bench.round_roofline(L, rnd, op, 12, 4, 4, 6500.0, 76.9, tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)
+    R = int(rnd.max())
+    assert [r["round"] for r in rows[:-1]] == [1, 2, 3, 4, 5]
+    assert rows[-1]["round"] == f"6-{R} (tail)" and abs(rows[-1]["ms"] - 0.07) < 1e-12
+    assert rows[-1]["rakes"] == int(nr[6:].sum()) and rows[-1]["compresses"] == int(nc[6:].sum())
+    assert abs(sum(r["ms"] for r in rows) - sum(x[2] for x in L)) < 1e-12
