@@ -48,6 +48,20 @@ __device__ __forceinline__ void stage_async(double* dst, const double* src, int 
   }
 }
 
+// s += sum_b a[b * STRIDE] * (xh[b] + xl[b]) (sign -1: minus), with four
+// independent float-float accumulators to shorten the dependent chain; returns
+// the FP32 sum of |a_hi| for the absolute row sums.
+template <int K, int STRIDE>
+__device__ __forceinline__ float ff_dot(FF& s, const double* a, const float* xh, const float* xl, float sign = 1.f) {
+  FF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  float rs = 0.f;
+#pragma unroll
+  for (int b = 0; b < K; ++b) rs += ff_fma_d(acc[b & 3], a[b * STRIDE], sign * xh[b], sign * xl[b]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ff_add2(s, acc[q].h, acc[q].l);
+  return rs;
+}
+
 // Warp-contiguous node ranges: warp w handles nodes [w*C, (w+1)*C), OPS at a time.
 struct NodeRange {
   int begin, end;
@@ -162,15 +176,10 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
       ff_add(s, a.c[tr]);
       ff_add2(s, -f.xh[tr], -f.xl[tr]);
       float rs = 1.f;
-      if (hd) {
-#pragma unroll 8
-        for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sD[r * LDA + b], -vyh[b], -vyl[b]);
-      }
+      if (hd) rs += ff_dot<N, 1>(s, sD + r * LDA, vyh, vyl, -1.f);
       if (has_p) {
-#pragma unroll 8
-        for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sA[r * LDA + b], vxh[b], vxl[b]);
-#pragma unroll
-        for (int c = 0; c < M; ++c) rs += ff_fma_d(s, sB[r * LDB + c], vuh[c], vul[c]);
+        rs += ff_dot<N, 1>(s, sA + r * LDA, vxh, vxl);
+        rs += ff_dot<M, 1>(s, sB + r * LDB, vuh, vul);
       }
       const double out = ff_value(s);
       if (valid && gl < N) a.res_c[tr] = out;
@@ -186,14 +195,9 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
         FF s{0.f, 0.f};
         ff_add(s, a.r[tu]);
         float rs = 0.f;
-        if (hm) {
-#pragma unroll 8
-          for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sM[b * LDB + gl], vxh[b], vxl[b]);
-        }
-#pragma unroll
-        for (int c = 0; c < M; ++c) rs += ff_fma_d(s, sR[gl * LDB + c], vuh[c], vul[c]);
-#pragma unroll 8
-        for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sB[b * LDB + gl], vyh[b], vyl[b]);
+        if (hm) rs += ff_dot<N, LDB>(s, sM + gl, vxh, vxl);
+        rs += ff_dot<M, 1>(s, sR + gl * LDB, vuh, vul);
+        rs += ff_dot<N, LDB>(s, sB + gl, vyh, vyl);
         const double out = ff_value(s);
         if (valid) a.res_u[tu] = out;
         const unsigned long long ob = abits(out), kb = ks ? abits(f2d_bits(rs)) : 0ull;
@@ -206,13 +210,8 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
     // message w_j = A_j^T y_j + M_j u_j to the parent's stationarity rows
     if (has_p && gl < N) {
       FF wv{0.f, 0.f};
-      float wk = 0.f;
-#pragma unroll 8
-      for (int b = 0; b < N; ++b) wk += ff_fma_d(wv, sA[b * LDA + r], vyh[b], vyl[b]);
-      if (hm) {
-#pragma unroll
-        for (int c = 0; c < M; ++c) wk += ff_fma_d(wv, sM[r * LDB + c], vuh[c], vul[c]);
-      }
+      float wk = ff_dot<N, LDA>(wv, sA + r, vyh, vyl);
+      if (hm) wk += ff_dot<M, 1>(wv, sM + r * LDB, vuh, vul);
       if (valid) {
         na.wh[(size_t)j * N + r] = wv.h;
         na.wl[(size_t)j * N + r] = wv.l;
@@ -300,9 +299,7 @@ __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, Node
     FF s{0.f, 0.f};
     ff_add(s, a.q[tr]);
     ff_add2(s, -f.yh[tr], -f.yl[tr]);
-    float rs = 1.f;
-#pragma unroll 8
-    for (int b = 0; b < N; ++b) rs += ff_fma_d(s, sQ[r * LDQ + b], vxh[b], vxl[b]);
+    float rs = 1.f + ff_dot<N, 1>(s, sQ + r * LDQ, vxh, vxl);
     for (int k = a.child_start[i]; k < a.child_start[i + 1]; ++k) {
       const int jc = a.child_list[k];
       ff_add2(s, na.wh[(size_t)jc * N + r], na.wl[(size_t)jc * N + r]);

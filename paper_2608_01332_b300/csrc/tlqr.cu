@@ -457,10 +457,15 @@ cudaError_t launch_block(Recorder* rc, int kind, Kernel kernel, int threads, siz
 }
 
 // First round of the factorisation's tail: the longest suffix of rounds whose
-// phases each hold at most three block-loads of operations.
+// phases each hold at most kFactorTailOps operations.  One block runs a phase's
+// operations side by side on one SM, so the tail only pays where a phase is a
+// handful of operations and launch gaps outweigh the shared SM; for n = 32 a
+// single operation's latency (~0.1 ms) dominates and no tail is used.
+constexpr int kFactorTailOps = 8;
 template <typename T, int N>
 int factor_tail_start(const tlqr_plan_t* P) {
-  const int lim = 3 * fx::FactorTail<T, N>::gpb;
+  if (N > 16) return (int)P->rounds.size();
+  const int lim = std::min(kFactorTailOps, fx::FactorTail<T, N>::gpb);
   int r0 = (int)P->rounds.size();
   while (r0 > 0) {
     const tlqr_round& r = P->rounds[r0 - 1];
