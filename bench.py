@@ -213,7 +213,8 @@ def workload(args, device=None):
         device = "cuda" if torch.cuda.is_available() else "cpu"
     if args.workload == "batch":
         return inputs.recursive_batch_device(device, count=args.count), True
-    return inputs.spine_hybrid_device(device, N=args.total or (1 << 20), kappa_R=args.kappa), False
+    N = args.total or (1 << 20)                     # spine of N / 16 nodes (2^16 at full size)
+    return inputs.spine_hybrid_device(device, N=N, spine=max(1, N >> 4), kappa_R=args.kappa), False
 
 
 def host_slice(w, a, b):

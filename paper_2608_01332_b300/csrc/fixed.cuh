@@ -16,6 +16,7 @@
 // all register indexing is static.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -30,8 +31,11 @@ template <typename T, int N>
 struct D {
   static constexpr int G = N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
   static constexpr int W = Vec<T>::W;
-  static constexpr int LD = (N + W - 1) / W * W;       // padded row stride (elements)
-  static constexpr int NV = LD / W;                    // vectors per row
+  static constexpr int NV = (N + W - 1) / W;          // vectors per row
+  // padded row stride (elements): a whole number of 16-byte vectors, and an odd
+  // one, so that the rows owned by consecutive lanes start in different
+  // shared-memory bank quads (conflict-free 16-byte row accesses)
+  static constexpr int LD = (NV % 2 == 1 ? NV : NV + 1) * W;
   static constexpr int OPS = 32 / G;                   // operations per warp
   static constexpr int MAT = N * LD;                   // elements of one staged matrix
 };
@@ -108,6 +112,43 @@ __device__ __forceinline__ void row_store(T* row, const T (&a)[N]) {
 #pragma unroll
     for (int i = 0; i < W; ++i) vset(v, i, q * W + i < N ? a[q * W + i] : T(0));
     reinterpret_cast<V*>(row)[q] = v;
+  }
+}
+
+// A length-N row of a node block in global memory (row-major, rows of N
+// elements, blocks 256-byte aligned): 16-byte vector accesses when a row is a
+// whole number of vectors, else element by element.
+template <typename T, int N>
+__device__ __forceinline__ void grow_load(T (&a)[N], const T* row) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+  if constexpr ((N * sizeof(T)) % 16 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / W; ++q) {
+      const V v = reinterpret_cast<const V*>(row)[q];
+#pragma unroll
+      for (int i = 0; i < W; ++i) a[q * W + i] = vget<T>(v, i);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; ++c) a[c] = row[c];
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void grow_store(T* row, const T (&a)[N]) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+  if constexpr ((N * sizeof(T)) % 16 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / W; ++q) {
+      V v;
+#pragma unroll
+      for (int i = 0; i < W; ++i) vset(v, i, a[q * W + i]);
+      reinterpret_cast<V*>(row)[q] = v;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; ++c) row[c] = a[c];
   }
 }
 
@@ -298,13 +339,14 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   if (g.gl < N) row_store<T, N>(sU + r * LD, z); // Z over U
   __syncwarp();
   T o[N];
+  if constexpr (std::is_same<S, T>::value) {
+    grow_load<T, N>(o, Pg + r * N);
+  } else {
 #pragma unroll
-  for (int j = 0; j < N; ++j) o[j] = (T)Pg[r * N + j];
-  col_mm<T, N, N, LD, LD>(o, sA, r, sU);        // P + A^T Z
-  if (g.valid && g.gl < N) {
-#pragma unroll
-    for (int j = 0; j < N; ++j) out[r * N + j] = o[j];
+    for (int j = 0; j < N; ++j) o[j] = (T)Pg[r * N + j];
   }
+  col_mm<T, N, N, LD, LD>(o, sA, r, sU);        // P + A^T Z
+  if (g.valid && g.gl < N) grow_store<T, N>(out + r * N, o);
   return ok;
 }
 
@@ -338,7 +380,10 @@ __global__ void kf_expand(Ws<T> w, int begin, int count) {
 // 2N columns), bc (2 LD), order.
 template <typename T, int N>
 struct CompSmem {
-  static constexpr int LD2 = 2 * D<T, N>::LD;             // [Y1 | Y2] row stride, Y2 at column LD
+  // [Y1 | Y2]: Y2 at column YW (N rounded up to whole vectors); row stride an
+  // odd number of vectors (conflict-free row stores)
+  static constexpr int YW = D<T, N>::NV * D<T, N>::W;
+  static constexpr int LD2 = (2 * D<T, N>::NV + 1) * D<T, N>::W;
   static constexpr int elems = 4 * D<T, N>::MAT + N * LD2 + LD2;
   static constexpr int bytes = elems * (int)sizeof(T) + ((N * 4 + 15) / 16) * 16;
 };
@@ -346,7 +391,8 @@ struct CompSmem {
 template <typename T, int N>
 __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g, T* sm) {
   using Dm = D<T, N>;
-  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, LD2 = CompSmem<T, N>::LD2, NN = N * N;
+  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, LD2 = CompSmem<T, N>::LD2, YW = CompSmem<T, N>::YW;
+  constexpr int NN = N * N;
   T *sPt = sm, *sAl = sm + MAT, *sCl = sm + 2 * MAT, *sAr = sm + 3 * MAT, *sY = sm + 4 * MAT,
     *bc = sm + 4 * MAT + N * LD2;
   int* order = reinterpret_cast<int*>(bc + LD2);
@@ -363,7 +409,7 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   gload<T, N, N, LD, G>(sCl, w.Ec + oj, gl);
   gload<T, N, N, LD, G>(sAr, w.Ea + ok_, gl);
   __syncwarp();
-  T s[N], b[2 * LD];
+  T s[N], b[2 * YW];
   {
     T cl[N], t1[N], t2[N];
     row_load<T, N>(cl, sCl + r * LD);
@@ -375,14 +421,14 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
     zero(t2);
     row_mmT<T, N, N, LD>(t2, cl, sAr);          // row r of C_l A_r^T
 #pragma unroll
-    for (int c = 0; c < 2 * LD; ++c)
-      b[c] = c < N ? t1[c] : (c >= LD && c < LD + N) ? t2[c - LD] : T(0);
+    for (int c = 0; c < 2 * YW; ++c)
+      b[c] = c < N ? t1[c] : (c >= YW && c < YW + N) ? t2[c - YW] : T(0);
   }
   __syncwarp();
   int kpos;
   const bool okf = glu<T, N, G>(s, gl, bc, order, kpos);
-  glu_solve<T, N, 2 * LD>(s, kpos, b, bc);      // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
-  if (gl < N) row_store<T, 2 * LD>(sY + kpos * LD2, b);
+  glu_solve<T, N, 2 * YW>(s, kpos, b, bc);      // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
+  if (gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
   // A_new = A_r Y1, C_new = C_r + A_r Y2  (rows r); C_r read before slot k is overwritten
   T an[N], cn[N];
@@ -391,9 +437,8 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
     row_load<T, N>(ar, sAr + r * LD);
     zero(an);
     row_mm<T, N, N, LD2>(an, ar, sY);
-#pragma unroll
-    for (int c = 0; c < N; ++c) cn[c] = w.Ec[ok_ + r * N + c];
-    row_mm<T, N, N, LD2>(cn, ar, sY + LD);
+    grow_load<T, N>(cn, w.Ec + ok_ + r * N);
+    row_mm<T, N, N, LD2>(cn, ar, sY + YW);
   }
   // W = P~ Y1 (rows r) -> over C_l ; P_new = P_l + A_l^T W
   {
@@ -406,27 +451,24 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   }
   __syncwarp();
   T pn[N];
-#pragma unroll
-  for (int c = 0; c < N; ++c) pn[c] = w.Ep[oj + r * N + c];    // P_l, read before slot j is overwritten
+  grow_load<T, N>(pn, w.Ep + oj + r * N);                      // P_l, read before slot j is overwritten
   col_mm<T, N, N, LD, LD>(pn, sAl, r, sCl);
   __syncwarp();
   if (g.valid && gl < N) {
     // tape into slot j: (A_r, C_r, P~); composed edge into slot k
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-      w.Ea[oj + r * N + c] = sAr[r * LD + c];
-      w.Ec[oj + r * N + c] = w.Ec[ok_ + r * N + c];
-      w.Ep[oj + r * N + c] = sPt[r * LD + c];
-    }
+    T v[N];
+    row_load<T, N>(v, sAr + r * LD);
+    grow_store<T, N>(w.Ea + oj + r * N, v);
+    grow_load<T, N>(v, w.Ec + ok_ + r * N);
+    grow_store<T, N>(w.Ec + oj + r * N, v);
+    row_load<T, N>(v, sPt + r * LD);
+    grow_store<T, N>(w.Ep + oj + r * N, v);
   }
   __syncwarp();
   if (g.valid && gl < N) {
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-      w.Ea[ok_ + r * N + c] = an[c];
-      w.Ec[ok_ + r * N + c] = cn[c];
-      w.Ep[ok_ + r * N + c] = pn[c];
-    }
+    grow_store<T, N>(w.Ea + ok_ + r * N, an);
+    grow_store<T, N>(w.Ec + ok_ + r * N, cn);
+    grow_store<T, N>(w.Ep + ok_ + r * N, pn);
   }
   __syncwarp();
   return okf;
@@ -457,17 +499,13 @@ __device__ __forceinline__ void compose_op(const Ws<T>& w, int rr, const Grp& g,
   const int gl = g.gl, r = gl < N ? gl : 0;
   gload<T, N, N, LD, G>(sTj, w.Tm + (size_t)j * NN, gl);
   T tk[N], o[N];
-#pragma unroll
-  for (int c = 0; c < N; ++c) tk[c] = w.Tm[(size_t)k * NN + r * N + c];
+  grow_load<T, N>(tk, w.Tm + (size_t)k * NN + r * N);
   __syncwarp();
   zero(o);
   row_mm<T, N, N, LD>(o, tk, sTj);
   if (g.valid && gl < N) {
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-      w.Tr[(size_t)j * NN + r * N + c] = tk[c];
-      w.Tm[(size_t)k * NN + r * N + c] = o[c];
-    }
+    grow_store<T, N>(w.Tr + (size_t)j * NN + r * N, tk);
+    grow_store<T, N>(w.Tm + (size_t)k * NN + r * N, o);
   }
   __syncwarp();
 }

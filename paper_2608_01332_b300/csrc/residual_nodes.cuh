@@ -188,23 +188,48 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
         row[3] = ks ? abits(f2d_bits(rs)) : 0ull;
       }
     }
-    // control row gl of the edge into j (lanes gl < M)
-    if (gl < M) {
-      const size_t tu = (size_t)j * M + gl;
+    // control rows of the edge into j: P = G / M lanes per row, each summing
+    // every P-th term, then a float-float reduction over those P lanes
+    {
+      constexpr int P = G / M;
+      static_assert(P * M == G, "M must divide the group size");
+      const int ua = gl / P, part = gl - ua * P;
+      FF s{0.f, 0.f};
+      float rs = 0.f;
       if (has_p) {
-        FF s{0.f, 0.f};
-        ff_add(s, a.r[tu]);
-        float rs = 0.f;
-        if (hm) rs += ff_dot<N, LDB>(s, sM + gl, vxh, vxl);
-        rs += ff_dot<M, 1>(s, sR + gl * LDB, vuh, vul);
-        rs += ff_dot<N, LDB>(s, sB + gl, vyh, vyl);
-        const double out = ff_value(s);
-        if (valid) a.res_u[tu] = out;
-        const unsigned long long ob = abits(out), kb = ks ? abits(f2d_bits(rs)) : 0ull;
-        row[0] = ob > row[0] ? ob : row[0];
-        row[3] = kb > row[3] ? kb : row[3];
-      } else if (valid) {
-        a.res_u[tu] = 0.0;
+#pragma unroll
+        for (int k = 0; k < (N + P - 1) / P; ++k) {
+          const int b = part + k * P;
+          if (b < N) {
+            if (hm) rs += ff_fma_d(s, sM[b * LDB + ua], vxh[b], vxl[b]);
+            rs += ff_fma_d(s, sB[b * LDB + ua], vyh[b], vyl[b]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < (M + P - 1) / P; ++k) {
+          const int c = part + k * P;
+          if (c < M) rs += ff_fma_d(s, sR[ua * LDB + c], vuh[c], vul[c]);
+        }
+        if (part == 0) ff_add(s, a.r[(size_t)j * M + ua]);
+      }
+#pragma unroll
+      for (int off = P / 2; off; off >>= 1) {
+        const float oh = __shfl_xor_sync(TLQR_FULL_MASK, s.h, off, P);
+        const float ol = __shfl_xor_sync(TLQR_FULL_MASK, s.l, off, P);
+        rs += __shfl_xor_sync(TLQR_FULL_MASK, rs, off, P);
+        ff_add2(s, oh, ol);
+      }
+      if (part == 0) {
+        const size_t tu = (size_t)j * M + ua;
+        if (has_p) {
+          const double out = ff_value(s);
+          if (valid) a.res_u[tu] = out;
+          const unsigned long long ob = abits(out), kb = ks ? abits(f2d_bits(rs)) : 0ull;
+          row[0] = ob > row[0] ? ob : row[0];
+          row[3] = kb > row[3] ? kb : row[3];
+        } else if (valid) {
+          a.res_u[tu] = 0.0;
+        }
       }
     }
     // message w_j = A_j^T y_j + M_j u_j to the parent's stationarity rows
