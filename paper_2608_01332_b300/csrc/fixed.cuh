@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "mma32.cuh"
 
 namespace tlqr {
 namespace fx {
@@ -39,6 +40,12 @@ struct D {
   static constexpr int OPS = 32 / G;                   // operations per warp
   static constexpr int MAT = N * LD;                   // elements of one staged matrix
 };
+
+// n = 32 in FP32: one warp per operation, and the n x n block products run on
+// the tensor cores (3xTF32 mma.sync, mma32.cuh); the LU and triangular
+// solves stay on the FP32 pipe.
+template <typename T, int N>
+constexpr bool kTensorCores = std::is_same<T, float>::value && N == 32;
 
 template <typename T> __device__ __forceinline__ T vget(const typename Vec<T>::V& v, int i);
 template <> __device__ __forceinline__ float vget<float>(const float4& v, int i) {
@@ -313,7 +320,12 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   __syncwarp();
   const int r = g.gl < N ? g.gl : 0;
   T x[N], b[N];
-  {
+  if constexpr (kTensorCores<T, N>) {
+    tc::gemm32<false, false>(sY, LD, sU, LD, nullptr, 0, sY, LD, true);   // C U over C
+    row_load<T, N>(x, sY + r * LD);
+#pragma unroll
+    for (int c = 0; c < N; ++c) x[c] += (c == r) ? T(1) : T(0);
+  } else {
     T crow[N];
     row_load<T, N>(crow, sY + r * LD);
     zero(x);
@@ -328,6 +340,11 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   glu_solve<T, N, N>(x, kpos, b, bc);           // Y = (I + C U)^{-1} A, row kpos in b
   if (g.gl < N) row_store<T, N>(sY + kpos * LD, b);
   __syncwarp();
+  if constexpr (kTensorCores<T, N> && std::is_same<S, T>::value) {
+    tc::gemm32<false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, true);   // Z = U Y over U
+    tc::gemm32<true, false>(sA, LD, sU, LD, Pg, N, out, N, g.valid);     // P + A^T Z
+    return ok;
+  }
   T z[N];
   {
     T urow[N];
@@ -410,7 +427,20 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   gload<T, N, N, LD, G>(sAr, w.Ea + ok_, gl);
   __syncwarp();
   T s[N], b[2 * YW];
-  {
+  if constexpr (kTensorCores<T, N>) {
+    // C_l P~ into the Y1 columns and C_l A_r^T into the Y2 columns of sY
+    tc::gemm32<false, false>(sCl, LD, sPt, LD, nullptr, 0, sY, LD2, true);
+    tc::gemm32<false, true>(sCl, LD, sAr, LD, nullptr, 0, sY + YW, LD2, true);
+    T t1[N], t2[N];
+    row_load<T, N>(s, sY + r * LD2);
+#pragma unroll
+    for (int c = 0; c < N; ++c) s[c] += (c == r) ? T(1) : T(0);   // S = I + C_l P~
+    row_load<T, N>(t1, sAl + r * LD);
+    row_load<T, N>(t2, sY + r * LD2 + YW);
+#pragma unroll
+    for (int c = 0; c < 2 * YW; ++c)
+      b[c] = c < N ? t1[c] : (c >= YW && c < YW + N) ? t2[c - YW] : T(0);
+  } else {
     T cl[N], t1[N], t2[N];
     row_load<T, N>(cl, sCl + r * LD);
     zero(s);
@@ -430,6 +460,26 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   glu_solve<T, N, 2 * YW>(s, kpos, b, bc);      // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
   if (gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
+  if constexpr (kTensorCores<T, N>) {
+    // W = P~ Y1 over C_l; P_new = P_l + A_l^T W into slot k (P_r is folded into P~
+    // already); A_new = A_r Y1 into slot k (A_r stays in shared memory for the tape)
+    tc::gemm32<false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, true);
+    tc::gemm32<true, false>(sAl, LD, sCl, LD, w.Ep + oj, N, w.Ep + ok_, N, g.valid);
+    tc::gemm32<false, false>(sAr, LD, sY, LD2, nullptr, 0, w.Ea + ok_, N, g.valid);
+    if (g.valid && gl < N) {
+      // tape into slot j: (A_r, C_r, P~); C_r copied before slot k's C is updated
+      T v[N];
+      row_load<T, N>(v, sAr + r * LD);
+      grow_store<T, N>(w.Ea + oj + r * N, v);
+      grow_load<T, N>(v, w.Ec + ok_ + r * N);
+      grow_store<T, N>(w.Ec + oj + r * N, v);
+      row_load<T, N>(v, sPt + r * LD);
+      grow_store<T, N>(w.Ep + oj + r * N, v);
+    }
+    __syncwarp();
+    tc::gemm32<false, false>(sAr, LD, sY + YW, LD2, w.Ec + ok_, N, w.Ec + ok_, N, g.valid);  // C_r + A_r Y2
+    return okf;
+  }
   // A_new = A_r Y1, C_new = C_r + A_r Y2  (rows r); C_r read before slot k is overwritten
   T an[N], cn[N];
   {
@@ -500,6 +550,13 @@ __device__ __forceinline__ void compose_op(const Ws<T>& w, int rr, const Grp& g,
   gload<T, N, N, LD, G>(sTj, w.Tm + (size_t)j * NN, gl);
   T tk[N], o[N];
   grow_load<T, N>(tk, w.Tm + (size_t)k * NN + r * N);
+  if constexpr (kTensorCores<T, N>) {
+    __syncwarp();
+    if (g.valid && gl < N) grow_store<T, N>(w.Tr + (size_t)j * NN + r * N, tk);
+    __syncwarp();
+    tc::gemm32<false, false>(w.Tm + (size_t)k * NN, N, sTj, LD, nullptr, 0, w.Tm + (size_t)k * NN, N, g.valid);
+    return;
+  }
   __syncwarp();
   zero(o);
   row_mm<T, N, N, LD>(o, tk, sTj);
