@@ -707,7 +707,10 @@ cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::
   constexpr int OPS = rn::RG<N>::OPS, threads = 128, gpb = (threads / 32) * OPS;
   const size_t se = (size_t)rn::EdgeBuf<N, M>::group_bytes(a.Delta != nullptr, a.M != nullptr) * gpb;
   const size_t sn = (size_t)rn::NodeBuf<N>::group_bytes * gpb;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, 148 * 16));
+  // one wave of resident blocks (each warp then walks a long contiguous node
+  // range and its double-buffered copies stay ahead of the arithmetic)
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (227 * 1024) / std::max(se, sn)));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, 148LL * per_sm));
   const bool forest = a.tree != nullptr;
   auto ek = forest ? rn::k_res_edge<N, M, true> : rn::k_res_edge<N, M, false>;
   auto nk = forest ? rn::k_res_node<N, true> : rn::k_res_node<N, false>;
