@@ -268,7 +268,11 @@ int tlqr_tree_residuals(const tlqr_factor_t *f, double *abs_res, double *eta, in
 int tlqr_last_info(const tlqr_factor_t *f, tlqr_info *out);
 
 /* ------------------------------------------------------------- profiling */
-/* Kernel kinds launched by the library (one per step of Alg. 1 above). */
+/* Kernel kinds launched by the library (one per step of Alg. 1 above).
+ * TLQR_K_AFF_TAIL / TLQR_K_STATE_TAIL: the single-block kernels that run the
+ * late rounds of the affine and state passes; TLQR_K_FACTOR_TAIL is reserved
+ * (no factorisation tail kernel is launched: in the late rounds one
+ * operation's latency, not the launch, sets the time). */
 enum {
   TLQR_K_CONDENSE = 0, TLQR_K_RAKE, TLQR_K_ABSORB, TLQR_K_COMPRESS, TLQR_K_EXPAND,
   TLQR_K_LOCAL_FACTOR, TLQR_K_COMPOSE_T, TLQR_K_AFF_INIT, TLQR_K_AFF_RAKE, TLQR_K_AFF_ABSORB,

@@ -755,92 +755,6 @@ __global__ void kf_state_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
   }
 }
 
-// ---------------------------------------------------------------- factor tail
-// The late structural rounds of the factorisation hold a handful of
-// operations each; one block runs them all: forward rounds r0..R-1 (rakes,
-// in-order sibling sums absorbed into the parents, compressions), then the
-// reverse expansions R-1..r0.  Same device functions, same per-operation
-// arithmetic as the per-round launches; __syncthreads() orders the phases.
-template <typename T, int N>
-struct FactorTail {
-  static constexpr int G = D<T, N>::G;
-  static constexpr int gbytes = CompSmem<T, N>::bytes > TauSmem<T, N>::bytes ? CompSmem<T, N>::bytes
-                                                                              : TauSmem<T, N>::bytes;
-  // groups per block: shared memory within 200 KB, at most 32 groups, whole warps
-  static constexpr int gmax = (200 * 1024) / gbytes;
-  static constexpr int gpb_raw = gmax < 32 ? gmax : 32;
-  static constexpr int per_warp = 32 / G;
-  static constexpr int gpb = (gpb_raw / per_warp) * per_warp;
-  static constexpr int threads = gpb * G;
-  static constexpr int smem = gpb * gbytes;
-};
-
-// U_i += sum of the segment's contributions, in sibling order (as k_absorb)
-template <typename T, int N>
-__device__ __forceinline__ void absorb_op(const Ws<T>& w, int sidx, bool valid, int gl) {
-  constexpr int G = D<T, N>::G, NN = N * N;
-  const int i = w.seg_parent[sidx], b = w.seg_start[sidx], e = w.seg_start[sidx + 1];
-  for (int x = gl; x < NN; x += G) {
-    T acc = w.contrib[(size_t)b * NN + x];
-    for (int r = b + 1; r < e; ++r) acc += w.contrib[(size_t)r * NN + x];
-    if (valid) w.U[(size_t)i * NN + x] += acc;
-  }
-}
-
-template <typename T, int N>
-__global__ void __launch_bounds__(FactorTail<T, N>::threads, 1)
-    kf_factor_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  using FT = FactorTail<T, N>;
-  constexpr int G = FT::G, NN = N * N;
-  const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
-  T* sm = reinterpret_cast<T*>(smem_raw + gid * FT::gbytes);
-  bool ok = true;
-  for (int r = r0; r < R; ++r) {
-    const RoundDesc d = rounds[r];
-    TLQR_BLOCK_OPS(d.re - d.rb, {
-      const int rr = d.rb + op, j = w.rake_leaf[rr];
-      const size_t o = (size_t)j * NN;
-      const Grp g{gl, gid, valid};
-      ok &= tau_group<T, N>(g, w.U + o, w.Ea + o, w.Ec + o, w.Ep + o, w.contrib + (size_t)rr * NN, sm) || !valid;
-    });
-    __syncthreads();
-    TLQR_BLOCK_OPS(d.se - d.sb, absorb_op<T, N>(w, d.sb + op, valid, gl));
-    __syncthreads();
-    TLQR_BLOCK_OPS(d.ce - d.cb, {
-      const Grp g{gl, gid, valid};
-      ok &= compress_op<T, N>(w, d.cb + op, g, sm) || !valid;
-    });
-    __syncthreads();
-  }
-  for (int r = R - 1; r >= r0; --r) {
-    const RoundDesc d = rounds[r];
-    TLQR_BLOCK_OPS(d.ce - d.cb, {
-      const int rr = d.cb + op, j = w.comp_j[rr], k = w.comp_k[rr];
-      const size_t oj = (size_t)j * NN;
-      const Grp g{gl, gid, valid};
-      ok &= tau_group<T, N>(g, w.U + (size_t)k * NN, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm) || !valid;
-    });
-    __syncthreads();
-  }
-  if (!ok && gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
-}
-
-// Composite transitions of the tail rounds (after the local factors).
-template <typename T, int N>
-__global__ void __launch_bounds__(FactorTail<T, N>::threads, 1)
-    kf_compose_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int G = D<T, N>::G;
-  const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
-  T* sTj = reinterpret_cast<T*>(smem_raw + gid * ComposeSmem<T, N>::bytes);
-  for (int r = r0; r < R; ++r) {
-    const RoundDesc d = rounds[r];
-    TLQR_BLOCK_OPS(d.ce - d.cb, compose_op<T, N>(w, d.cb + op, Grp{gl, gid, valid}, sTj));
-    __syncthreads();
-  }
-}
-
 }  // namespace fx
 }  // namespace tlqr
 

@@ -438,43 +438,6 @@ cudaError_t launch_tail(Recorder* rc, int kind, Kernel kernel, cudaStream_t st, 
   return e;
 }
 
-// One block of `threads` threads with `smem` bytes of dynamic shared memory.
-template <typename Kernel, typename... Args>
-cudaError_t launch_block(Recorder* rc, int kind, Kernel kernel, int threads, size_t smem, cudaStream_t st,
-                         Args... args) {
-  if (!(rc && rc->capture)) {
-    cudaError_t e = ensure_smem(kernel, smem);
-    if (e != cudaSuccess) return e;
-  }
-  const bool timed = rc && (rc->mask >> kind) & 1u;
-  EvPair ev{kind, nullptr, nullptr, 1};
-  if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  kernel<<<1, threads, smem, st>>>(args...);
-  cudaError_t e = cudaGetLastError();
-  if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
-  if (rc) { rc->launches[kind]++; rc->units[kind] += 1; }
-  return e;
-}
-
-// First round of the factorisation's tail: the longest suffix of rounds whose
-// phases each hold at most kFactorTailOps operations.  One block runs a phase's
-// operations side by side on one SM, so the tail only pays where a phase is a
-// handful of operations and launch gaps outweigh the shared SM; for n = 32 a
-// single operation's latency (~0.1 ms) dominates and no tail is used.
-constexpr int kFactorTailOps = 8;
-template <typename T, int N>
-int factor_tail_start(const tlqr_plan_t* P) {
-  if (N > 16) return (int)P->rounds.size();
-  const int lim = std::min(kFactorTailOps, fx::FactorTail<T, N>::gpb);
-  int r0 = (int)P->rounds.size();
-  while (r0 > 0) {
-    const tlqr_round& r = P->rounds[r0 - 1];
-    if (std::max({r.rake_end - r.rake_begin, r.seg_end - r.seg_begin, r.comp_end - r.comp_begin}) > lim) break;
-    --r0;
-  }
-  return r0;
-}
-
 cudaError_t launch_split(Recorder* rc, const SplitList& L, cudaStream_t st) {
   const int blocks = 148 * 4, threads = 256;
   k_split_ff<<<blocks, threads, 0, st>>>(L);
@@ -502,9 +465,7 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
     return e;
   }
   const int R = (int)P->rounds.size();
-  int ft0 = R;                                  // rounds ft0..R-1 run in the factor tail kernel
-  if constexpr (NF > 0) ft0 = factor_tail_start<T, NX>(P);
-  for (int ri = 0; ri < ft0; ++ri) {
+  for (int ri = 0; ri < R; ++ri) {
     const tlqr_round& rd = P->rounds[ri];
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
     if constexpr (NF > 0) {
@@ -522,13 +483,7 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
       return e;
     }
   }
-  if constexpr (NF > 0) {
-    using FT = fx::FactorTail<T, NX>;
-    if (ft0 < R && (e = launch_block(rc, TLQR_K_FACTOR_TAIL, fx::kf_factor_tail<T, NX>, FT::threads,
-                                     (size_t)FT::smem, st, w, f->d_rounds, ft0, R)))
-      return e;
-  }
-  for (int ri = ft0 - 1; ri >= 0; --ri) {
+  for (int ri = R - 1; ri >= 0; --ri) {
     const tlqr_round* it = &P->rounds[ri];
     const int nc = it->comp_end - it->comp_begin;
     if constexpr (NF > 0) {
@@ -545,7 +500,7 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
                                (int)wb.local_factor))) {
     return e;
   }
-  for (int ri = 0; ri < ft0; ++ri) {
+  for (int ri = 0; ri < R; ++ri) {
     const tlqr_round& rd = P->rounds[ri];
     const int nc = rd.comp_end - rd.comp_begin;
     if constexpr (NF > 0) {
@@ -555,12 +510,6 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
                                  (int)wb.compose_T))) {
       return e;
     }
-  }
-  if constexpr (NF > 0) {
-    using FT = fx::FactorTail<T, NX>;
-    if (ft0 < R && (e = launch_block(rc, TLQR_K_FACTOR_TAIL, fx::kf_compose_tail<T, NX>, FT::threads,
-                                     (size_t)FT::gpb * fx::ComposeSmem<T, NX>::bytes, st, w, f->d_rounds, ft0, R)))
-      return e;
   }
   return cudaSuccess;
 }
@@ -1023,8 +972,6 @@ cudaError_t configure_fixed() {
   cudaError_t e = ensure_smem(fx::kf_rake<T, N>, (size_t)fx::TauSmem<T, N>::bytes * gpb);
   if (!e) e = ensure_smem(fx::kf_expand<T, N>, (size_t)fx::TauSmem<T, N>::bytes * gpb);
   if (!e) e = ensure_smem(fx::kf_compress<T, N>, (size_t)fx::CompSmem<T, N>::bytes * gpb);
-  if (!e) e = ensure_smem(fx::kf_factor_tail<T, N>, (size_t)fx::FactorTail<T, N>::smem);
-  if (!e) e = ensure_smem(fx::kf_compose_tail<T, N>, (size_t)fx::FactorTail<T, N>::gpb * fx::ComposeSmem<T, N>::bytes);
   if (!e) e = ensure_smem(fx::kf_compose_T<T, N>, (size_t)fx::ComposeSmem<T, N>::bytes * gpb);
   return e;
 }
