@@ -656,10 +656,7 @@ cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::
   constexpr int OPS = rn::RG<N>::OPS, threads = 128, gpb = (threads / 32) * OPS;
   const size_t se = (size_t)rn::EdgeBuf<N, M>::group_bytes(a.Delta != nullptr, a.M != nullptr) * gpb;
   const size_t sn = (size_t)rn::NodeBuf<N>::group_bytes * gpb;
-  // one wave of resident blocks (each warp then walks a long contiguous node
-  // range and its double-buffered copies stay ahead of the arithmetic)
-  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (227 * 1024) / std::max(se, sn)));
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, 148LL * per_sm));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, 148 * 16));
   const bool forest = a.tree != nullptr;
   auto ek = forest ? rn::k_res_edge<N, M, true> : rn::k_res_edge<N, M, false>;
   auto nk = forest ? rn::k_res_node<N, true> : rn::k_res_node<N, false>;
@@ -699,6 +696,12 @@ cudaError_t dispatch_res_nodes(int n, int m, const ResidualArgs& a, const FFArgs
   return cudaErrorNotSupported;
 }
 
+// Which float-float residual runs: the node-organised kernels were measured
+// faster than the row-per-thread kernels at n = 16 (-25 % on a batch of 1,024
+// trees) and slower at n = 12 and n = 32 (B300, 2^16 to 3e6 nodes), so they
+// are used at n = 16 only.
+bool use_node_residual(const tlqr_factor_t* f) { return f->fixed_m > 0 && f->fixed_n == 16; }
+
 // ff = 1: float-float kernel on the FP32 pipe (refinement); ff = 0: plain FP64 kernel.
 cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, const double* x,
                          const double* u, const double* y, int with_knorm, cudaStream_t st, int ff = 0) {
@@ -721,7 +724,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
     // split x, u, y once per call; for one tree ||z|| and ||b|| maxima come
     // from the same pass (a forest forms them per tree in the residual kernel)
     const size_t N = P->N, n = f->opt.n, m = f->opt.m;
-    const bool by_node = f->fixed_m > 0;            // node kernels form all four maxima themselves
+    const bool by_node = use_node_residual(f);      // node kernels form all four maxima themselves
     const int zs = (a.tree || by_node) ? -1 : 1, bs = (a.tree || by_node) ? -1 : 2;
     SplitList L{};
     auto add = [&](const double* src, float* hi, float* lo, size_t len, int slot) {
@@ -746,7 +749,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
   EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr, P->N};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  if (ff && f->fixed_m > 0) {
+  if (ff && use_node_residual(f)) {
     const rn::NodeArgs na{f->rwh, f->rwl, f->rwk};
     if ((e = dispatch_res_nodes(f->fixed_n, f->fixed_m, a, fa, na, st, rc && rc->capture))) return e;
   } else if (a.tree) {
