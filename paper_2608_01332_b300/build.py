@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtlqr.so")
 SOURCES = ["tlqr.cu", "planner.cpp", "lifting.cpp", "noalloc.cu"]
-HEADERS = ["kernels.cuh", "fixed.cuh", "smallmat.cuh", "residual.cuh", "residual_nodes.cuh", "plan.hpp"]
+HEADERS = ["kernels.cuh", "fixed.cuh", "smallmat.cuh", "residual.cuh", "residual_nodes.cuh", "mma32.cuh", "plan.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

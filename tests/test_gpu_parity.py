@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (derived from the arithmetic; the benchmark spec's targets are stated as
+Tolerances (derived from the arithmetic; the accuracy targets are stated as
 backward errors):
   * FP64 path: eta <= 1e-10 (normwise backward error of eq. (kkt)); elementwise
     |z - z_oracle| <= 1e-8 max|z_oracle| for z = (x, u, y), and P, K within
