@@ -38,6 +38,18 @@ def test_reference_arm_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["config"]["N"] == 2048
 
 
+@pytest.mark.parametrize("workload,extra", [("batch", ["--count", "6"]), ("serve", [])])
+def test_reference_arm_other_workloads(workload, extra):
+    """The reference arm on a batch (whole trees of the forest) and on the
+    serving topologies: one line, the oracle's sample named in it."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    line = _run(["bench.py", "--impl", "reference", "--workload", workload, *extra, "--steps", "1", "--warmup",
+                 "1", "--ref-seconds", "1"], env=env)
+    d = [json.loads(s) for s in line.splitlines() if s.startswith("{")][-1]
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["sample_nodes"] > 0
+    assert "tree(s)" in d["cpu_baseline"]["sample"]
+
+
 def test_reference_arm_two_rank_gloo():
     """torchrun with two CPU ranks: rank 0 alone prints; the job exits 0."""
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
