@@ -13,7 +13,9 @@
 // FMAs per shared-memory load.  LU with partial pivoting keeps the rows where
 // they are (implicit pivoting): the pivot is found with group shuffles and its
 // row is broadcast through shared memory.  Loops over n are fully unrolled, so
-// all register indexing is static.
+// all register indexing is static.  At n = 32 in FP32 (one warp per operation)
+// the block products run on the tensor cores instead (mma32.cuh); the LU and
+// the triangular solves stay as described.
 #pragma once
 #include <cstdint>
 #include <type_traits>
