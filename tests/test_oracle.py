@@ -305,3 +305,163 @@ def test_local_factor_consistent_with_recursion():
         np.testing.assert_allclose(lf["K"], sol["K"][j], rtol=1e-11, atol=1e-12)
         Pacc[p[j]] += d["M"][j] @ lf["K"] + d["A"][j].T @ lf["W"] @ lf["Acl"]
     np.testing.assert_allclose(Pacc, sol["P"], rtol=1e-11, atol=1e-11)
+
+
+# ------------------------------------------------------------------ brute-force subtree maps
+# The value function of a subtree with its root state held fixed is quadratic
+# in that state, and the subtree's optimal states are affine in it.  Both are
+# obtained here by dense solves of the subtree's KKT system with the root's
+# state moved to the right-hand side (no tree recursion involved); by the
+# envelope theorem the gradient of the value at x_i is sum over the children j
+# of (M_j u_j + A_j^T y_j).  These pin the oracle's affine maps (Sec. VI) and
+# state maps (Sec. VII) at one operation.
+
+def _subtree_nodes(parent, i):
+    parent = np.asarray(parent)
+    out, stack = [], [i]
+    while stack:
+        v = stack.pop()
+        out.append(v)
+        stack.extend(int(c) for c in np.nonzero(parent == v)[0][::-1])
+    return [out[0]] + sorted(out[1:])
+
+
+def _fixed_root(parent, n, m, d, i, xi):
+    """Saddle point of the subtree of i with x_i = xi held fixed (root data of
+    i excluded).  Returns (nodes, x, u, y, grad) in subtree order, grad = the
+    gradient of the subtree's value at xi."""
+    parent = np.asarray(parent)
+    nodes = _subtree_nodes(parent, i)
+    idx = {v: t for t, v in enumerate(nodes)}
+    sp = np.array([-1] + [idx[int(parent[v])] for v in nodes[1:]], dtype=np.int32)
+    sd = {k: (None if v is None else np.asarray(v)[nodes]) for k, v in d.items()}
+    K, b, (X, U, Y, nonroot) = dense.assemble_kkt(sp, n, m, sd)
+    dim = K.shape[0]
+    drop = set(range(X(0).start, X(0).stop)) | set(range(Y(0).start, Y(0).stop))
+    keep = [t for t in range(dim) if t not in drop]
+    cols = list(range(X(0).start, X(0).stop))
+    z = np.zeros(dim)
+    z[cols] = xi
+    z[keep] = np.linalg.solve(K[np.ix_(keep, keep)], -(b[keep] + K[np.ix_(keep, cols)] @ xi))
+    Ns = len(nodes)
+    x = np.stack([z[X(t)] for t in range(Ns)])
+    y = np.stack([z[Y(t)] for t in range(Ns)])
+    u = np.zeros((Ns, m))
+    for j in nonroot:
+        u[j] = z[U(j)]
+    grad = np.zeros(n)
+    for j in range(1, Ns):
+        if sp[j] == 0:
+            grad += (sd["M"][j] @ u[j] if sd.get("M") is not None else 0.0) + sd["A"][j].T @ y[j]
+    return nodes, x, u, y, grad
+
+
+def _affine_in_root(parent, n, m, d, i, what):
+    """(Jacobian, value at 0) of an affine function of x_i computed by _fixed_root."""
+    f0 = what(*_fixed_root(parent, n, m, d, i, np.zeros(n)))
+    J = np.stack([what(*_fixed_root(parent, n, m, d, i, np.eye(n)[a])) - f0 for a in range(n)], axis=1)
+    return J, f0
+
+
+def _chain_case(seed, N, n, m, delta):
+    rng = inputs.rng_for(seed)
+    p = inputs.chain(N)
+    d = inputs.problem_data(p, n, m, rng, M_scale=0.3, delta=delta, delta_value=0.4)
+    return p, d
+
+
+@pytest.mark.parametrize("delta", [None, "random"])
+def test_expand_compress_gives_the_subtree_value_hessian(delta):
+    """eq. (value-reconstruction): at a centre j compressed between the edges
+    (i, j) and (j, k), expanding its tape with P_k gives P_j, the Hessian of the
+    value of j's subtree (Thm. 1) -- here obtained by brute force."""
+    n, m = 3, 2
+    p, d = _chain_case(41, 4, n, m, delta)
+    D = d.get("Delta")
+    cond = lambda e: ops.condense(d["A"][e], d["B"][e], d["R"][e], d["M"][e], None if D is None else D[e])
+    i, j, k = 1, 2, 3
+    Pk = d["Q"][k]                                    # a leaf's value Hessian is its own Q
+    _, tape = ops.compose(cond(k), cond(j), d["Q"][j])
+    Pj = ops.expand_compress(tape, Pk)
+    J, _ = _affine_in_root(p, n, m, d, j, lambda nodes, x, u, y, g: g)
+    np.testing.assert_allclose(Pj, d["Q"][j] + J, rtol=1e-10, atol=1e-11)
+    # Delta = 0, M != 0: also the textbook one-step Riccati update of P_k across edge (j, k)
+    if D is None:
+        A, B, M, R = d["A"][k], d["B"][k], d["M"][k], d["R"][k]
+        H = A.T @ Pk @ B + M
+        textbook = d["Q"][j] + A.T @ Pk @ A - H @ np.linalg.solve(R + B.T @ Pk @ B, H.T)
+        np.testing.assert_allclose(Pj, textbook, rtol=1e-10, atol=1e-11)
+
+
+@pytest.mark.parametrize("delta", [None, "random"])
+def test_affine_edge_is_the_value_gradient_of_a_leaf_edge(delta):
+    """eq. (affine-edge): for a leaf j under i, the message T_e^T p_j + z_e with
+    p_j = q_j is the gradient of the leaf edge's value at x_i = 0, and T_e^T
+    is its sensitivity to q_j (brute force on the two-node subtree)."""
+    n, m = 3, 2
+    p, d = _chain_case(42, 3, n, m, delta)
+    D = d.get("Delta")
+    i, j = 1, 2
+    lf = ops.local_factor(d["Q"][j], d["A"][j], d["B"][j], d["R"][j], d["M"][j], None if D is None else D[j])
+    Z, z = ops.affine_edge(lf["T"], lf["K"], lf["W"], lf["Acl"], d["r"][j], d["c"][j])
+    grad0 = _fixed_root(p, n, m, d, i, np.zeros(n))[4]
+    np.testing.assert_allclose(Z @ d["q"][j] + z, grad0, rtol=1e-10, atol=1e-11)
+    sens = []
+    for a in range(n):
+        d2 = {k: (None if v is None else v.copy()) for k, v in d.items()}
+        d2["q"][j] += np.eye(n)[a]
+        sens.append(_fixed_root(p, n, m, d2, i, np.zeros(n))[4] - grad0)
+    np.testing.assert_allclose(np.stack(sens, axis=1), Z, rtol=1e-10, atol=1e-11)
+
+
+@pytest.mark.parametrize("delta", [None, "random"])
+def test_affine_compose_is_the_value_gradient_across_a_compressed_node(delta):
+    """eq. (affine-compose): composing the affine maps of the edges (i, j) and
+    (j, k) through the centre's linear data h_j = q_j gives the message from
+    k's subtree to i: Zhat p_k + zhat with p_k = q_k equals the gradient of the
+    value of i's subtree at x_i = 0, and Zhat = Z_l Z_r is its sensitivity to
+    q_k (brute force on a three-edge chain)."""
+    n, m = 3, 2
+    p, d = _chain_case(43, 4, n, m, delta)
+    D = d.get("Delta")
+    i, j, k = 1, 2, 3
+    J, _ = _affine_in_root(p, n, m, d, j, lambda nodes, x, u, y, g: g)
+    Pj = d["Q"][j] + J                                  # brute-force value Hessian at j
+
+    def edge(e, Pe):
+        lf = ops.local_factor(Pe, d["A"][e], d["B"][e], d["R"][e], d["M"][e], None if D is None else D[e])
+        return ops.affine_edge(lf["T"], lf["K"], lf["W"], lf["Acl"], d["r"][e], d["c"][e])
+
+    Zl, zl = edge(j, Pj)
+    Zr, zr = edge(k, d["Q"][k])
+    Zh, zh = ops.affine_compose(Zl, zl, Zr, zr, d["q"][j])
+    grad0 = _fixed_root(p, n, m, d, i, np.zeros(n))[4]
+    np.testing.assert_allclose(Zh @ d["q"][k] + zh, grad0, rtol=1e-10, atol=1e-11)
+    sens = []
+    for a in range(n):
+        d2 = {kk: (None if v is None else v.copy()) for kk, v in d.items()}
+        d2["q"][k] += np.eye(n)[a]
+        sens.append(_fixed_root(p, n, m, d2, i, np.zeros(n))[4] - grad0)
+    np.testing.assert_allclose(np.stack(sens, axis=1), Zh, rtol=1e-10, atol=1e-11)
+
+
+@pytest.mark.parametrize("delta", [None, "random"])
+def test_transition_compose_matches_the_brute_force_state_maps(delta):
+    """eq. (transition-compose): the optimal x_j is affine in x_i (x_j = T_l x_i
+    + b_l) and x_k in x_j (T_r, b_r); composing the two maps gives x_k as a
+    function of x_i.  All three maps come from dense solves of the subtrees with
+    their root state held fixed; T_l also equals the local factor's
+    T = F^{-1} A_cl of eq. (FW)."""
+    n, m = 3, 2
+    p, d = _chain_case(44, 4, n, m, delta)
+    D = d.get("Delta")
+    i, j, k = 1, 2, 3
+    Tl, bl = _affine_in_root(p, n, m, d, i, lambda nodes, x, u, y, g: x[nodes.index(j)])
+    Tr, br = _affine_in_root(p, n, m, d, j, lambda nodes, x, u, y, g: x[nodes.index(k)])
+    Tik, bik = _affine_in_root(p, n, m, d, i, lambda nodes, x, u, y, g: x[nodes.index(k)])
+    T, b = ops.transition_compose(Tr, br, Tl, bl)
+    np.testing.assert_allclose(T, Tik, rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(b, bik, rtol=1e-10, atol=1e-11)
+    J, _ = _affine_in_root(p, n, m, d, j, lambda nodes, x, u, y, g: g)
+    lf = ops.local_factor(d["Q"][j] + J, d["A"][j], d["B"][j], d["R"][j], d["M"][j], None if D is None else D[j])
+    np.testing.assert_allclose(lf["T"], Tl, rtol=1e-10, atol=1e-11)
