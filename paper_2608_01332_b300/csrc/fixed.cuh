@@ -10,12 +10,14 @@
 // right operand of a product sits in shared memory (row stride LD, rows 16-byte
 // aligned) and is read as whole 16-byte vectors that every lane of the group
 // reads at the same address (broadcast): a lane performs W = 16 / sizeof(T)
-// FMAs per shared-memory load.  LU with partial pivoting keeps the rows where
-// they are (implicit pivoting): the pivot is found with group shuffles and its
-// row is broadcast through shared memory.  Loops over n are fully unrolled, so
+// FMAs per shared-memory load.  The linear solves with S = I + C P~ and
+// F = I + Delta P are Gauss-Jordan eliminations with partial pivoting that keep
+// the rows where they are (implicit pivoting): the pivot is found with one
+// unsigned-max reduction over the group and its row is broadcast through
+// shared memory.  Loops over n are fully unrolled, so
 // all register indexing is static.  At n = 32 in FP32 (one warp per operation)
-// the block products run on the tensor cores instead (mma32.cuh); the LU and
-// the triangular solves stay as described.
+// the block products run on the tensor cores instead (mma32.cuh); the
+// eliminations stay on the FP32 pipe.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -44,7 +46,7 @@ struct D {
 };
 
 // n = 32 in FP32: one warp per operation, and the n x n block products run on
-// the tensor cores (3xTF32 mma.sync, mma32.cuh); the LU and triangular
+// the tensor cores (3xTF32 mma.sync, mma32.cuh); the Gauss-Jordan
 // solves stay on the FP32 pipe.
 template <typename T, int N>
 constexpr bool kTensorCores = std::is_same<T, float>::value && N == 32;
@@ -213,85 +215,127 @@ __device__ __forceinline__ void row_mmT(T (&c)[C], const T (&a)[K], const T* B) 
   }
 }
 
-template <typename T> __device__ __forceinline__ T pivot_key(T v) { return isnan(v) ? T(INFINITY) : tabs(v); }
+// Pivot search key of a group lane: the bits of |v| (monotone for IEEE
+// numbers of one sign; NaN maps to +Inf so a NaN column is picked and then
+// rejected) with the low log2(G) bits replaced by G - 1 - gl, so that one
+// unsigned max over the group returns the largest |v| and, among values
+// equal in the remaining bits, the lowest lane.  Dropping those low mantissa
+// bits lets the chosen pivot be up to 2^-18 (FP32) or 2^-15 (FP64, high word)
+// below the true maximum in relative terms, which partial pivoting tolerates.
+template <typename T> __device__ __forceinline__ unsigned pivot_bits(T v);
+template <> __device__ __forceinline__ unsigned pivot_bits<float>(float v) {
+  const unsigned u = __float_as_uint(v) & 0x7fffffffu;
+  return u > 0x7f800000u ? 0x7f800000u : u;
+}
+template <> __device__ __forceinline__ unsigned pivot_bits<double>(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v) & 0x7fffffffu, lo = (unsigned)__double2loint(v);
+  return (hi > 0x7ff00000u || (hi == 0x7ff00000u && lo != 0u)) ? 0x7ff00000u : hi;
+}
 
-// LU with partial (implicit) pivoting of the N x N matrix whose row gl is in
-// a[] (lanes gl < N).  On return lane gl's row was chosen as pivot k = kpos:
-// a[j < k] are the multipliers L[k][j], a[j >= k] the entries U[k][j];
-// order[k] = lane of pivot k.  bc: N shared elements of this group.
+// Unsigned max over the G lanes of each group of a warp.  Whole warp: one
+// redux.sync.  Half warps: one full-warp redux per half (the other half
+// contributes 0).  Smaller groups: a shuffle butterfly.  Called by all lanes.
+template <int G>
+__device__ __forceinline__ unsigned group_umax(unsigned key) {
+  if constexpr (G == 32) {
+    return __reduce_max_sync(TLQR_FULL_MASK, key);
+  } else if constexpr (G == 16) {
+    const bool upper = (threadIdx.x & 16) != 0;
+    const unsigned lo = __reduce_max_sync(TLQR_FULL_MASK, upper ? 0u : key);
+    const unsigned hi = __reduce_max_sync(TLQR_FULL_MASK, upper ? key : 0u);
+    return upper ? hi : lo;
+  } else {
+#pragma unroll
+    for (int off = G / 2; off; off >>= 1) key = max(key, __shfl_xor_sync(TLQR_FULL_MASK, key, off, G));
+    return key;
+  }
+}
+
+// Shared broadcast buffer of ggj: two rows (double buffering) of the pivot
+// row of S (N entries, padded to whole vectors), of B (R entries, padded) and
+// one vector holding 1 / pivot.
+template <typename T, int N, int R>
+struct GjBuf {
+  static constexpr int W = Vec<T>::W;
+  static constexpr int NP = (N + W - 1) / W * W, RP = (R + W - 1) / W * W;
+  static constexpr int ROW = NP + RP + W;
+  static constexpr int elems = 2 * ROW;
+};
+
+// Solve S X = B by Gauss-Jordan elimination with partial pivoting, for one
+// group.  Lane gl < N holds row gl of S in a[] and row gl of B in b[]; rows
+// stay in their lanes (implicit pivoting).  At step k the undone lane with the
+// largest |a[k]| (group_umax of pivot keys) writes its row, unscaled, and
+// 1 / a[k] to the shared buffer; every other lane, pivots of earlier steps
+// included, subtracts l = a[k] / pivot times that row from columns > k of S
+// and from all of B.  After N steps the lane that was pivot k holds row k of
+// X once it divides its B row by its own pivot: on return lane gl holds row
+// kpos of X in b[].  N serial steps, against 3N for an LU followed by forward
+// and backward substitution; every lane issues the same N^2/2 + N R FMAs as
+// there (a lane owns a whole row, so the triangular sweeps saved no per-lane
+// work).  Double-buffered broadcast rows need one __syncwarp per step.
+// bc: GjBuf<T, N, R>::elems shared elements of this group, 16-byte aligned.
 // Returns false (uniformly in the group) on a zero or nonfinite pivot.
-template <typename T, int N, int G>
-__device__ __forceinline__ bool glu(T (&a)[N], int gl, T* bc, int* order, int& kpos) {
+template <typename T, int N, int G, int R>
+__device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kpos) {
+  using Bf = GjBuf<T, N, R>;
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
   bool done = gl >= N;
   kpos = N;
   bool ok = true;
+  T myinv = T(1);
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    T v = done ? T(-1) : pivot_key(a[k]);
-    int idx = gl;
-#pragma unroll
-    for (int off = G / 2; off; off >>= 1) {
-      const T ov = __shfl_xor_sync(TLQR_FULL_MASK, v, off, G);
-      const int oi = __shfl_xor_sync(TLQR_FULL_MASK, idx, off, G);
-      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-    }
-    ok = ok && (v > T(0)) && tfinite(v);
-    if (gl == idx) {
+    T* row = bc + (k & 1) * Bf::ROW;
+    const unsigned key = done ? 0u : ((pivot_bits<T>(a[k]) & ~unsigned(G - 1)) | unsigned(G - 1 - gl));
+    const unsigned mx = group_umax<G>(key);
+    const int p = G - 1 - (int)(mx & unsigned(G - 1));
+    if (gl == p) {
       kpos = k;
       done = true;
-      order[k] = gl;
+      myinv = T(1) / a[k];
 #pragma unroll
-      for (int j = k; j < N; ++j) bc[j] = a[j];
+      for (int q = k / W; q < Bf::NP / W; ++q) {
+        V v;
+#pragma unroll
+        for (int i = 0; i < W; ++i) vset(v, i, q * W + i < N ? a[q * W + i] : T(0));
+        reinterpret_cast<V*>(row)[q] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < Bf::RP / W; ++q) {
+        V v;
+#pragma unroll
+        for (int i = 0; i < W; ++i) vset(v, i, q * W + i < R ? b[q * W + i] : T(0));
+        reinterpret_cast<V*>(row + Bf::NP)[q] = v;
+      }
+      row[Bf::NP + Bf::RP] = myinv;
     }
     __syncwarp();
-    if (!done) {
-      const T l = a[k] / bc[k];
-      a[k] = l;
+    const T inv = row[Bf::NP + Bf::RP];
+    ok = ok && tfinite(inv) && inv != T(0);
+    if (gl != p && gl < N) {
+      const T l = a[k] * inv;
 #pragma unroll
-      for (int j = k + 1; j < N; ++j) a[j] = fma(-l, bc[j], a[j]);
+      for (int q = (k + 1) / W; q < Bf::NP / W; ++q) {
+        const V v = reinterpret_cast<const V*>(row)[q];
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+          if (q * W + i > k && q * W + i < N) a[q * W + i] = fma(-l, vget<T>(v, i), a[q * W + i]);
+      }
+#pragma unroll
+      for (int q = 0; q < Bf::RP / W; ++q) {
+        const V v = reinterpret_cast<const V*>(row + Bf::NP)[q];
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+          if (q * W + i < R) b[q * W + i] = fma(-l, vget<T>(v, i), b[q * W + i]);
+      }
     }
-    __syncwarp();
   }
+#pragma unroll
+  for (int c = 0; c < R; ++c) b[c] *= myinv;
+  __syncwarp();
   return ok;
-}
-
-// Solve (LU) X = B for R right-hand sides held by rows: lane gl holds row gl of
-// B in b[] on entry and row kpos of X on return.  bc: LDR shared elements.
-template <typename T, int N, int R>
-__device__ __forceinline__ void glu_solve(const T (&a)[N], int kpos, T (&b)[R], T* bc) {
-  constexpr int LDR = (R + Vec<T>::W - 1) / Vec<T>::W * Vec<T>::W;
-  (void)LDR;
-  // forward: L y = P b
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    if (kpos == k) row_store<T, R>(bc, b);
-    __syncwarp();
-    if (kpos > k && kpos < N) {
-      T y[R];
-      row_load<T, R>(y, bc);
-#pragma unroll
-      for (int c = 0; c < R; ++c) b[c] = fma(-a[k], y[c], b[c]);
-    }
-    __syncwarp();
-  }
-  // backward: U x = y
-#pragma unroll
-  for (int k = N - 1; k >= 0; --k) {
-    if (kpos == k) {
-      const T inv = T(1) / a[k];
-#pragma unroll
-      for (int c = 0; c < R; ++c) b[c] *= inv;
-      row_store<T, R>(bc, b);
-    }
-    __syncwarp();
-    if (kpos < k) {
-      T x[R];
-      row_load<T, R>(x, bc);
-#pragma unroll
-      for (int c = 0; c < R; ++c) b[c] = fma(-a[k], x[c], b[c]);
-    }
-    __syncwarp();
-  }
 }
 
 template <typename T, int N>
@@ -302,11 +346,11 @@ __device__ __forceinline__ void zero(T (&a)[N]) {
 
 // ---------------------------------------------------------------- tau
 // out = P + A^T U (I + C U)^{-1} A  (eq. terminal-fold) for one group.
-// sm (group): U, A, Y matrices + bc (LD) + order (N ints).
+// sm (group): U, A, Y matrices + the Gauss-Jordan broadcast rows.
 template <typename T, int N>
 struct TauSmem {
-  static constexpr int elems = 3 * D<T, N>::MAT + D<T, N>::LD;
-  static constexpr int bytes = elems * (int)sizeof(T) + ((N * 4 + 15) / 16) * 16;
+  static constexpr int elems = 3 * D<T, N>::MAT + GjBuf<T, N, N>::elems;
+  static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
 template <typename T, int N, typename S>
@@ -315,7 +359,6 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   using Dm = D<T, N>;
   constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT;
   T *sU = sm, *sA = sm + MAT, *sY = sm + 2 * MAT, *bc = sm + 3 * MAT;
-  int* order = reinterpret_cast<int*>(sm + 3 * MAT + LD);
   gload<T, N, N, LD, G>(sU, Ug, g.gl);
   gload<T, N, N, LD, G>(sA, Ag, g.gl);
   gload<T, N, N, LD, G>(sY, Cg, g.gl);      // C staged in sY
@@ -338,8 +381,7 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   row_load<T, N>(b, sA + r * LD);               // row r of A (right-hand side)
   __syncwarp();
   int kpos;
-  const bool ok = glu<T, N, G>(x, g.gl, bc, order, kpos);
-  glu_solve<T, N, N>(x, kpos, b, bc);           // Y = (I + C U)^{-1} A, row kpos in b
+  const bool ok = ggj<T, N, G, N>(x, b, g.gl, bc, kpos);   // Y = (I + C U)^{-1} A, row kpos in b
   if (g.gl < N) row_store<T, N>(sY + kpos * LD, b);
   __syncwarp();
   if constexpr (kTensorCores<T, N> && std::is_same<S, T>::value) {
@@ -396,15 +438,15 @@ __global__ void kf_expand(Ws<T> w, int begin, int count) {
 // ---------------------------------------------------------------- compress
 // eq. (compress-intermediates)-(composition) with the tape of
 // eq. (quadratic-compress).  sm (group): Pt, Al, Cl, Ar, Y (2 matrices of
-// 2N columns), bc (2 LD), order.
+// 2N columns), the Gauss-Jordan broadcast rows.
 template <typename T, int N>
 struct CompSmem {
   // [Y1 | Y2]: Y2 at column YW (N rounded up to whole vectors); row stride an
   // odd number of vectors (conflict-free row stores)
   static constexpr int YW = D<T, N>::NV * D<T, N>::W;
   static constexpr int LD2 = (2 * D<T, N>::NV + 1) * D<T, N>::W;
-  static constexpr int elems = 4 * D<T, N>::MAT + N * LD2 + LD2;
-  static constexpr int bytes = elems * (int)sizeof(T) + ((N * 4 + 15) / 16) * 16;
+  static constexpr int elems = 4 * D<T, N>::MAT + N * LD2 + GjBuf<T, N, 2 * YW>::elems;
+  static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
 template <typename T, int N>
@@ -414,7 +456,6 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   constexpr int NN = N * N;
   T *sPt = sm, *sAl = sm + MAT, *sCl = sm + 2 * MAT, *sAr = sm + 3 * MAT, *sY = sm + 4 * MAT,
     *bc = sm + 4 * MAT + N * LD2;
-  int* order = reinterpret_cast<int*>(bc + LD2);
   const int j = w.comp_j[rr], k = w.comp_k[rr];
   const size_t oj = (size_t)j * NN, ok_ = (size_t)k * NN;
   const int gl = g.gl, r = gl < N ? gl : 0;
@@ -458,8 +499,7 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   }
   __syncwarp();
   int kpos;
-  const bool okf = glu<T, N, G>(s, gl, bc, order, kpos);
-  glu_solve<T, N, 2 * YW>(s, kpos, b, bc);      // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
+  const bool okf = ggj<T, N, G, 2 * YW>(s, b, gl, bc, kpos);   // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
   if (gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
   if constexpr (kTensorCores<T, N>) {
@@ -983,10 +1023,9 @@ __global__ void kf_condense(Ws<T> w, int count) {
 template <typename T, int N, int M>
 struct LfSmem {
   static constexpr int MAT = D<T, N>::MAT, LD = D<T, N>::LD, MLD = MPad<T, M>::LD;
-  // P, Finv, A (-> A_cl), Delta, K (M x LD), B, W B, M (N x MLD), G (M x MLD), bc (LD); then order
-  static constexpr int elems = 4 * MAT + M * LD + 3 * N * MLD + M * MLD + LD;
-  static constexpr int tbytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
-  static constexpr int bytes = tbytes + ((N * 4 + 15) / 16) * 16;
+  // P, Finv, A (-> A_cl), Delta, K (M x LD), B, W B, M (N x MLD), G (M x MLD), Gauss-Jordan rows
+  static constexpr int elems = 4 * MAT + M * LD + 3 * N * MLD + M * MLD + GjBuf<T, N, N>::elems;
+  static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
 // Local factors eq. (FW), (factor-local).  The F = I + Delta P branch runs in
@@ -1004,7 +1043,6 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
   T* sm = reinterpret_cast<T*>(gbase);
   T *sP = sm, *sFi = sm + MAT, *sA = sm + 2 * MAT, *sD = sm + 3 * MAT, *sK = sm + 4 * MAT, *sB = sK + M * LD,
     *sWB = sB + N * MLD, *sMm = sWB + N * MLD, *sG = sMm + N * MLD, *bc = sG + M * MLD;
-  int* order = reinterpret_cast<int*>(gbase + L::tbytes);
   const int gl = g.gl, r = gl < N ? gl : 0;
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
   const bool is_root = node_is_root(w, j);
@@ -1030,8 +1068,7 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
 #pragma unroll
     for (int c = 0; c < N; ++c) { f[c] += (c == r) ? T(1) : T(0); e[c] = (c == r) ? T(1) : T(0); }
     int kpos;
-    ok = glu<T, N, G>(f, gl, bc, order, kpos);
-    glu_solve<T, N, N>(f, kpos, e, bc);         // rows of F^{-1}
+    ok = ggj<T, N, G, N>(f, e, gl, bc, kpos);  // rows of F^{-1}
     if (gl < N) row_store<T, N>(sFi + kpos * LD, e);
     __syncwarp();
     if (dnz) {
