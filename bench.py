@@ -40,9 +40,25 @@ from paper_2608_01332_b300 import inputs  # noqa: E402
 
 METRIC = "tree-LQR nodes/sec at 1e-8 rel KKT residual vs plain FP64; p50/p99 solve latency"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Fallbacks when the on-device FMA microbenchmark (tlqr_pipe_peak) cannot run:
 # FP32 lanes per SM x SMs x 2 flop per FMA x max SM clock (recipe figures); FP64 nominal.
 FP32_PEAK_TFLOPS = 128 * 148 * 2 * 2.032e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+
+
+def alu_peaks():
+    """FP32 and FP64 FMA throughput measured on this GPU (TFLOP/s) with the
+    library's FMA-chain microbenchmark, and where each number came from."""
+    from paper_2608_01332_b300 import tlqr
+    out = {}
+    for key, prec, fallback, what in (("fp32", tlqr.TLQR_PREC_MIXED, FP32_PEAK_TFLOPS,
+                                       "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz"),
+                                      ("fp64", tlqr.TLQR_PREC_FP64, FP64_PEAK_TFLOPS, "nominal FP64 1.25 TFLOP/s")):
+        try:
+            out[key] = (tlqr.tlqr_pipe_peak(prec), "measured: FMA-chain microbenchmark on this GPU, this run")
+        except Exception as e:                     # pragma: no cover - only without a working device
+            out[key] = (fallback, f"{what} (microbenchmark failed: {e})")
+    return out
 
 
 def parse():
@@ -65,6 +81,8 @@ def parse():
                     help="reference arm: CPU seconds for warm-up + timed steps together")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--e2e", action="store_true", help="run the end-to-end leg for the 10^6-node workloads too")
+    ap.add_argument("--no-spine", action="store_true",
+                    help="skip the per-round roofline of the N=2^20 spine tree in the default line")
     ap.add_argument("--quick", action="store_true",
                     help="time the headline mode only (no FP64 comparison, e2e or CPU legs); for profiler runs")
     return ap.parse_args()
@@ -243,7 +261,7 @@ def load_peaks():
 # launch divided by its operation count) from one `ncu --set full` capture of
 # the round-1 launch of the headline workload; keyed by (kernel kind, n, m,
 # precision).  Entries must be dropped when the kernel changes.
-NCU_BYTES_PER_OP = {("compress", 12, 4, "mixed"): (104.832256e6 + 30.864896e6) / 25647}
+NCU_BYTES_PER_OP = {}
 
 
 # ----------------------------------------------------------------- algorithmic work per unit
@@ -478,8 +496,8 @@ def round_roofline(launches, rnd, op, n, m, wbytes, hbm_gbs, alu_tflops, rake_co
     its rake, absorb and compress launches (and of the reverse expansion and
     T-composite launches of the same round), the measured time, and the
     roofline time max(bytes / HBM, flops / ALU peak).  The late rounds that the
-    library runs in one block (its factor tail kernel and composite tail
-    kernel) form one row together.
+    library runs in its level-asynchronous launch (contraction and expansion,
+    kind factor_tail), together with their T-composite launches, form one row.
 
     launches: (kind, operations, ms) in launch order for one factorisation."""
     R = int(rnd.max()) if len(rnd) else 0
@@ -534,12 +552,13 @@ def round_roofline(launches, rnd, op, n, m, wbytes, hbm_gbs, alu_tflops, rake_co
         if nc[r]:
             u, ms = take("expand", r, int(nc[r]))
             add(r, "expand", u, ms)
-    for r in range(1, min(R, r0 - 1) + 1):          # T composites of the head rounds
+    for r in range(1, R + 1):                       # T composites, every round
         if nc[r]:
             u, ms = take("compose_T", r, int(nc[r]))
-            add(r, "compose_T", u, ms)
-    if r0 <= R:
-        tail_ms += take("factor_tail", r0)[1]
+            if r < r0:
+                add(r, "compose_T", u, ms)
+            else:
+                tail_ms += ms
     out = []
     for r in range(1, min(R, r0 - 1) + 1):
         out.append(rows[r])
@@ -558,6 +577,63 @@ def round_roofline(launches, rnd, op, n, m, wbytes, hbm_gbs, alu_tflops, rake_co
         row["frac"] = (1e3 * t_roof / row["ms"]) if row["ms"] > 0 else None
         row["bound"] = "hbm" if row["bytes"] / (hbm_gbs * 1e9) >= row["flops"] / (alu_tflops * 1e12) else "alu"
     return out
+
+
+def profiled_rounds(solver, solve, N, n, m, wbytes, hbm, alu, dev):
+    """Per-round roofline rows of one factorisation (launches of the round kinds
+    timed one by one with CUDA events in a separate, untimed step)."""
+    import torch
+    from paper_2608_01332_b300 import tlqr
+    solve()
+    tlqr.tlqr_profile_mask(solver.f, ROUND_KINDS)
+    solve()
+    solve()
+    torch.cuda.synchronize(dev)
+    launches = tlqr.tlqr_profile_launches(solver.f)
+    tlqr.tlqr_profile_mask(solver.f, ())
+    tlqr.tlqr_profile_read(solver.f)
+    rnd, op = tlqr.tlqr_plan_schedule(solver.plan, N)
+    try:
+        half = len(launches) // 2                  # two identical steps were recorded: keep the second
+        return round_roofline(launches[half:], rnd, op, n, m, wbytes, hbm, alu,
+                              tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)
+    except RuntimeError as e:
+        return {"error": str(e)}
+
+
+def spine_round_roofline(dev, hbm, fp32_peak):
+    """Per-round roofline of the factorisation of the N = 2^20 spine hybrid
+    (n = 32, m = 8, kappa(R) = 1e2, mixed precision), measured in the same run
+    as the headline; rounds 1-3 hold 95 % of its operations."""
+    import torch
+    from paper_2608_01332_b300 import tlqr
+    w = inputs.spine_hybrid_device(dev)
+    N, n, m = len(w.parent), w.n, w.m
+    dd = w.data
+    x = torch.zeros((N, n), dtype=torch.float64, device=dev)
+    u = torch.zeros((N, m), dtype=torch.float64, device=dev)
+    y = torch.zeros((N, n), dtype=torch.float64, device=dev)
+    s = tlqr.TreeLQR(w.parent, n, m, tlqr.TLQR_PREC_MIXED)
+    try:
+        solve = lambda: tlqr.tlqr_solve(s.f, dd, x, u, y)  # noqa: E731
+        for _ in range(2):
+            solve()
+        rows = profiled_rounds(s, solve, N, n, m, 4, hbm, fp32_peak[0], dev)
+        eta = tlqr.tlqr_last_info(s.f).get("eta")
+    finally:
+        s.close()
+    del dd, x, u, y, w
+    torch.cuda.empty_cache()
+    if not isinstance(rows, list):
+        return rows
+    tot_meas = sum(r["ms"] for r in rows)
+    tot_roof = sum(r["roof_ms"] for r in rows)
+    head = [r for r in rows if isinstance(r["round"], int) and r["round"] <= 3]
+    return {"workload": f"spine_hybrid_N{N}_n{n}_m{m}_kR100 (mixed)", "eta": eta,
+            "frac": tot_roof / tot_meas if tot_meas > 0 else None, "measured_ms": tot_meas, "roof_ms": tot_roof,
+            "frac_rounds_1_3": (sum(r["roof_ms"] for r in head) / sum(r["ms"] for r in head)) if head else None,
+            "alu_peak_tflops": fp32_peak[0], "alu_peak_source": fp32_peak[1], "hbm_gbs": hbm,
+            "rounds": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in r.items()} for r in rows]}
 
 
 # ----------------------------------------------------------------- our arm
@@ -652,23 +728,9 @@ def run_ours(args, rank, world, dist):
     # per-round roofline of the factorisation (one profiled step, launches timed one by one)
     wbytes = 4 if mixed else 8
     hbm, hbm_src = load_peaks()
-    alu = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
-    solve()
-    tlqr.tlqr_profile_mask(solver.f, ROUND_KINDS)
-    solve()
-    solve()
-    torch.cuda.synchronize(dev)
-    launches = tlqr.tlqr_profile_launches(solver.f)
-    tlqr.tlqr_profile_mask(solver.f, ())
-    tlqr.tlqr_profile_read(solver.f)
-    rnd, op = tlqr.tlqr_plan_schedule(solver.plan, N)
-    per_round = None
-    try:
-        half = len(launches) // 2                  # two identical steps were recorded: keep the second
-        per_round = round_roofline(launches[half:], rnd, op, n, m, wbytes, hbm, alu,
-                                   tlqr.TLQR_OP_RAKE, tlqr.TLQR_OP_COMPRESS)
-    except RuntimeError as e:
-        per_round = {"error": str(e)}
+    peaks = alu_peaks()
+    alu, alu_src = peaks["fp32"] if mixed else peaks["fp64"]
+    per_round = profiled_rounds(solver, solve, N, n, m, wbytes, hbm, alu, dev)
 
     # plain FP64 contraction on the same GPU (the comparison of the metric)
     fp64 = None
@@ -723,7 +785,8 @@ def run_ours(args, rank, world, dist):
         bw = by * pd["units"] / sec
         fp32_kernel = mixed                        # in mixed precision every kernel runs on the FP32 pipe
                                                    # (the residual in float-float arithmetic)
-        peak_alu = (FP32_PEAK_TFLOPS if fp32_kernel else FP64_PEAK_TFLOPS) * 1e12
+        peak_alu, peak_alu_src = peaks["fp32"] if fp32_kernel else peaks["fp64"]
+        peak_alu *= 1e12
         t_alu = fl / peak_alu
         t_mem = by / (hbm * 1e9)
         if t_mem >= t_alu:
@@ -731,9 +794,7 @@ def run_ours(args, rank, world, dist):
                     "traffic": None, "peak_source": hbm_src}
         else:
             roof = {"bound": "alu", "achieved": flops / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / peak_alu, "traffic": None,
-                    "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz" if fp32_kernel
-                    else "nominal FP64 1.25 TFLOP/s"}
+                    "frac": flops / peak_alu, "traffic": None, "peak_source": peak_alu_src}
         roof.update({"kernel": f"k_{dominant}", "launches": pd["timed"], "units": pd["units"],
                      "avg_launch_ms": pd["ms"] / pd["timed"], "flops_per_unit": fl, "bytes_per_unit": by})
         bpo = NCU_BYTES_PER_OP.get((dominant, n, m, args.mode))
@@ -770,10 +831,13 @@ def run_ours(args, rank, world, dist):
         tot_roof = sum(r["roof_ms"] for r in per_round)
         line["round_roofline"] = {
             "frac": tot_roof / tot_meas if tot_meas > 0 else None, "measured_ms": tot_meas, "roof_ms": tot_roof,
-            "alu_peak_tflops": alu, "hbm_gbs": hbm,
+            "alu_peak_tflops": alu, "alu_peak_source": alu_src, "hbm_gbs": hbm,
             "rounds": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in r.items()} for r in per_round]}
     else:
         line["round_roofline"] = per_round
+    line["alu_peaks_tflops"] = {k: {"value": v[0], "source": v[1]} for k, v in peaks.items()}
+    if args.workload == "long_trunk" and not args.no_spine and rank == 0:
+        line["spine_round_roofline"] = spine_round_roofline(dev, hbm, peaks["fp32"])
     if not args.no_baseline:
         v_cpu, desc, ref = oracle_leg(w, forest)
         line["cpu_baseline"] = {"value": v_cpu, "unit": "nodes/s", "cores": 1, "kind": "oracle",

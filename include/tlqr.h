@@ -89,7 +89,20 @@ typedef struct {
   int32_t use_graphs;    /* 1: replay per-round launch sequences from CUDA graphs */
   int32_t generic_kernels; /* 1: use the run-time-n kernels even where compile-time-n
                               kernels exist (n = 4, 6, 8, 12, 16); for testing        */
-  int32_t reserved[6];
+  int32_t async_ops;     /* level-asynchronous factorisation tail (compile-time-n
+                            kernels): every structural round from the first one after
+                            which each round holds at most this many rakes plus
+                            compressions runs, with its expansions, in one persistent
+                            launch ordered by the dependency levels of
+                            eq. (earliest-level) instead of round by round.
+                            0 = the library's default (1024), < 0 = off            */
+  int32_t spin_limit;    /* polls of one dependency wait of that launch before it
+                            gives up with TLQR_ERR_TIMEOUT (0 = default, about a
+                            second with backoff)                                   */
+  int32_t test_withhold; /* testing failure detection only: 1 = the first operation of
+                            the level-asynchronous launch never signals completion, so
+                            the waits that depend on it run out (TLQR_ERR_TIMEOUT)    */
+  int32_t reserved[3];
 } tlqr_options;
 
 #define TLQR_MAX_DIM 64
@@ -180,6 +193,25 @@ int tlqr_factor_create(const tlqr_plan_t *plan, const tlqr_options *opts, tlqr_f
  * staging area of the problem's size. */
 int tlqr_factor_workspace_bytes(const tlqr_plan_t *plan, const tlqr_options *opts, size_t *bytes);
 
+/* The operation list of the level-asynchronous factorisation tail that a
+ * factor object with state dimension n and tlqr_options.async_ops = async_ops
+ * would run for this plan (host only, for inspection and testing).  counts[4]
+ * receives the first asynchronous round (0-based; = rounds when there is
+ * none), the padded operation count P, the flag count and the number of
+ * dependency levels.  When `kind` is non-NULL the host arrays receive, per
+ * position p < P: kind[p] (0 rake, 1 absorption, 2 compression, 3 expansion),
+ * node[p] (raked leaf, absorbing parent or compressed centre; -1 for a padding
+ * slot), round[p] (1-based structural round), dep_flag[3p..3p+2] (flag
+ * indices, -1 = none), dep_target[3p..3p+2] (the value each flag must reach;
+ * flag q < P is the completion flag of position q, flags >= P count the
+ * finished rakes of one sibling segment) and signal[p] (the counter a rake
+ * increments, else -1).  Errors: TLQR_ERR_ARG, TLQR_ERR_OOM. */
+int tlqr_async_schedule(const tlqr_plan_t *plan, int32_t n, int32_t async_ops, int32_t *counts, int32_t *kind,
+                        int32_t *node, int32_t *round, int32_t *dep_flag, int32_t *dep_target, int32_t *signal);
+
+/* dims[3] = {N, n, m} of a factor object (host array). */
+int tlqr_factor_dims(const tlqr_factor_t *f, int32_t *dims);
+
 /* Device bytes a factor object holds now (workspace + staging, if any). */
 int tlqr_factor_bytes(const tlqr_factor_t *f, size_t *bytes);
 
@@ -216,6 +248,22 @@ int tlqr_solve_rhs(tlqr_factor_t *f, int32_t mem, const double *q, const double 
  * non-NULL, P and K.  prob->mem and sol->mem may differ. */
 int tlqr_solve(tlqr_factor_t *f, const tlqr_problem *prob, tlqr_solution *sol, void *stream);
 
+/* Adjoint (reverse-mode) solve through the right-hand side, for
+ * differentiating a loss L(x, u, y) of the solution with respect to the data
+ * (q, r, c) (Sec. IX-A mentions differentiation through a right-hand side).
+ * The solution is z = -K^{-1} b with K the matrix of eq. (kkt) and b = (q, r, c)
+ * in its row blocks; K is symmetric, so dL/db = -K^{-1} dL/dz, which is the
+ * solution of the same factored system with (q, r, c) := (xbar, ubar, ybar).
+ * Inputs xbar [N][n], ubar [N][m] (root slot ignored), ybar [N][n] = dL/dx,
+ * dL/du, dL/dy; outputs qbar [N][n], rbar [N][m] (root slot 0), cbar [N][n] =
+ * dL/dq, dL/dr, dL/dc.  Uses the factor of the last tlqr_factor / tlqr_solve;
+ * in MIXED precision the result is refined like tlqr_solve (to refine_tol),
+ * which needs that call's problem matrices to still be valid.  Pointers follow
+ * `mem`.  Errors: TLQR_ERR_STATE before a factorisation, and those of
+ * tlqr_solve. */
+int tlqr_solve_adjoint(tlqr_factor_t *f, int32_t mem, const double *xbar, const double *ubar, const double *ybar,
+                       double *qbar, double *rbar, double *cbar, void *stream);
+
 /* Copy the Riccati matrices P_i (Thm. 1) and gains K_e (eq. (factor-local)) of
  * the last factorisation into P [N][n][n] and K [N][m][n] (either may be
  * NULL).  In MIXED precision these are the FP32 factors widened to FP64. */
@@ -236,22 +284,28 @@ int tlqr_kkt_residual(tlqr_factor_t *f, const tlqr_problem *prob, int32_t mem, c
  * run -- for example a receding-horizon controller with a hard deadline
  * (cudaMalloc / cudaFree can synchronise the device and take unbounded time) or
  * a process whose device memory belongs to another framework's allocator.  It
- * computes the same stats as tlqr_kkt_residual() (stats[0] = ||K z - b||_inf,
- * stats[1] = eta) from a plan alone, without a factor object.
- *   - prob->mem must be TLQR_MEM_DEVICE; x [N][n], u [N][m], y [N][n] are device
- *     pointers; stats is a host array of 2 doubles.
- *   - Scratch (the tree's parent/child lists, the residual vectors and the
- *     running maxima) lives in one fixed device array of
- *     TLQR_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
- *     the process exits; nothing is allocated per call.  A tree that needs
- *     more scratch (about N (2n + m) 8 + 12 N bytes) is rejected with
- *     TLQR_ERR_ARG before any work is issued.
+ * computes the same stats as tlqr_kkt_residual() from a plan alone, without a
+ * factor object: stats[0] = ||K z - b||_inf and stats[1] = eta, and for a
+ * forest plan the largest residual and the largest eta over the trees, each
+ * tree's norms taken on its own (the per-tree rule of tlqr_kkt_residual).
+ *   - prob->mem must be TLQR_MEM_DEVICE, and every data pointer as well as x
+ *     [N][n], u [N][m], y [N][n] must be device (or managed) memory: the call
+ *     asks CUDA what each pointer is and returns TLQR_ERR_ARG for a host
+ *     pointer before any work is issued.  stats is a host array of 2 doubles.
+ *   - Scratch (the tree's parent/child lists, the tree ordinals of a forest,
+ *     the residual vectors and the running maxima) lives in one fixed device
+ *     array of TLQR_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ *     keeps until the process exits; nothing is allocated per call.  A plan
+ *     that needs more scratch (about N (2n + m) 8 + 12 N bytes, plus 4 N + 32 T
+ *     for a forest of T trees) is rejected with TLQR_ERR_ARG before any work is
+ *     issued.
  *   - The first call on a device looks up the array's device address with that
  *     device current; make that first call before any stream capture.
+ *   - Each call copies the plan's index arrays from host memory and waits for
+ *     `stream`.
  *   - All calls share the one array and it keeps the previous call's contents:
  *     calls whose GPU work can overlap (different streams, different host
- *     threads) race on it and must be serialised by the caller.
- *   - Synchronises `stream`. */
+ *     threads) race on it and must be serialised by the caller. */
 #define TLQR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int tlqr_kkt_residual_noalloc(const tlqr_plan_t *plan, int32_t n, int32_t m, const tlqr_problem *prob,
                               const double *x, const double *u, const double *y, double *stats,
@@ -270,9 +324,9 @@ int tlqr_last_info(const tlqr_factor_t *f, tlqr_info *out);
 /* ------------------------------------------------------------- profiling */
 /* Kernel kinds launched by the library (one per step of Alg. 1 above).
  * TLQR_K_AFF_TAIL / TLQR_K_STATE_TAIL: the single-block kernels that run the
- * late rounds of the affine and state passes; TLQR_K_FACTOR_TAIL is reserved
- * (no factorisation tail kernel is launched: in the late rounds one
- * operation's latency, not the launch, sets the time). */
+ * late rounds of the affine and state passes; TLQR_K_FACTOR_TAIL: the
+ * persistent level-asynchronous launch of the late factorisation rounds (see
+ * tlqr_options.async_ops; its units are the operations of its list). */
 enum {
   TLQR_K_CONDENSE = 0, TLQR_K_RAKE, TLQR_K_ABSORB, TLQR_K_COMPRESS, TLQR_K_EXPAND,
   TLQR_K_LOCAL_FACTOR, TLQR_K_COMPOSE_T, TLQR_K_AFF_INIT, TLQR_K_AFF_RAKE, TLQR_K_AFF_ABSORB,
@@ -304,15 +358,31 @@ int tlqr_profile_read(tlqr_factor_t *f, tlqr_kernel_profile *out);
 int tlqr_profile_launches(tlqr_factor_t *f, int32_t *kind, int64_t *units, double *ms, int32_t max,
                           int32_t *count);
 
+/* Measured FMA throughput of the current device's FP32 (precision =
+ * TLQR_PREC_MIXED) or FP64 (TLQR_PREC_FP64) pipe in TFLOP/s: independent FMA
+ * chains on every resident warp, best of five ~10 ms launches timed with CUDA
+ * events on `stream` (a diagnostic for roofline denominators, not part of the
+ * solver).  Changes no clock or device setting. */
+int tlqr_pipe_peak(int32_t precision, double *tflops, void *stream);
+
 /* Static name of a status code. */
 const char *tlqr_status_string(int code);
 
 /* ---------------------------------------------------- batched primitives */
 /* Device-pointer batches of the local algebra, for testing each kernel on its
- * own.  count independent problems, contiguous [count][..] arrays, FP64 in and
- * out; `precision` selects the arithmetic (TLQR_PREC_FP64 or TLQR_PREC_MIXED =
- * FP32).  Return TLQR_ERR_SINGULAR / TLQR_ERR_NOT_PD if any factorisation in the
- * batch failed (synchronises `stream`). */
+ * own.  count independent problems, contiguous [count][..] device arrays, FP64
+ * in and out (converted to and from the working precision by device kernels on
+ * `stream`); `precision` selects the arithmetic (TLQR_PREC_FP64 or
+ * TLQR_PREC_MIXED = FP32).  Each call runs the kernel the solver itself
+ * launches for this n and precision: the compile-time-(n, m) group kernels for
+ * n in {4, 6, 8, 12, 16, 32} (at n = 32 in FP32 with the 3xTF32 tensor-core
+ * block products), else the run-time-n warp kernels; OR-ing
+ * TLQR_BATCHED_GENERIC into `precision` forces the run-time-n kernels.  The
+ * library allocates its own device workspace per call.  Return
+ * TLQR_ERR_SINGULAR / TLQR_ERR_NOT_PD if any factorisation in the batch failed,
+ * TLQR_ERR_ARG on a null pointer or a size out of range (synchronises
+ * `stream`). */
+#define TLQR_BATCHED_GENERIC 0x100
 
 /* Rake fold eq. (terminal-fold): out = P + A^T U (I + C U)^{-1} A.  All n x n. */
 int tlqr_batched_tau(int32_t count, int32_t n, const double *A, const double *C, const double *P,
@@ -332,6 +402,24 @@ int tlqr_batched_compose(int32_t count, int32_t n, const double *Al, const doubl
 int tlqr_batched_condense(int32_t count, int32_t n, int32_t m, const double *A, const double *B,
                           const double *R, const double *M, const double *Delta, double *Abar,
                           double *Cbar, double *Pbar, int32_t precision, void *stream);
+
+/* Reconstruction at a compressed node, eq. (value-reconstruction): from the
+ * tape (Ar, Cr, Pt) of eq. (quadratic-compress) and the child's P_k,
+ * Pj = Pt + Ar^T Pk (I + Cr Pk)^{-1} Ar.  All n x n. */
+int tlqr_batched_expand(int32_t count, int32_t n, const double *Ar, const double *Cr, const double *Pt,
+                        const double *Pk, double *Pj, int32_t precision, void *stream);
+
+/* Local factors eq. (FW), (factor-local) of an edge given the child's Riccati
+ * matrix P [n x n]: F = I + Delta P, W = P F^{-1}, G = R + B^T W B (Cholesky),
+ * K = -G^{-1} (B^T W A + M^T) [m x n], T = F^{-1} (A + B K) [n x n].  A [n x n],
+ * B [n x m], R [m x m], M [n x m] (NULL = 0), Delta [n x n] (NULL = 0). */
+int tlqr_batched_local_factor(int32_t count, int32_t n, int32_t m, const double *P, const double *A,
+                              const double *B, const double *R, const double *M, const double *Delta,
+                              double *K, double *T, int32_t precision, void *stream);
+
+/* Composite transition of eq. (transition-compose): out = Tk Tj.  All n x n. */
+int tlqr_batched_compose_T(int32_t count, int32_t n, const double *Tk, const double *Tj, double *out,
+                           int32_t precision, void *stream);
 
 /* ------------------------------------------------ node-control lifting */
 
@@ -360,6 +448,61 @@ int tlqr_lift_node_controls(const int32_t *parent, int32_t N, int32_t n, int32_t
  * y [N][n].  Host arrays. */
 int tlqr_project_lifted(int32_t N, int32_t n, int32_t m, const int32_t *map, const double *lx,
                         const double *lu, const double *ly, double *x, double *v, double *y);
+
+/* Device-side versions of the two calls above, for node-form data that already
+ * live on the GPU.  The topology arguments (parent, Nl, lifted_parent, map)
+ * are host arrays, computed on the host as by tlqr_lift_node_controls (plans
+ * are built on the host from them); every numerical array (Q ... Delta in,
+ * lQ ... lDelta out; lx, lu, ly in and x, v, y out for the projection) must be
+ * device memory (checked: TLQR_ERR_ARG otherwise), and every lifted block is
+ * written by a kernel on `stream`.  Same layouts and size query (call with
+ * lifted_parent = NULL for *Nl).  The calls allocate a small index array with
+ * cudaMallocAsync on `stream` and return after the stream has finished.
+ * Errors: TLQR_ERR_ARG, TLQR_ERR_TOPOLOGY, TLQR_ERR_OOM, TLQR_ERR_CUDA. */
+int tlqr_lift_node_controls_device(const int32_t *parent, int32_t N, int32_t n, int32_t m, const double *Q,
+                                   const double *q, const double *Mv, const double *Rv, const double *rv,
+                                   const double *Av, const double *Bv, const double *c, const double *Delta,
+                                   int32_t *Nl, int32_t *lifted_parent, double *lQ, double *lq, double *lM,
+                                   double *lR, double *lr, double *lA, double *lB, double *lc, double *lDelta,
+                                   int32_t *map, void *stream);
+int tlqr_project_lifted_device(int32_t N, int32_t n, int32_t m, const int32_t *map, const double *lx,
+                               const double *lu, const double *ly, double *x, double *v, double *y, void *stream);
+
+/* ------------------------------------------- interior-point driver (synthetic) */
+/* Box-constrained tree LQR solved by a primal-dual interior-point method whose
+ * Newton systems are tree KKT solves -- the call pattern of the nonlinear
+ * solver the paper plugs its method into (Sec. IX-B, XI-B): the problem of
+ * eq. (1)-(2) with u_lo <= u_e <= u_hi componentwise (+-Inf = no bound; the
+ * root slots are ignored).  With slacks s_lo = u - u_lo, s_hi = u_hi - u and
+ * multipliers l_lo, l_hi > 0, each iteration solves the tree system with
+ * R~ = R + diag(S), r~ = r - S u - mu / s_lo + mu / s_hi, S = l_lo / s_lo +
+ * l_hi / s_hi (tlqr_solve on `f`, in its precision), steps to the fraction tau
+ * of the boundary and sets mu = sigma * mean(l s); it stops after a full Newton
+ * step once mean(l s) <= tol.  Device arrays: prob (mem must be
+ * TLQR_MEM_DEVICE), u_lo, u_hi [N][m]; outputs x, u, y [N][n|m|n] and the
+ * multipliers lam_lo, lam_hi [N][m] (zero where a bound is absent).  f must be
+ * a factor object of `plan`.  The call allocates one device workspace for its
+ * duration and synchronises `stream` once per iteration.  Errors:
+ * TLQR_ERR_ARG (bad pointer, host memory, empty box), TLQR_ERR_NO_CONVERGENCE
+ * (max_iter reached), and those of tlqr_solve. */
+typedef struct {
+  int32_t max_iter;      /* default 100 */
+  double mu0;            /* initial barrier parameter, default 1 */
+  double sigma;          /* centring factor in (0, 1), default 0.1 */
+  double tau;            /* fraction to the boundary in (0, 1), default 0.995 */
+  double tol;            /* target mean complementarity, default 1e-9 */
+} tlqr_ipm_options;
+
+typedef struct {
+  int32_t iterations;
+  double mu, mean_gap;   /* last barrier parameter and mean l s */
+  double last_alpha;     /* step length of the last iteration */
+  double last_eta;       /* backward error of the last Newton solve (MIXED) */
+} tlqr_ipm_info;
+
+int tlqr_ipm_box(const tlqr_plan_t *plan, tlqr_factor_t *f, const tlqr_problem *prob, const double *u_lo,
+                 const double *u_hi, const tlqr_ipm_options *opts, double *x, double *u, double *y,
+                 double *lam_lo, double *lam_hi, tlqr_ipm_info *info, void *stream);
 
 #ifdef __cplusplus
 }

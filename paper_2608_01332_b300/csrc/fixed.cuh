@@ -576,6 +576,144 @@ __global__ void kf_compress(Ws<T> w, int begin, int count) {
   if (!okf && g.valid && g.gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
 }
 
+// ================================================================ level-asynchronous contraction
+// The late structural rounds hold few operations each, and executing them
+// round by round puts one kernel launch and one operation latency on the
+// critical path per phase.  Here the rakes, absorptions and compressions of
+// rounds [r0, R) and the expansions of the same compressions run in ONE
+// persistent launch without round barriers: each operation starts as soon as
+// the data it reads are final, following the dependency DAG of
+// eq. (earliest-level) (Sec. X-B, "Static dependency levels").
+//
+// The host lists the operations sorted by dependency level (so every
+// operation comes after the ones it depends on) with runs of one kind padded
+// to whole warps, and gives each operation at most three (flag, target)
+// dependencies.  A warp takes the next OPS operations from a global counter;
+// each of its lanes polls the flags of its group's operation with
+// ld.acquire.gpu until they reach their targets, the warp runs the operations
+// (all groups of a warp run the same kind, so the warp-wide collectives stay
+// converged) and then publishes completion with st.release.gpu on the
+// operation's flag; a rake also adds 1 to its sibling segment's counter, on
+// which the absorption of that segment waits.  No deadlock is possible: an
+// operation is only taken by a running warp, and its dependencies were taken
+// earlier.  Every wait is bounded (spin_limit polls with backoff): when one
+// runs out the kernel records ST_TIMEOUT, raises `abort` so that all warps
+// leave, and returns -- the context stays usable and the host reports
+// TLQR_ERR_TIMEOUT.
+enum : int { AK_RAKE = 0, AK_ABSORB = 1, AK_COMPRESS = 2, AK_EXPAND = 3 };
+constexpr int kAsyncPad = 0x0fffffff;       // index field of a padding slot
+
+struct AsyncArgs {
+  const int* op;            // [n_ops] kind << 28 | index (rake, segment or compression index)
+  const int* dep_flag;      // [3 n_ops] flag indices, -1 = none
+  const int* dep_target;    // [3 n_ops] value each flag must reach
+  const int* signal;        // [n_ops] extra flag to increment on completion (-1 = none)
+  int* flags;               // [n_flags]: done flag of op p at p, segment counters after them
+  int* counter;             // next operation to hand out
+  int* abort;               // set when a wait gave up
+  int n_ops;                // multiple of the operations per warp
+  int spin_limit;           // polls per wait before giving up
+  int withhold;             // testing: the operation at this position never signals (-1 = none)
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_gpu(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int* p) {
+  int v;
+  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T, int N>
+struct AsyncSmem {
+  static constexpr int bytes = TauSmem<T, N>::bytes > CompSmem<T, N>::bytes ? TauSmem<T, N>::bytes
+                                                                            : CompSmem<T, N>::bytes;
+};
+
+template <typename T, int N>
+__global__ void kf_async(Ws<T> w, AsyncArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Dm = D<T, N>;
+  constexpr int G = Dm::G, OPS = Dm::OPS, NN = N * N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane & (G - 1), gsub = lane / G;
+  T* sm = reinterpret_cast<T*>(smem_raw + (warp * OPS + gsub) * AsyncSmem<T, N>::bytes);
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(a.counter, OPS);
+    base = __shfl_sync(TLQR_FULL_MASK, base, 0);
+    if (base >= a.n_ops) break;
+    const int pos = base + gsub;
+    const int word = a.op[pos];
+    const int kind = word >> 28;                       // one kind per warp (host padding)
+    int idx = word & kAsyncPad;
+    const bool valid = idx != kAsyncPad;
+    // wait for the operation's inputs: every lane acquires every flag itself
+    bool gave_up = false;
+#pragma unroll 1
+    for (int d = 0; d < 3 && !gave_up; ++d) {
+      const int f = a.dep_flag[3 * pos + d];
+      if (f < 0) continue;
+      const int target = a.dep_target[3 * pos + d];
+      int polls = 0;
+      while (ld_acquire_gpu(a.flags + f) < target) {
+        if (++polls > a.spin_limit || ld_volatile(a.abort)) { gave_up = true; break; }
+        __nanosleep(polls < 64 ? 32 : 256);
+      }
+    }
+    if (__any_sync(TLQR_FULL_MASK, gave_up)) {
+      if (lane == 0) {
+        atomicCAS(w.status, 0, ST_TIMEOUT);
+        atomicExch(a.abort, 1);
+      }
+      return;
+    }
+    // a padding group repeats the warp's first operation and stores nothing
+    const int idx0 = __shfl_sync(TLQR_FULL_MASK, idx, 0);
+    if (!valid) idx = idx0;
+    const Grp g{gl, warp * OPS + gsub, valid};
+    bool ok = true;
+    if (kind == AK_RAKE) {
+      const int j = w.rake_leaf[idx];
+      const size_t o = (size_t)j * NN;
+      ok = tau_group<T, N>(g, w.U + o, w.Ea + o, w.Ec + o, w.Ep + o, w.contrib + (size_t)idx * NN, sm);
+    } else if (kind == AK_ABSORB) {
+      const int i = w.seg_parent[idx], b = w.seg_start[idx], e = w.seg_start[idx + 1];
+      T* Ui = w.U + (size_t)i * NN;
+#pragma unroll 1
+      for (int x = gl; x < NN; x += G) {
+        T acc = w.contrib[(size_t)b * NN + x];
+        for (int t = b + 1; t < e; ++t) acc += w.contrib[(size_t)t * NN + x];
+        if (valid) Ui[x] += acc;
+      }
+    } else if (kind == AK_COMPRESS) {
+      ok = compress_op<T, N>(w, idx, g, sm);
+    } else {
+      const int j = w.comp_j[idx], k = w.comp_k[idx];
+      const size_t oj = (size_t)j * NN;
+      ok = tau_group<T, N>(g, w.U + (size_t)k * NN, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm);
+    }
+    if (!ok && valid && gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
+    // publish: every lane's writes, then the release by the group's first lane
+    __threadfence();
+    __syncwarp();
+    if (valid && gl == 0 && pos != a.withhold) {
+      st_release_gpu(a.flags + pos, 1);
+      const int sig = a.signal[pos];
+      if (sig >= 0) red_release_add_gpu(a.flags + sig, 1);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- composite transitions
 // Tr_j <- T_k ; T_k <- T_k T_j  (eq. transition-compose), one group per compression.
 template <typename T, int N>

@@ -27,7 +27,7 @@
 
 namespace tlqr {
 
-enum : int { ST_OK = 0, ST_NOT_PD = 3, ST_SINGULAR = 4, ST_NONFINITE = 5 };
+enum : int { ST_OK = 0, ST_NOT_PD = 3, ST_SINGULAR = 4, ST_NONFINITE = 5, ST_TIMEOUT = 7 };
 
 template <typename T>
 struct Ws {

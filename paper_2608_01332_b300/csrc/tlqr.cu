@@ -37,6 +37,8 @@ namespace {
 constexpr int kMaxWarpsPerBlock = 8;
 constexpr int kTailOps = 512;        // per-phase operation count below which rounds join the tail kernel
 constexpr int kTailThreads = 1024;
+constexpr int kAsyncOps = 1024;     // default: rounds with at most this many operations run level-asynchronously
+constexpr int kSpinLimit = 1 << 22;  // polls of one dependency wait (with backoff: about a second) before TIMEOUT
 constexpr size_t kSmemBudget = 200 * 1024;
 
 inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -190,6 +192,133 @@ T* dalloc(size_t count, cudaError_t* err) {
   return (T*)p;
 }
 
+// Operation list of the level-asynchronous factorisation tail (fx::kf_async):
+// the rakes, absorptions and compressions of rounds [r0, R) and then the
+// expansions of those compressions in reverse round order, each with the
+// operations whose outputs it reads:
+//   rake of leaf j            <- last writer of U_j, last writer of edge slot j
+//   absorption into i         <- all rakes of its segment (a counter), last writer of U_i
+//   compression of j (i, k)   <- last writers of U_j, edge slot j, edge slot k
+//   expansion of j            <- the compression of j (its tape), producer of P_k
+//                                (the expansion of k, else the last writer of U_k)
+// Writers before round r0 ran in earlier launches and are not waited for.
+// Operations are sorted by dependency level (eq. earliest-level) and every run
+// of one (level, kind) is padded to whole warps of `ops_per_warp` operations,
+// so that a warp's operations share one code path and never depend on each
+// other.
+struct AsyncPlan {
+  int r0 = 0, n_ops = 0, n_flags = 0, levels = 0;
+  std::vector<int32_t> op, dep_flag, dep_target, signal;
+};
+
+AsyncPlan build_async(const tlqr_plan_t* P, int r0, int ops_per_warp) {
+  AsyncPlan A;
+  const int R = (int)P->rounds.size();
+  A.r0 = r0;
+  if (r0 >= R) return A;
+  struct Op { int kind, idx, level; int dep[3]; int sig; };
+  std::vector<Op> ops;
+  const int N = P->N;
+  std::vector<int> lastU(N, -1), lastE(N, -1), lastP(N, -1);
+  const int seg0 = P->rounds[r0].seg_begin, seg1 = P->rounds[R - 1].seg_end;
+  const int nseg = seg1 - seg0;
+  std::vector<int> seg_level(nseg, 0), seg_size(nseg, 0);
+  std::vector<int> comp_op(P->comp_j.size(), -1);
+  auto level_of = [&](const Op& o) {
+    int l = 0;
+    for (int d : o.dep) {
+      if (d >= 0) l = std::max(l, ops[d].level);
+      else if (d <= -2) l = std::max(l, seg_level[-2 - d]);
+    }
+    return l + 1;
+  };
+  for (int r = r0; r < R; ++r) {
+    const tlqr_round& rd = P->rounds[r];
+    for (int s = rd.seg_begin; s < rd.seg_end; ++s) {
+      for (int rr = P->seg_start[s]; rr < P->seg_start[s + 1]; ++rr) {
+        const int j = P->rake_leaf[rr];
+        Op o{fx::AK_RAKE, rr, 0, {lastU[j], lastE[j], -1}, s - seg0};
+        o.level = level_of(o);
+        seg_level[s - seg0] = std::max(seg_level[s - seg0], o.level);
+        seg_size[s - seg0]++;
+        ops.push_back(o);
+      }
+    }
+    for (int s = rd.seg_begin; s < rd.seg_end; ++s) {
+      const int i = P->seg_parent[s];
+      Op o{fx::AK_ABSORB, s, 0, {-2 - (s - seg0), lastU[i], -1}, -1};
+      o.level = level_of(o);
+      lastU[i] = (int)ops.size();
+      ops.push_back(o);
+    }
+    for (int c = rd.comp_begin; c < rd.comp_end; ++c) {
+      const int j = P->comp_j[c], k = P->comp_k[c];
+      Op o{fx::AK_COMPRESS, c, 0, {lastU[j], lastE[j], lastE[k]}, -1};
+      o.level = level_of(o);
+      comp_op[c] = (int)ops.size();
+      lastE[k] = lastE[j] = (int)ops.size();
+      ops.push_back(o);
+    }
+  }
+  for (int r = R - 1; r >= r0; --r) {
+    const tlqr_round& rd = P->rounds[r];
+    for (int c = rd.comp_begin; c < rd.comp_end; ++c) {
+      const int j = P->comp_j[c], k = P->comp_k[c];
+      Op o{fx::AK_EXPAND, c, 0, {comp_op[c], lastP[k] >= 0 ? lastP[k] : lastU[k], -1}, -1};
+      o.level = level_of(o);
+      lastP[j] = (int)ops.size();
+      ops.push_back(o);
+    }
+  }
+  std::vector<int> order(ops.size());
+  for (size_t t = 0; t < ops.size(); ++t) order[t] = (int)t;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return ops[a].level != ops[b].level ? ops[a].level < ops[b].level : ops[a].kind < ops[b].kind;
+  });
+  std::vector<int> pos_of(ops.size(), -1);
+  std::vector<int> slot_op;                                  // op id per position, -1 = padding
+  for (size_t t = 0; t < order.size(); ++t) {
+    const Op& o = ops[order[t]];
+    if (t > 0) {
+      const Op& prev = ops[order[t - 1]];
+      if (prev.level != o.level || prev.kind != o.kind)
+        while (slot_op.size() % ops_per_warp) slot_op.push_back(-1);
+    }
+    pos_of[order[t]] = (int)slot_op.size();
+    slot_op.push_back(order[t]);
+    A.levels = std::max(A.levels, o.level);
+  }
+  while (slot_op.size() % ops_per_warp) slot_op.push_back(-1);
+  A.n_ops = (int)slot_op.size();
+  A.n_flags = A.n_ops + nseg;
+  A.op.assign(A.n_ops, 0);
+  A.dep_flag.assign(3 * (size_t)A.n_ops, -1);
+  A.dep_target.assign(3 * (size_t)A.n_ops, 0);
+  A.signal.assign(A.n_ops, -1);
+  int last_kind = 0;
+  for (int p = 0; p < A.n_ops; ++p) {
+    const int id = slot_op[p];
+    if (id < 0) {                                            // padding: the kind of its run
+      A.op[p] = (last_kind << 28) | fx::kAsyncPad;
+      continue;
+    }
+    const Op& o = ops[id];
+    last_kind = o.kind;
+    A.op[p] = (o.kind << 28) | o.idx;
+    for (int d = 0; d < 3; ++d) {
+      if (o.dep[d] >= 0) {
+        A.dep_flag[3 * (size_t)p + d] = pos_of[o.dep[d]];
+        A.dep_target[3 * (size_t)p + d] = 1;
+      } else if (o.dep[d] <= -2) {
+        A.dep_flag[3 * (size_t)p + d] = A.n_ops + (-2 - o.dep[d]);
+        A.dep_target[3 * (size_t)p + d] = seg_size[-2 - o.dep[d]];
+      }
+    }
+    if (o.sig >= 0) A.signal[p] = A.n_ops + o.sig;
+  }
+  return A;
+}
+
 struct DevPlan {
   int *rake_leaf = nullptr, *rake_parent = nullptr, *seg_parent = nullptr, *seg_start = nullptr;
   int *comp_j = nullptr, *comp_i = nullptr, *comp_k = nullptr;
@@ -239,7 +368,13 @@ struct tlqr_factor_t {
   int fixed_n = 0;                 // n of the fixed-dimension kernels in use (0 = run-time n)
   int fixed_m = 0;                 // m of the fixed (n, m) kernels in use (0 = run-time m)
   fx::RoundDesc* d_rounds = nullptr;  // device copy of the plan's rounds
+  int sms = 0;                     // streaming multiprocessors of the factor's device
   int tail_r0 = 0;                 // first round handled by the single-block tail kernels
+  // level-asynchronous factorisation tail (compile-time-n kernels only)
+  AsyncPlan async;                 // host copy of the operation list; async.r0 == rounds: none
+  int *a_op = nullptr, *a_dep_flag = nullptr, *a_dep_target = nullptr, *a_signal = nullptr;
+  int* a_flags = nullptr;          // [n_flags] flags, then the work counter and the abort word
+  int async_blocks = 0;            // persistent grid of kf_async
 
   template <typename T>
   Ws<T> ws(const tlqr_problem& p) const {
@@ -299,6 +434,7 @@ int map_status(int st) {
     case ST_NOT_PD: return TLQR_ERR_NOT_PD;
     case ST_SINGULAR: return TLQR_ERR_SINGULAR;
     case ST_NONFINITE: return TLQR_ERR_NONFINITE;
+    case ST_TIMEOUT: return TLQR_ERR_TIMEOUT;
     default: return TLQR_ERR_CUDA;
   }
 }
@@ -343,6 +479,13 @@ void carve_factor(tlqr_factor_t* f, Carve& c) {
   f->dp.child_list = ints(P->child_list);
   f->dp.tree = P->n_trees > 1 ? ints(P->tree_of) : nullptr;
   f->d_rounds = reinterpret_cast<fx::RoundDesc*>(c.take<int>(6 * P->rounds.size(), sizeof(int)));
+  if (f->async.n_ops > 0) {
+    f->a_op = ints(f->async.op);
+    f->a_dep_flag = ints(f->async.dep_flag);
+    f->a_dep_target = ints(f->async.dep_target);
+    f->a_signal = ints(f->async.signal);
+    f->a_flags = c.take<int>((size_t)f->async.n_flags + 2, sizeof(int));
+  }
   const size_t N = P->N, n = f->opt.n, m = f->opt.m, nn = n * n, nm = n * m, mm = m * m;
   const size_t nrake = std::max<size_t>(1, P->rake_leaf.size());
   const size_t ts = f->ts;
@@ -388,6 +531,12 @@ int upload_plan(tlqr_factor_t* f) {
   up(P->child_list, f->dp.child_list);
   if (P->n_trees > 1) up(P->tree_of, f->dp.tree);
   up(round_table(P), reinterpret_cast<int*>(f->d_rounds));
+  if (f->async.n_ops > 0) {
+    up(f->async.op, f->a_op);
+    up(f->async.dep_flag, f->a_dep_flag);
+    up(f->async.dep_target, f->a_dep_target);
+    up(f->async.signal, f->a_signal);
+  }
   // tail: the longest suffix of rounds whose phases each hold at most kTailOps operations
   const int R = (int)P->rounds.size();
   f->tail_r0 = R;
@@ -438,11 +587,37 @@ cudaError_t launch_tail(Recorder* rc, int kind, Kernel kernel, cudaStream_t st, 
   return e;
 }
 
-cudaError_t launch_split(Recorder* rc, const SplitList& L, cudaStream_t st) {
-  const int blocks = 148 * 4, threads = 256;
+cudaError_t launch_split(Recorder* rc, const SplitList& L, int sms, cudaStream_t st) {
+  const int blocks = sms * 4, threads = 256;
   k_split_ff<<<blocks, threads, 0, st>>>(L);
   cudaError_t e = cudaGetLastError();
   if (rc) { rc->launches[TLQR_K_RESIDUAL]++; }
+  return e;
+}
+
+// One persistent launch of the level-asynchronous factorisation tail.
+template <typename T, int N>
+cudaError_t launch_async(tlqr_factor_t* f, Recorder* rc, const Ws<T>& w, cudaStream_t st) {
+  const AsyncPlan& A = f->async;
+  cudaError_t e = cudaMemsetAsync(f->a_flags, 0, ((size_t)A.n_flags + 2) * sizeof(int), st);
+  if (e) return e;
+  fx::AsyncArgs a{};
+  a.op = f->a_op; a.dep_flag = f->a_dep_flag; a.dep_target = f->a_dep_target; a.signal = f->a_signal;
+  a.flags = f->a_flags; a.counter = f->a_flags + A.n_flags; a.abort = f->a_flags + A.n_flags + 1;
+  a.n_ops = A.n_ops;
+  a.spin_limit = f->opt.spin_limit > 0 ? f->opt.spin_limit : kSpinLimit;
+  a.withhold = f->opt.test_withhold ? 0 : -1;
+  constexpr int gpb = 128 / fx::D<T, N>::G;
+  const size_t smem = (size_t)fx::AsyncSmem<T, N>::bytes * gpb;
+  if (!(rc && rc->capture) && (e = ensure_smem(fx::kf_async<T, N>, smem))) return e;
+  const int blocks = std::max(1, std::min((A.n_ops + gpb - 1) / gpb, f->async_blocks));
+  const bool timed = rc && (rc->mask >> TLQR_K_FACTOR_TAIL) & 1u;
+  EvPair ev{TLQR_K_FACTOR_TAIL, nullptr, nullptr, A.n_ops};
+  if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
+  fx::kf_async<T, N><<<blocks, 128, smem, st>>>(w, a);
+  e = cudaGetLastError();
+  if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
+  if (rc) { rc->launches[TLQR_K_FACTOR_TAIL]++; rc->units[TLQR_K_FACTOR_TAIL] += A.n_ops; }
   return e;
 }
 
@@ -465,7 +640,9 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
     return e;
   }
   const int R = (int)P->rounds.size();
-  for (int ri = 0; ri < R; ++ri) {
+  // rounds [RA, R) and their expansions run in the level-asynchronous kernel
+  const int RA = (NF > 0 && f->async.n_ops > 0) ? f->async.r0 : R;
+  for (int ri = 0; ri < RA; ++ri) {
     const tlqr_round& rd = P->rounds[ri];
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
     if constexpr (NF > 0) {
@@ -483,7 +660,10 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
       return e;
     }
   }
-  for (int ri = R - 1; ri >= 0; --ri) {
+  if constexpr (NF > 0) {
+    if (RA < R && (e = launch_async<T, NX>(f, rc, w, st))) return e;
+  }
+  for (int ri = RA - 1; ri >= 0; --ri) {
     const tlqr_round* it = &P->rounds[ri];
     const int nc = it->comp_end - it->comp_begin;
     if constexpr (NF > 0) {
@@ -651,12 +831,12 @@ bool has_fixed_pair(int n, int m) {
 // node pass (see residual_nodes.cuh).  Returns cudaErrorNotSupported when
 // (n, m) has no such kernels.
 template <int N, int M>
-cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::NodeArgs& na, cudaStream_t st,
-                             bool capturing) {
+cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::NodeArgs& na, int sms,
+                             cudaStream_t st, bool capturing) {
   constexpr int OPS = rn::RG<N>::OPS, threads = 128, gpb = (threads / 32) * OPS;
   const size_t se = (size_t)rn::EdgeBuf<N, M>::group_bytes(a.Delta != nullptr, a.M != nullptr) * gpb;
   const size_t sn = (size_t)rn::NodeBuf<N>::group_bytes * gpb;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, 148 * 16));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, (long long)sms * 16));
   const bool forest = a.tree != nullptr;
   auto ek = forest ? rn::k_res_edge<N, M, true> : rn::k_res_edge<N, M, false>;
   auto nk = forest ? rn::k_res_node<N, true> : rn::k_res_node<N, false>;
@@ -688,9 +868,9 @@ cudaError_t configure_res_nodes(int n, int m) {
 }
 
 cudaError_t dispatch_res_nodes(int n, int m, const ResidualArgs& a, const FFArgs& fa, const rn::NodeArgs& na,
-                               cudaStream_t st, bool capturing) {
+                               int sms, cudaStream_t st, bool capturing) {
 #define X(n_, m_) \
-  if (n == n_ && m == m_) return launch_res_nodes<n_, m_>(a, fa, na, st, capturing);
+  if (n == n_ && m == m_) return launch_res_nodes<n_, m_>(a, fa, na, sms, st, capturing);
   TLQR_FIXED_PAIRS(X)
 #undef X
   return cudaErrorNotSupported;
@@ -740,18 +920,18 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
       add(p.c, nullptr, nullptr, N * n, bs);
     }
     L.maxes = f->maxes;
-    if ((e = launch_split(rc, L, st))) return e;
+    if ((e = launch_split(rc, L, f->sms, st))) return e;
     fa = FFArgs{f->xh, f->xl, f->uh, f->ul, f->yh, f->yl};
   }
   const size_t rows = (size_t)P->N * (2 * f->opt.n + f->opt.m);
   const int threads = 256;
-  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, 148 * 32);
+  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, (size_t)f->sms * 32);
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
   EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr, P->N};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
   if (ff && use_node_residual(f)) {
     const rn::NodeArgs na{f->rwh, f->rwl, f->rwk};
-    if ((e = dispatch_res_nodes(f->fixed_n, f->fixed_m, a, fa, na, st, rc && rc->capture))) return e;
+    if ((e = dispatch_res_nodes(f->fixed_n, f->fixed_m, a, fa, na, f->sms, st, rc && rc->capture))) return e;
   } else if (a.tree) {
     if (ff) k_residual_ff_trees<<<blocks, threads, 0, st>>>(a, fa);
     else k_residual_trees<<<blocks, threads, 0, st>>>(a);
@@ -976,7 +1156,36 @@ cudaError_t configure_fixed() {
   if (!e) e = ensure_smem(fx::kf_expand<T, N>, (size_t)fx::TauSmem<T, N>::bytes * gpb);
   if (!e) e = ensure_smem(fx::kf_compress<T, N>, (size_t)fx::CompSmem<T, N>::bytes * gpb);
   if (!e) e = ensure_smem(fx::kf_compose_T<T, N>, (size_t)fx::ComposeSmem<T, N>::bytes * gpb);
+  if (!e) e = ensure_smem(fx::kf_async<T, N>, (size_t)fx::AsyncSmem<T, N>::bytes * gpb);
   return e;
+}
+
+// Resident 128-thread blocks of kf_async per SM (its persistent grid is this
+// times the SM count; correctness does not depend on it).
+template <typename T, int N>
+int async_occupancy() {
+  constexpr int gpb = 128 / fx::D<T, N>::G;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fx::kf_async<T, N>, 128,
+                                                    (size_t)fx::AsyncSmem<T, N>::bytes * gpb) != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return std::max(1, b);
+}
+template <typename T>
+int async_occupancy_n(int n) {
+  switch (n) {
+    case 4: return async_occupancy<T, 4>();
+    case 6: return async_occupancy<T, 6>();
+    case 8: return async_occupancy<T, 8>();
+    case 12: return async_occupancy<T, 12>();
+    case 16: return async_occupancy<T, 16>();
+    case 32:
+      if constexpr (fixed_for<T>(32)) return async_occupancy<T, 32>();
+      return 1;
+    default: return 1;
+  }
 }
 template <typename T, int N, int M>
 cudaError_t configure_fixed_nm() {
@@ -1008,6 +1217,39 @@ cudaError_t configure_fixed_n(int n) {
       return cudaSuccess;
     default: return cudaSuccess;
   }
+}
+
+// Host-side kernel selection of a factor object (no CUDA calls): the
+// compile-time-(n, m) kernels where they exist, and the rounds handed to the
+// level-asynchronous kernel -- every round from the first one after which each
+// round holds at most async_ops operations (default kAsyncOps).  Returns
+// nonzero when the host ran out of memory.
+int select_kernels(tlqr_factor_t* f) {
+  const tlqr_options& o = f->opt;
+  const int n = o.n, m = o.m;
+  f->fixed_n = (has_fixed_kernels(n) && !o.generic_kernels) ? n : 0;
+  // FP64: groups of 8 / 16 lanes for n = 6 / 12 leave lanes idle, which costs FP64 issue slots;
+  // the run-time-n kernels keep all 32 lanes busy and are faster there.
+  if (f->ts == 8 && (n == 6 || n == 12 || n == 32)) f->fixed_n = 0;
+  f->fixed_m = (f->fixed_n && has_fixed_pair(n, m)) ? m : 0;
+  f->async = AsyncPlan{};
+  f->async.r0 = (int)f->plan->rounds.size();
+  if (f->fixed_n > 0 && o.async_ops >= 0) {
+    const int thr = o.async_ops > 0 ? o.async_ops : kAsyncOps;
+    int r0 = (int)f->plan->rounds.size();
+    while (r0 > 0) {
+      const tlqr_round& r = f->plan->rounds[r0 - 1];
+      if ((r.rake_end - r.rake_begin) + (r.comp_end - r.comp_begin) > thr) break;
+      --r0;
+    }
+    const int G = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+    try {
+      f->async = build_async(f->plan, r0, 32 / G);
+    } catch (const std::bad_alloc&) {
+      return 1;
+    }
+  }
+  return 0;
 }
 
 // Enqueue the factorisation; with `sync` also wait and report its status.
@@ -1083,7 +1325,11 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   if (f->opt.max_refine <= 0) f->opt.max_refine = 10;
   if (!(f->opt.refine_tol > 0)) f->opt.refine_tol = 1e-8;
   f->ts = opts->precision == TLQR_PREC_FP64 ? 8 : 4;
-  if (cudaGetDevice(&f->device)) { delete f; return TLQR_ERR_CUDA; }
+  if (cudaGetDevice(&f->device) ||
+      cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device) || f->sms < 1) {
+    delete f;
+    return TLQR_ERR_CUDA;
+  }
   if (cudaStreamCreateWithFlags(&f->work, cudaStreamNonBlocking) ||
       cudaEventCreateWithFlags(&f->ev_in, cudaEventDisableTiming) ||
       cudaEventCreateWithFlags(&f->ev_out, cudaEventDisableTiming)) {
@@ -1094,11 +1340,7 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   const WarpBytes wb = warp_bytes(n, m, f->ts);
   const size_t worst = std::max({wb.compress, wb.local_factor, wb.tau, wb.condense});
   if (worst > kSmemBudget) { delete f; return TLQR_ERR_ARG; }
-  f->fixed_n = (has_fixed_kernels(n) && !opts->generic_kernels) ? n : 0;
-  // FP64: groups of 8 / 16 lanes for n = 6 / 12 leave lanes idle, which costs FP64 issue slots;
-  // the run-time-n kernels keep all 32 lanes busy and are faster there.
-  if (f->ts == 8 && (n == 6 || n == 12 || n == 32)) f->fixed_n = 0;
-  f->fixed_m = (f->fixed_n && has_fixed_pair(n, m)) ? m : 0;
+  if (select_kernels(f)) { delete f; return TLQR_ERR_OOM; }
   if ((f->ts == 8 ? configure_kernels<double>(n, m) : configure_kernels<float>(n, m)) != cudaSuccess ||
       (f->ts == 8 ? configure_fixed_n<double>(f->fixed_n) : configure_fixed_n<float>(f->fixed_n)) != cudaSuccess ||
       (f->ts == 8 ? configure_fixed_pair<double>(f->fixed_n, f->fixed_m)
@@ -1107,6 +1349,8 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
     delete f;
     return TLQR_ERR_CUDA;
   }
+  if (f->async.n_ops > 0)
+    f->async_blocks = f->sms * (f->ts == 8 ? async_occupancy_n<double>(n) : async_occupancy_n<float>(n));
   Carve sizing;
   carve_factor(f, sizing);
   void* arena = nullptr;
@@ -1143,9 +1387,64 @@ extern "C" int tlqr_factor_workspace_bytes(const tlqr_plan_t* plan, const tlqr_o
   tmp.plan = plan;
   tmp.opt = *opts;
   tmp.ts = opts->precision == TLQR_PREC_FP64 ? 8 : 4;
+  if (select_kernels(&tmp)) return TLQR_ERR_OOM;
   Carve c;
   carve_factor(&tmp, c);
   *bytes = c.off;
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_async_schedule(const tlqr_plan_t* plan, int32_t n, int32_t async_ops, int32_t* counts,
+                                   int32_t* kind, int32_t* node, int32_t* round, int32_t* dep_flag,
+                                   int32_t* dep_target, int32_t* signal) {
+  if (!plan || !counts || n < 1 || n > TLQR_MAX_DIM) return TLQR_ERR_ARG;
+  const int R = (int)plan->rounds.size();
+  int r0 = R;
+  if (async_ops >= 0) {
+    const int thr = async_ops > 0 ? async_ops : kAsyncOps;
+    while (r0 > 0) {
+      const tlqr_round& r = plan->rounds[r0 - 1];
+      if ((r.rake_end - r.rake_begin) + (r.comp_end - r.comp_begin) > thr) break;
+      --r0;
+    }
+  }
+  const int G = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+  AsyncPlan A;
+  try {
+    A = build_async(plan, r0, 32 / G);
+  } catch (const std::bad_alloc&) {
+    return TLQR_ERR_OOM;
+  }
+  counts[0] = A.r0; counts[1] = A.n_ops; counts[2] = A.n_flags; counts[3] = A.levels;
+  if (!kind) return TLQR_OK;
+  std::vector<int> seg_round(plan->seg_parent.size(), 0);
+  for (int r = 0; r < R; ++r)
+    for (int s2 = plan->rounds[r].seg_begin; s2 < plan->rounds[r].seg_end; ++s2) seg_round[s2] = r + 1;
+  for (int p = 0; p < A.n_ops; ++p) {
+    const int k = A.op[p] >> 28, idx = A.op[p] & fx::kAsyncPad;
+    kind[p] = k;
+    int v = -1, rr = 0;
+    if (idx != fx::kAsyncPad) {
+      if (k == fx::AK_RAKE) { v = plan->rake_leaf[idx]; rr = plan->round_of_node[v]; }
+      else if (k == fx::AK_ABSORB) { v = plan->seg_parent[idx]; rr = seg_round[idx]; }
+      else { v = plan->comp_j[idx]; rr = plan->round_of_node[v]; }
+    }
+    if (node) node[p] = v;
+    if (round) round[p] = rr;
+    for (int d = 0; d < 3; ++d) {
+      if (dep_flag) dep_flag[3 * p + d] = A.dep_flag[3 * (size_t)p + d];
+      if (dep_target) dep_target[3 * p + d] = A.dep_target[3 * (size_t)p + d];
+    }
+    if (signal) signal[p] = A.signal[p];
+  }
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_factor_dims(const tlqr_factor_t* f, int32_t* dims) {
+  if (!f || !dims) return TLQR_ERR_ARG;
+  dims[0] = f->plan->N;
+  dims[1] = f->opt.n;
+  dims[2] = f->opt.m;
   return TLQR_OK;
 }
 
@@ -1208,7 +1507,7 @@ int get_PK_impl(tlqr_factor_t* f, int32_t mem, double* P, double* K, cudaStream_
     dP = P ? s.P : nullptr;
     dK = K ? s.K : nullptr;
   }
-  const int blocks = 4 * 148;
+  const int blocks = 4 * f->sms;
   if (f->ts == 8)
     k_export_PK<double><<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, (const int*)f->dp.parent, (const double*)f->U,
                                                 (const double*)f->K, dP, dK);
@@ -1235,6 +1534,72 @@ extern "C" int tlqr_get_PK(tlqr_factor_t* f, int32_t mem, double* P, double* K, 
   return get_PK_impl(f, mem, P, K, scope.st);
 }
 
+namespace {
+// FP64 iterative refinement through the FP32 factors: the FP64 residual of
+// eq. (kkt) for the problem dp (matrices and right-hand side) is re-solved
+// and added to (x, u, y) until the largest per-tree eta <= refine_tol.
+int refine(tlqr_factor_t* f, const tlqr_problem& dp, double* x, double* u, double* y, cudaStream_t st) {
+  int steps = 0, rc = 0;
+  double absr = 0, eta = INFINITY;
+  for (;;) {
+    // residual graph: FP64 residual, ||.|| maxima and the status word to the host
+    if (residual_impl(f, dp, x, u, y, steps == 0 ? 1 : 0, st)) return TLQR_ERR_CUDA;
+    if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+    f->prof.harvest();
+    if ((rc = map_status(*f->h_status))) { f->factored = false; return rc; }
+    residual_stats(f, &absr, &eta);
+    if (eta <= f->opt.refine_tol || steps >= f->opt.max_refine || !std::isfinite(eta)) break;
+    if (solve_impl(f, f->res_x, f->res_u, f->res_c, x, u, y, 1, st)) return TLQR_ERR_CUDA;
+    ++steps;
+  }
+  f->info.refine_steps = steps;
+  f->info.eta = eta;
+  f->info.abs_residual = absr;
+  if (!std::isfinite(eta)) return TLQR_ERR_NONFINITE;
+  if (eta > f->opt.refine_tol) return TLQR_ERR_NO_CONVERGENCE;
+  return TLQR_OK;
+}
+}  // namespace
+
+extern "C" int tlqr_solve_adjoint(tlqr_factor_t* f, int32_t mem, const double* xbar, const double* ubar,
+                                  const double* ybar, double* qbar, double* rbar, double* cbar, void* stream) {
+  if (!f || !xbar || !ubar || !ybar || !qbar || !rbar || !cbar) return TLQR_ERR_ARG;
+  if (mem != TLQR_MEM_DEVICE && mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
+  if (!f->factored) return TLQR_ERR_STATE;
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  const double *q = xbar, *r = ubar, *c = ybar;
+  double *x = qbar, *u = rbar, *y = cbar;
+  int rc = 0;
+  if (mem == TLQR_MEM_HOST) {
+    if ((rc = ensure_stage(f))) return rc;
+    Stage s = stage_layout(f);
+    cudaError_t e = h2d(s.q, xbar, N * n, st);
+    if (!e) e = h2d(s.r, ubar, N * m, st);
+    if (!e) e = h2d(s.c, ybar, N * n, st);
+    if (e) return TLQR_ERR_CUDA;
+    q = s.q; r = s.r; c = s.c; x = s.x; u = s.u; y = s.y;
+  }
+  f->info = tlqr_info{};
+  // the KKT matrix of eq. (kkt) is symmetric: the cotangent is the right-hand side
+  if (solve_impl(f, q, r, c, x, u, y, 0, st)) return TLQR_ERR_CUDA;
+  if (f->opt.precision == TLQR_PREC_MIXED) {
+    tlqr_problem dp = f->dprob;
+    dp.q = q; dp.r = r; dp.c = c;
+    if ((rc = refine(f, dp, x, u, y, st))) return rc;
+  }
+  if (mem == TLQR_MEM_HOST) {
+    cudaError_t e = d2h(qbar, x, N * n, st);
+    if (!e) e = d2h(rbar, u, N * m, st);
+    if (!e) e = d2h(cbar, y, N * n, st);
+    if (e) return TLQR_ERR_CUDA;
+  }
+  rc = read_status(f, st);
+  f->prof.harvest();
+  return rc;
+}
+
 extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solution* sol, void* stream) {
   if (!f || !sol || !sol->x || !sol->u || !sol->y) return TLQR_ERR_ARG;
   if (sol->mem != TLQR_MEM_DEVICE && sol->mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
@@ -1256,27 +1621,7 @@ extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solut
   if ((rc = factor_impl(f, &dp, st, false))) return rc;
   f->info = tlqr_info{};
   if (solve_impl(f, dp.q, dp.r, dp.c, x, u, y, 0, st)) return TLQR_ERR_CUDA;
-  if (f->opt.precision == TLQR_PREC_MIXED) {
-    // FP64 iterative refinement through the FP32 factors
-    int steps = 0;
-    double absr = 0, eta = INFINITY;
-    for (;;) {
-      // residual graph: FP64 residual, ||.|| maxima and the status word to the host
-      if (residual_impl(f, dp, x, u, y, steps == 0 ? 1 : 0, st)) return TLQR_ERR_CUDA;
-      if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
-      f->prof.harvest();
-      if ((rc = map_status(*f->h_status))) { f->factored = false; return rc; }
-      residual_stats(f, &absr, &eta);
-      if (eta <= f->opt.refine_tol || steps >= f->opt.max_refine || !std::isfinite(eta)) break;
-      if (solve_impl(f, f->res_x, f->res_u, f->res_c, x, u, y, 1, st)) return TLQR_ERR_CUDA;
-      ++steps;
-    }
-    f->info.refine_steps = steps;
-    f->info.eta = eta;
-    f->info.abs_residual = absr;
-    if (!std::isfinite(eta)) return TLQR_ERR_NONFINITE;
-    if (eta > f->opt.refine_tol) return TLQR_ERR_NO_CONVERGENCE;
-  }
+  if (f->opt.precision == TLQR_PREC_MIXED && (rc = refine(f, dp, x, u, y, st))) return rc;
   if (sol->P || sol->K) {
     if ((rc = get_PK_impl(f, sol->mem, sol->P, sol->K, st))) return rc;
   }
@@ -1339,11 +1684,82 @@ extern "C" int tlqr_last_info(const tlqr_factor_t* f, tlqr_info* out) {
 
 namespace {
 
+// FP64 <-> working precision on the device (a plain copy when both are FP64).
+template <typename D, typename S>
+__global__ void k_convert(D* dst, const S* src, size_t count) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (D)src[e];
+}
+template <typename D, typename S>
+cudaError_t convert(D* dst, const S* src, size_t count, int sms, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const int blocks = (int)std::min<size_t>((count + 255) / 256, (size_t)sms * 8);
+  k_convert<D, S><<<blocks, 256, 0, st>>>(dst, src, count);
+  return cudaGetLastError();
+}
+
+enum { B_TAU = 0, B_COMPOSE, B_CONDENSE, B_EXPAND, B_LOCAL_FACTOR, B_COMPOSE_T };
+
+// Launch one batched primitive with the compile-time-(n, m) group kernels the
+// solver itself runs for this n (NF > 0; at n = 32 in FP32 with the
+// tensor-core block products), or the run-time-n warp kernels (NF == 0).
+template <typename T, int NF, int MF>
+cudaError_t batched_launch(int kind, const Ws<T>& w, int count, int n, int m, cudaStream_t st) {
+  const WarpBytes wb = warp_bytes(n, m, sizeof(T));
+  constexpr int NX = NF > 0 ? NF : 4;
+  constexpr int MX = MF > 0 ? MF : 2;
+  constexpr int G = fx::D<T, NX>::G;
+  switch (kind) {
+    case B_TAU:
+      if constexpr (NF > 0) return launch_groups(nullptr, TLQR_K_RAKE, fx::kf_rake<T, NX>, count, G, fx::TauSmem<T, NX>::bytes, st, w, 0, count);
+      return launch_warps(nullptr, TLQR_K_RAKE, k_rake<T>, count, wb.tau, st, w, 0, count, (int)wb.tau);
+    case B_EXPAND:
+      if constexpr (NF > 0) return launch_groups(nullptr, TLQR_K_EXPAND, fx::kf_expand<T, NX>, count, G, fx::TauSmem<T, NX>::bytes, st, w, 0, count);
+      return launch_warps(nullptr, TLQR_K_EXPAND, k_expand<T>, count, wb.tau, st, w, 0, count, (int)wb.tau);
+    case B_COMPOSE:
+      if constexpr (NF > 0) return launch_groups(nullptr, TLQR_K_COMPRESS, fx::kf_compress<T, NX>, count, G, fx::CompSmem<T, NX>::bytes, st, w, 0, count);
+      return launch_warps(nullptr, TLQR_K_COMPRESS, k_compress<T>, count, wb.compress, st, w, 0, count, (int)wb.compress);
+    case B_COMPOSE_T:
+      if constexpr (NF > 0) return launch_groups(nullptr, TLQR_K_COMPOSE_T, fx::kf_compose_T<T, NX>, count, G, fx::ComposeSmem<T, NX>::bytes, st, w, 0, count);
+      return launch_warps(nullptr, TLQR_K_COMPOSE_T, k_compose_T<T>, count, wb.compose_T, st, w, 0, count, (int)wb.compose_T);
+    case B_CONDENSE:
+      if constexpr (MF > 0) return launch_groups(nullptr, TLQR_K_CONDENSE, fx::kf_condense<T, NX, MX>, count, G, fx::CondSmem<T, NX, MX>::bytes, st, w, count);
+      return launch_warps(nullptr, TLQR_K_CONDENSE, k_condense<T>, count, wb.condense, st, w, (int)wb.condense);
+    case B_LOCAL_FACTOR:
+      if constexpr (MF > 0) return launch_groups(nullptr, TLQR_K_LOCAL_FACTOR, fx::kf_local_factor<T, NX, MX>, count, G, fx::LfSmem<T, NX, MX>::bytes, st, w, count);
+      return launch_warps(nullptr, TLQR_K_LOCAL_FACTOR, k_local_factor<T>, count, wb.local_factor, st, w, (int)wb.local_factor);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
-int batched_ops(int kind, int count, int n, int m, const double* const* in, double* const* out, cudaStream_t st) {
-  // Slots 0..count-1 hold the "left" data, count..2count-1 the "right" data.
+cudaError_t batched_dispatch(int kind, const Ws<T>& w, int count, int n, int m, int generic, cudaStream_t st) {
+  const bool nm_kind = kind == B_CONDENSE || kind == B_LOCAL_FACTOR;
+  if (!generic) {
+#define X(n_, m_)                                                                       \
+    if constexpr (fixed_for<T>(n_))                                                     \
+      if (n == n_ && (m_ == 0 ? !nm_kind || !has_fixed_pair(n, m) : (nm_kind && m == m_))) \
+        return batched_launch<T, n_, m_>(kind, w, count, n, m, st);
+    TLQR_FIXED_CASES(X)
+#undef X
+  }
+  return batched_launch<T, 0, 0>(kind, w, count, n, m, st);
+}
+
+// Batched primitives: count independent problems in contiguous FP64 device
+// arrays.  Slots 0..count-1 of the workspace hold the "left" operands (the
+// edge into a compressed centre, the tape, the node whose factor is built),
+// slots count..2count-1 the "right" ones; index arrays map operation t to
+// slots t and count + t.  Inputs are converted to T and results back to FP64
+// by device kernels on `stream`.
+template <typename T>
+int batched_ops(int kind, int count, int n, int m, const double* const* in, double* const* out, int generic,
+                cudaStream_t st) {
   const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
   const size_t S = 2 * (size_t)count;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) || sms < 1)
+    return TLQR_ERR_CUDA;
   std::vector<void*> mine;
   cudaError_t err = cudaSuccess;
   auto take = [&](size_t elems, size_t es) -> void* {
@@ -1357,72 +1773,85 @@ int batched_ops(int kind, int count, int n, int m, const double* const* in, doub
   w.N = count; w.n = n; w.m = m;
   T *U = (T*)take(S * nn, sizeof(T)), *Ea = (T*)take(S * nn, sizeof(T)), *Ec = (T*)take(S * nn, sizeof(T)),
     *Ep = (T*)take(S * nn, sizeof(T)), *contrib = (T*)take(count * nn, sizeof(T));
+  T *K = (T*)take(count * nm, sizeof(T)), *Tm = (T*)take(S * nn, sizeof(T)), *Tr = (T*)take(count * nn, sizeof(T)),
+    *W = (T*)take(count * nn, sizeof(T)), *Finv = (T*)take(count * nn, sizeof(T)),
+    *LG = (T*)take(count * mm, sizeof(T));
   int* idx = (int*)take(S, sizeof(int));
   int* status = (int*)take(1, sizeof(int));
-  double* tmp = (double*)take(S * nn, sizeof(double));
+  double* zeros = (double*)take(count * nn, sizeof(double));
+  unsigned char* flags = (unsigned char*)take(count, 1);
   if (err) { for (void* p : mine) cudaFree(p); return TLQR_ERR_OOM; }
   std::vector<int> hidx(S);
   for (size_t t = 0; t < S; ++t) hidx[t] = (int)t;
-  cudaMemcpyAsync(idx, hidx.data(), S * sizeof(int), cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(status, 0, sizeof(int), st);
+  cudaError_t e = cudaMemcpyAsync(idx, hidx.data(), S * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   w.U = U; w.Ea = Ea; w.Ec = Ec; w.Ep = Ep; w.contrib = contrib; w.status = status;
-  const WarpBytes wb = warp_bytes(n, m, sizeof(T));
-  auto conv_in = [&](T* dst, const double* src, size_t elems) {   // FP64 -> T via the load kernel path
-    if (sizeof(T) == 8) cudaMemcpyAsync(dst, src, elems * 8, cudaMemcpyDeviceToDevice, st);
-    else {
-      std::vector<double> h(elems);
-      std::vector<float> hf(elems);
-      cudaMemcpyAsync(h.data(), src, elems * 8, cudaMemcpyDeviceToHost, st);
-      cudaStreamSynchronize(st);
-      for (size_t e = 0; e < elems; ++e) hf[e] = (float)h[e];
-      cudaMemcpyAsync(dst, hf.data(), elems * 4, cudaMemcpyHostToDevice, st);
-      cudaStreamSynchronize(st);
-    }
-  };
-  auto conv_out = [&](double* dst, const T* src, size_t elems) {
-    if (sizeof(T) == 8) cudaMemcpyAsync(dst, src, elems * 8, cudaMemcpyDeviceToDevice, st);
-    else {
-      std::vector<float> hf(elems);
-      std::vector<double> h(elems);
-      cudaMemcpyAsync(hf.data(), src, elems * 4, cudaMemcpyDeviceToHost, st);
-      cudaStreamSynchronize(st);
-      for (size_t e = 0; e < elems; ++e) h[e] = hf[e];
-      cudaMemcpyAsync(dst, h.data(), elems * 8, cudaMemcpyHostToDevice, st);
-      cudaStreamSynchronize(st);
-    }
-  };
-  cudaError_t e = cudaSuccess;
-  if (kind == 0) {              // tau: in = A, C, P, U
-    conv_in(Ea, in[0], count * nn); conv_in(Ec, in[1], count * nn);
-    conv_in(Ep, in[2], count * nn); conv_in(U, in[3], count * nn);
-    w.rake_leaf = idx;
-    e = launch_warps(nullptr, TLQR_K_RAKE, k_rake<T>, count, wb.tau, st, w, 0, count, (int)wb.tau);
-    conv_out(out[0], contrib, count * nn);
-  } else if (kind == 1) {       // compose: in = Al Cl Pl Ar Cr Pr U
-    conv_in(Ea, in[0], count * nn); conv_in(Ec, in[1], count * nn); conv_in(Ep, in[2], count * nn);
-    conv_in(Ea + count * nn, in[3], count * nn); conv_in(Ec + count * nn, in[4], count * nn);
-    conv_in(Ep + count * nn, in[5], count * nn); conv_in(U, in[6], count * nn);
-    w.comp_j = idx; w.comp_k = idx + count;
-    e = launch_warps(nullptr, TLQR_K_COMPRESS, k_compress<T>, count, wb.compress, st, w, 0, count, (int)wb.compress);
-    conv_out(out[0], Ea + count * nn, count * nn); conv_out(out[1], Ec + count * nn, count * nn);
-    conv_out(out[2], Ep + count * nn, count * nn); conv_out(out[3], Ep, count * nn);
-  } else {                      // condense: in = A B R M Delta
-    w.A = in[0]; w.B = in[1]; w.R = in[2]; w.M = in[3]; w.Delta = in[4];
-    w.has_M = in[3] != nullptr; w.has_delta = in[4] != nullptr;
-    w.Q = tmp;  // U <- Q is part of the kernel; feed zeros
-    cudaMemsetAsync(tmp, 0, count * nn * sizeof(double), st);
-    unsigned char* flags = (unsigned char*)take(count, 1);
-    w.dflag = flags;
-    e = launch_warps(nullptr, TLQR_K_CONDENSE, k_condense<T>, count, wb.condense, st, w, (int)wb.condense);
-    conv_out(out[0], Ea, count * nn); conv_out(out[1], Ec, count * nn); conv_out(out[2], Ep, count * nn);
+  w.K = K; w.Tm = Tm; w.Tr = Tr; w.W = W; w.Finv = Finv; w.LG = LG;
+  auto in_ = [&](T* dst, const double* src, size_t elems) { if (!e) e = convert(dst, src, elems, sms, st); };
+  auto out_ = [&](double* dst, const T* src, size_t elems) { if (!e) e = convert(dst, src, elems, sms, st); };
+  const size_t L = (size_t)count * nn;
+  switch (kind) {
+    case B_TAU:                 // in = A, C, P, U; out = P + A^T U (I + C U)^{-1} A
+      in_(Ea, in[0], L); in_(Ec, in[1], L); in_(Ep, in[2], L); in_(U, in[3], L);
+      w.rake_leaf = idx;
+      if (!e) e = batched_dispatch<T>(kind, w, count, n, m, generic, st);
+      out_(out[0], contrib, L);
+      break;
+    case B_EXPAND:              // in = Ar, Cr, Pt (tape into slot t), Pk (slot count + t); out = P_j (slot t)
+      in_(Ea, in[0], L); in_(Ec, in[1], L); in_(Ep, in[2], L); in_(U + L, in[3], L);
+      w.comp_j = idx; w.comp_k = idx + count;
+      if (!e) e = batched_dispatch<T>(kind, w, count, n, m, generic, st);
+      out_(out[0], U, L);
+      break;
+    case B_COMPOSE:             // in = Al Cl Pl (slot t) Ar Cr Pr (slot count + t) U (slot t)
+      in_(Ea, in[0], L); in_(Ec, in[1], L); in_(Ep, in[2], L);
+      in_(Ea + L, in[3], L); in_(Ec + L, in[4], L); in_(Ep + L, in[5], L); in_(U, in[6], L);
+      w.comp_j = idx; w.comp_k = idx + count;
+      if (!e) e = batched_dispatch<T>(kind, w, count, n, m, generic, st);
+      out_(out[0], Ea + L, L); out_(out[1], Ec + L, L); out_(out[2], Ep + L, L); out_(out[3], Ep, L);
+      break;
+    case B_COMPOSE_T:           // in = T_k (slot count + t), T_j (slot t); out = T_k T_j
+      in_(Tm + L, in[0], L); in_(Tm, in[1], L);
+      w.comp_j = idx; w.comp_k = idx + count;
+      if (!e) e = batched_dispatch<T>(kind, w, count, n, m, generic, st);
+      out_(out[0], Tm + L, L);
+      break;
+    case B_CONDENSE:            // in = A B R M Delta (FP64, read directly); U <- Q = 0
+      w.A = in[0]; w.B = in[1]; w.R = in[2]; w.M = in[3]; w.Delta = in[4];
+      w.has_M = in[3] != nullptr; w.has_delta = in[4] != nullptr;
+      w.Q = zeros;
+      if (!e) e = cudaMemsetAsync(zeros, 0, L * sizeof(double), st);
+      w.dflag = flags;
+      if (!e) e = batched_dispatch<T>(kind, w, count, n, m, generic, st);
+      out_(out[0], Ea, L); out_(out[1], Ec, L); out_(out[2], Ep, L);
+      break;
+    case B_LOCAL_FACTOR:        // in = P, A B R M Delta; out = K [m x n], T = F^{-1} A_cl
+      in_(U, in[0], L);
+      w.A = in[1]; w.B = in[2]; w.R = in[3]; w.M = in[4]; w.Delta = in[5];
+      w.has_M = in[4] != nullptr; w.has_delta = in[5] != nullptr;
+      w.dflag = flags;
+      if (!e) e = cudaMemsetAsync(flags, w.has_delta ? 1 : 0, count, st);
+      if (!e) e = batched_dispatch<T>(kind, w, count, n, m, generic, st);
+      out_(out[0], K, (size_t)count * nm); out_(out[1], Tm, L);
+      break;
+    default:
+      e = cudaErrorInvalidValue;
   }
   int hs = 0;
   if (!e) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (!e) e = cudaStreamSynchronize(st);
   for (void* p : mine) cudaFree(p);
   if (e) return TLQR_ERR_CUDA;
-  (void)mm; (void)nm;
   return map_status(hs);
+}
+
+int batched(int kind, int count, int n, int m, const double* const* in, double* const* out, int32_t precision,
+            void* stream) {
+  const int generic = (precision >> 8) & 1;
+  const int prec = precision & 0xff;
+  if (prec != TLQR_PREC_FP64 && prec != TLQR_PREC_MIXED) return TLQR_ERR_ARG;
+  return prec == TLQR_PREC_FP64 ? batched_ops<double>(kind, count, n, m, in, out, generic, (cudaStream_t)stream)
+                                : batched_ops<float>(kind, count, n, m, in, out, generic, (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -1433,8 +1862,7 @@ extern "C" int tlqr_batched_tau(int32_t count, int32_t n, const double* A, const
   if (count < 1 || n < 1 || n > TLQR_MAX_DIM || !A || !C || !P || !U || !out) return TLQR_ERR_ARG;
   const double* in[4] = {A, C, P, U};
   double* o[1] = {out};
-  return precision == TLQR_PREC_FP64 ? batched_ops<double>(0, count, n, 1, in, o, (cudaStream_t)stream)
-                                     : batched_ops<float>(0, count, n, 1, in, o, (cudaStream_t)stream);
+  return batched(B_TAU, count, n, 1, in, o, precision, stream);
 }
 
 extern "C" int tlqr_batched_compose(int32_t count, int32_t n, const double* Al, const double* Cl,
@@ -1446,8 +1874,7 @@ extern "C" int tlqr_batched_compose(int32_t count, int32_t n, const double* Al, 
     return TLQR_ERR_ARG;
   const double* in[7] = {Al, Cl, Pl, Ar, Cr, Pr, U};
   double* o[4] = {An, Cn, Pn, Pt};
-  return precision == TLQR_PREC_FP64 ? batched_ops<double>(1, count, n, 1, in, o, (cudaStream_t)stream)
-                                     : batched_ops<float>(1, count, n, 1, in, o, (cudaStream_t)stream);
+  return batched(B_COMPOSE, count, n, 1, in, o, precision, stream);
 }
 
 extern "C" int tlqr_batched_condense(int32_t count, int32_t n, int32_t m, const double* A, const double* B,
@@ -1458,8 +1885,34 @@ extern "C" int tlqr_batched_condense(int32_t count, int32_t n, int32_t m, const 
     return TLQR_ERR_ARG;
   const double* in[5] = {A, B, R, M, Delta};
   double* o[3] = {Abar, Cbar, Pbar};
-  return precision == TLQR_PREC_FP64 ? batched_ops<double>(2, count, n, m, in, o, (cudaStream_t)stream)
-                                     : batched_ops<float>(2, count, n, m, in, o, (cudaStream_t)stream);
+  return batched(B_CONDENSE, count, n, m, in, o, precision, stream);
+}
+
+extern "C" int tlqr_batched_expand(int32_t count, int32_t n, const double* Ar, const double* Cr,
+                                   const double* Pt, const double* Pk, double* Pj, int32_t precision,
+                                   void* stream) {
+  if (count < 1 || n < 1 || n > TLQR_MAX_DIM || !Ar || !Cr || !Pt || !Pk || !Pj) return TLQR_ERR_ARG;
+  const double* in[4] = {Ar, Cr, Pt, Pk};
+  double* o[1] = {Pj};
+  return batched(B_EXPAND, count, n, 1, in, o, precision, stream);
+}
+
+extern "C" int tlqr_batched_local_factor(int32_t count, int32_t n, int32_t m, const double* P, const double* A,
+                                         const double* B, const double* R, const double* M, const double* Delta,
+                                         double* K, double* T, int32_t precision, void* stream) {
+  if (count < 1 || n < 1 || m < 1 || n > TLQR_MAX_DIM || m > TLQR_MAX_DIM || !P || !A || !B || !R || !K || !T)
+    return TLQR_ERR_ARG;
+  const double* in[6] = {P, A, B, R, M, Delta};
+  double* o[2] = {K, T};
+  return batched(B_LOCAL_FACTOR, count, n, m, in, o, precision, stream);
+}
+
+extern "C" int tlqr_batched_compose_T(int32_t count, int32_t n, const double* Tk, const double* Tj, double* out,
+                                      int32_t precision, void* stream) {
+  if (count < 1 || n < 1 || n > TLQR_MAX_DIM || !Tk || !Tj || !out) return TLQR_ERR_ARG;
+  const double* in[2] = {Tk, Tj};
+  double* o[1] = {out};
+  return batched(B_COMPOSE_T, count, n, 1, in, o, precision, stream);
 }
 
 extern "C" int tlqr_profile_mask(tlqr_factor_t* f, uint32_t mask) {

@@ -16,10 +16,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libtlqr.so")
 
 TLQR_OK = 0
+TLQR_ERR_ARG = 1
 TLQR_MEM_DEVICE, TLQR_MEM_HOST = 0, 1
 TLQR_PREC_FP64, TLQR_PREC_MIXED = 0, 1
 TLQR_OP_ROOT, TLQR_OP_RAKE, TLQR_OP_COMPRESS = 0, 1, 2
 TLQR_MAX_DIM = 64
+TLQR_BATCHED_GENERIC = 0x100
 STATUS_NAMES = {0: "TLQR_OK", 1: "TLQR_ERR_ARG", 2: "TLQR_ERR_TOPOLOGY", 3: "TLQR_ERR_NOT_PD",
                 4: "TLQR_ERR_SINGULAR", 5: "TLQR_ERR_NONFINITE", 6: "TLQR_ERR_OOM",
                 7: "TLQR_ERR_TIMEOUT", 8: "TLQR_ERR_NO_CONVERGENCE", 9: "TLQR_ERR_CUDA",
@@ -40,7 +42,8 @@ class TLQRError(RuntimeError):
 class tlqr_options(ctypes.Structure):
     _fields_ = [("n", _i32), ("m", _i32), ("precision", _i32), ("has_M", _i32), ("has_delta", _i32),
                 ("max_refine", _i32), ("refine_tol", ctypes.c_double), ("use_graphs", _i32),
-                ("generic_kernels", _i32), ("reserved", _i32 * 6)]
+                ("generic_kernels", _i32), ("async_ops", _i32), ("spin_limit", _i32), ("test_withhold", _i32),
+                ("reserved", _i32 * 3)]
 
 
 class tlqr_problem(ctypes.Structure):
@@ -50,6 +53,16 @@ class tlqr_problem(ctypes.Structure):
 
 class tlqr_solution(ctypes.Structure):
     _fields_ = [("mem", _i32), ("x", _dp), ("u", _dp), ("y", _dp), ("P", _dp), ("K", _dp)]
+
+
+class tlqr_ipm_options(ctypes.Structure):
+    _fields_ = [("max_iter", _i32), ("mu0", ctypes.c_double), ("sigma", ctypes.c_double), ("tau", ctypes.c_double),
+                ("tol", ctypes.c_double)]
+
+
+class tlqr_ipm_info(ctypes.Structure):
+    _fields_ = [("iterations", _i32), ("mu", ctypes.c_double), ("mean_gap", ctypes.c_double),
+                ("last_alpha", ctypes.c_double), ("last_eta", ctypes.c_double)]
 
 
 class tlqr_plan_stats_t(ctypes.Structure):
@@ -70,10 +83,13 @@ _lib = None
 EXPORTS = ["tlqr_plan_create", "tlqr_plan_create_forest", "tlqr_plan_destroy", "tlqr_plan_stats", "tlqr_plan_schedule",
            "tlqr_factor_create", "tlqr_factor_destroy", "tlqr_factor", "tlqr_solve_rhs", "tlqr_solve",
            "tlqr_get_PK", "tlqr_kkt_residual", "tlqr_last_info", "tlqr_status_string",
-           "tlqr_batched_tau", "tlqr_batched_compose", "tlqr_batched_condense",
+           "tlqr_batched_tau", "tlqr_batched_compose", "tlqr_batched_condense", "tlqr_batched_expand",
+           "tlqr_batched_local_factor", "tlqr_batched_compose_T",
            "tlqr_lift_node_controls", "tlqr_project_lifted", "tlqr_profile_mask", "tlqr_profile_read",
            "tlqr_kkt_residual_noalloc", "tlqr_profile_launches", "tlqr_tree_residuals",
-           "tlqr_factor_workspace_bytes", "tlqr_factor_bytes"]
+           "tlqr_factor_workspace_bytes", "tlqr_factor_bytes", "tlqr_async_schedule", "tlqr_solve_adjoint",
+           "tlqr_lift_node_controls_device", "tlqr_project_lifted_device", "tlqr_factor_dims", "tlqr_ipm_box",
+           "tlqr_pipe_peak"]
 
 KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
                 "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
@@ -111,6 +127,18 @@ def lib():
         L.tlqr_batched_tau.argtypes = [_i32, _i32] + [_dp] * 5 + [_i32, _vp]
         L.tlqr_batched_compose.argtypes = [_i32, _i32] + [_dp] * 11 + [_i32, _vp]
         L.tlqr_batched_condense.argtypes = [_i32, _i32, _i32] + [_dp] * 8 + [_i32, _vp]
+        L.tlqr_lift_node_controls_device.argtypes = ([_ip, _i32, _i32, _i32] + [_dp] * 9 + [_ip, _ip] + [_dp] * 9
+                                                     + [_ip, _vp])
+        L.tlqr_project_lifted_device.argtypes = [_i32, _i32, _i32, _ip] + [_dp] * 6 + [_vp]
+        L.tlqr_factor_dims.argtypes = [_vp, _ip]
+        L.tlqr_pipe_peak.argtypes = [_i32, _dp, _vp]
+        L.tlqr_ipm_box.argtypes = ([_vp, _vp, ctypes.POINTER(tlqr_problem), _dp, _dp, ctypes.POINTER(tlqr_ipm_options)]
+                                   + [_dp] * 5 + [ctypes.POINTER(tlqr_ipm_info), _vp])
+        L.tlqr_solve_adjoint.argtypes = [_vp, _i32] + [_dp] * 6 + [_vp]
+        L.tlqr_async_schedule.argtypes = [_vp, _i32, _i32] + [_ip] * 7
+        L.tlqr_batched_expand.argtypes = [_i32, _i32] + [_dp] * 5 + [_i32, _vp]
+        L.tlqr_batched_local_factor.argtypes = [_i32, _i32, _i32] + [_dp] * 8 + [_i32, _vp]
+        L.tlqr_batched_compose_T.argtypes = [_i32, _i32] + [_dp] * 3 + [_i32, _vp]
         L.tlqr_lift_node_controls.argtypes = [_ip, _i32, _i32, _i32] + [_dp] * 9 + [_ip, _ip] + [_dp] * 9 + [_ip]
         L.tlqr_project_lifted.argtypes = [_i32, _i32, _i32, _ip] + [_dp] * 6
         L.tlqr_profile_mask.argtypes = [_vp, ctypes.c_uint32]
@@ -220,9 +248,11 @@ def tlqr_plan_schedule(plan, N: int):
 # ------------------------------------------------------------------ factor / solve
 
 def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
-                 refine_tol=1e-8, use_graphs=True, generic_kernels=False) -> tlqr_options:
+                 refine_tol=1e-8, use_graphs=True, generic_kernels=False, async_ops=0, spin_limit=0,
+                 test_withhold=False) -> tlqr_options:
     o = tlqr_options()
     o.generic_kernels = int(bool(generic_kernels))
+    o.async_ops, o.spin_limit, o.test_withhold = int(async_ops), int(spin_limit), int(bool(test_withhold))
     o.n, o.m, o.precision = int(n), int(m), int(precision)
     o.has_M, o.has_delta = int(bool(has_M)), int(bool(has_delta))
     o.max_refine, o.refine_tol, o.use_graphs = int(max_refine), float(refine_tol), int(bool(use_graphs))
@@ -284,6 +314,39 @@ def tlqr_solve_rhs(f, q, r, c, x, u, y, stream=None) -> None:
                                 _stream(stream)), "tlqr_solve_rhs")
 
 
+def tlqr_solve_adjoint(f, xbar, ubar, ybar, qbar, rbar, cbar, stream=None) -> None:
+    """Gradient of a loss with respect to (q, r, c) from its gradient with respect to (x, u, y)."""
+    mem = _mem_all([xbar, ubar, ybar, qbar, rbar, cbar])
+    _check(lib().tlqr_solve_adjoint(f, mem, *[_ptr(a) for a in (xbar, ubar, ybar, qbar, rbar, cbar)],
+                                    _stream(stream)), "tlqr_solve_adjoint")
+
+
+def tlqr_pipe_peak(precision, stream=None) -> float:
+    """Measured FP32 (TLQR_PREC_MIXED) or FP64 FMA throughput of the device, TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(lib().tlqr_pipe_peak(int(precision), ctypes.byref(v), _stream(stream)), "tlqr_pipe_peak")
+    return v.value
+
+
+def tlqr_factor_dims(f):
+    d = np.zeros(3, dtype=np.int32)
+    _check(lib().tlqr_factor_dims(f, _iptr(d)), "tlqr_factor_dims")
+    return int(d[0]), int(d[1]), int(d[2])
+
+
+def tlqr_ipm_box(plan, f, data: dict, u_lo, u_hi, x, u, y, lam_lo, lam_hi, max_iter=0, mu0=0.0, sigma=0.0, tau=0.0,
+                 tol=0.0, stream=None) -> dict:
+    """Box-constrained tree LQR by the primal-dual interior-point driver (device arrays)."""
+    p = make_problem(data)
+    o = tlqr_ipm_options(int(max_iter), float(mu0), float(sigma), float(tau), float(tol))
+    info = tlqr_ipm_info()
+    _check(lib().tlqr_ipm_box(plan, f, ctypes.byref(p), _ptr(u_lo), _ptr(u_hi), ctypes.byref(o), _ptr(x), _ptr(u),
+                              _ptr(y), _ptr(lam_lo), _ptr(lam_hi), ctypes.byref(info), _stream(stream)),
+           "tlqr_ipm_box")
+    return dict(iterations=info.iterations, mu=info.mu, mean_gap=info.mean_gap, last_alpha=info.last_alpha,
+                last_eta=info.last_eta)
+
+
 def tlqr_get_PK(f, P, K, stream=None) -> None:
     mem = _mem_all([P, K])
     _check(lib().tlqr_get_PK(f, mem, _ptr(P), _ptr(K), _stream(stream)), "tlqr_get_PK")
@@ -299,8 +362,11 @@ def tlqr_kkt_residual(f, data: dict, x, u, y, stream=None):
 
 
 def tlqr_kkt_residual_noalloc(plan, n: int, m: int, data: dict, x, u, y, stream=None):
-    """FP64 KKT residual from a plan alone, with no device allocation (device arrays only)."""
+    """FP64 KKT residual from a plan alone, with no device allocation (device arrays only:
+    host arrays raise TLQRError with TLQR_ERR_ARG)."""
     p = make_problem(data)
+    if p.mem != TLQR_MEM_DEVICE or _mem_all([x, u, y]) != TLQR_MEM_DEVICE:
+        raise TLQRError(TLQR_ERR_ARG, "tlqr_kkt_residual_noalloc")
     st = np.zeros(2)
     _check(lib().tlqr_kkt_residual_noalloc(plan, int(n), int(m), ctypes.byref(p), _ptr(x), _ptr(u), _ptr(y),
                                            _ptr(st), _stream(stream)), "tlqr_kkt_residual_noalloc")
@@ -369,6 +435,44 @@ def tlqr_batched_condense(A, B, R, M, Delta, Abar, Cbar, Pbar, precision=TLQR_PR
                                        precision, _stream(stream)), "tlqr_batched_condense")
 
 
+def tlqr_batched_expand(Ar, Cr, Pt, Pk, Pj, precision=TLQR_PREC_FP64, stream=None) -> None:
+    count, n = Ar.shape[0], Ar.shape[1]
+    _check(lib().tlqr_batched_expand(count, n, *[_ptr(a) for a in (Ar, Cr, Pt, Pk, Pj)], precision,
+                                     _stream(stream)), "tlqr_batched_expand")
+
+
+def tlqr_batched_local_factor(P, A, B, R, M, Delta, K, T, precision=TLQR_PREC_FP64, stream=None) -> None:
+    count, n, m = B.shape
+    _check(lib().tlqr_batched_local_factor(count, n, m, *[_ptr(a) for a in (P, A, B, R, M, Delta, K, T)],
+                                           precision, _stream(stream)), "tlqr_batched_local_factor")
+
+
+def tlqr_batched_compose_T(Tk, Tj, out, precision=TLQR_PREC_FP64, stream=None) -> None:
+    count, n = Tk.shape[0], Tk.shape[1]
+    _check(lib().tlqr_batched_compose_T(count, n, _ptr(Tk), _ptr(Tj), _ptr(out), precision, _stream(stream)),
+           "tlqr_batched_compose_T")
+
+
+def tlqr_async_schedule(plan, n: int, async_ops: int = 0) -> dict:
+    """Operation list of the level-asynchronous factorisation tail (host only)."""
+    counts = np.zeros(4, dtype=np.int32)
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(_i32))
+    L = lib()
+    nul = ctypes.POINTER(_i32)()
+    _check(L.tlqr_async_schedule(plan, int(n), int(async_ops), ip(counts), nul, nul, nul, nul, nul, nul),
+           "tlqr_async_schedule")
+    P = int(counts[1])
+    out = dict(r0=int(counts[0]), n_ops=P, n_flags=int(counts[2]), levels=int(counts[3]))
+    arr = {k: np.zeros(max(1, P) * (3 if k.startswith("dep") else 1), dtype=np.int32)
+           for k in ("kind", "node", "round", "dep_flag", "dep_target", "signal")}
+    _check(L.tlqr_async_schedule(plan, int(n), int(async_ops), ip(counts), *[ip(arr[k]) for k in
+                                 ("kind", "node", "round", "dep_flag", "dep_target", "signal")]),
+           "tlqr_async_schedule")
+    for k, v in arr.items():
+        out[k] = v[:P * 3].reshape(P, 3) if k.startswith("dep") else v[:P]
+    return out
+
+
 # ------------------------------------------------------------------ lifting (host)
 
 def tlqr_lift_node_controls(parent, n: int, m: int, nd: dict) -> dict:
@@ -400,6 +504,45 @@ def tlqr_project_lifted(N: int, n: int, m: int, lmap, lx, lu, ly):
                                      _ptr(np.ascontiguousarray(lx)), _ptr(np.ascontiguousarray(lu)),
                                      _ptr(np.ascontiguousarray(ly)), _ptr(x), _ptr(v), _ptr(y)),
            "tlqr_project_lifted")
+    return x, v, y
+
+
+def tlqr_lift_node_controls_device(parent, n: int, m: int, nd: dict, stream=None) -> dict:
+    """Prop. 2 lifting of node-form data held in CUDA tensors; lifted blocks are
+    written on the device (torch tensors out), topology arrays are numpy."""
+    import torch
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    N = len(parent)
+    L = lib()
+    args = [_ptr(nd.get(k)) for k in ("Q", "q", "Mv", "Rv", "rv", "Av", "Bv", "c", "Delta")]
+    Nl = _i32(0)
+    _check(L.tlqr_lift_node_controls_device(_iptr(parent), N, n, m, *args, ctypes.byref(Nl), _ip(),
+                                            *([_dp()] * 9), _ip(), _stream(stream)),
+           "tlqr_lift_node_controls_device")
+    Nl = Nl.value
+    s = n + m
+    dev = nd["Q"].device
+    z = lambda *sh: torch.empty(sh, dtype=torch.float64, device=dev)
+    out = dict(parent=np.zeros(Nl, dtype=np.int32), Q=z(Nl, s, s), q=z(Nl, s), M=z(Nl, s, m), R=z(Nl, m, m),
+               r=z(Nl, m), A=z(Nl, s, s), B=z(Nl, s, m), c=z(Nl, s), Delta=z(Nl, s, s),
+               map=np.zeros(2 * N, dtype=np.int32))
+    nl = _i32(0)
+    _check(L.tlqr_lift_node_controls_device(_iptr(parent), N, n, m, *args, ctypes.byref(nl), _iptr(out["parent"]),
+                                            *[_ptr(out[k]) for k in ("Q", "q", "M", "R", "r", "A", "B", "c",
+                                                                     "Delta")],
+                                            _iptr(out["map"]), _stream(stream)), "tlqr_lift_node_controls_device")
+    return out
+
+
+def tlqr_project_lifted_device(N: int, n: int, m: int, lmap, lx, lu, ly, stream=None):
+    import torch
+    dev = lx.device
+    x = torch.empty((N, n), dtype=torch.float64, device=dev)
+    v = torch.empty((N, m), dtype=torch.float64, device=dev)
+    y = torch.empty((N, n), dtype=torch.float64, device=dev)
+    _check(lib().tlqr_project_lifted_device(N, n, m, _iptr(np.ascontiguousarray(lmap, dtype=np.int32)),
+                                            _ptr(lx), _ptr(lu), _ptr(ly), _ptr(x), _ptr(v), _ptr(y),
+                                            _stream(stream)), "tlqr_project_lifted_device")
     return x, v, y
 
 

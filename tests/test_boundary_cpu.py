@@ -148,3 +148,28 @@ def test_forest_planner_equals_schedule_oracle():
         tlqr.tlqr_plan_destroy(h)
     with pytest.raises(tlqr.TLQRError):
         tlqr.tlqr_plan_create(par)          # the single-tree entry point refuses several roots
+
+
+def test_noalloc_residual_refuses_host_arrays():
+    """The allocation-free residual takes device arrays only: host arrays are
+    refused with TLQR_ERR_ARG by the binding, and by the C entry point itself
+    when a caller flags host pointers as device memory (it asks CUDA what each
+    pointer is before any launch)."""
+    import ctypes
+    p = inputs.chain(16)
+    n, m = 3, 2
+    d = inputs.problem_data(p, n, m, inputs.rng_for(5))
+    x, u, y = np.zeros((16, n)), np.zeros((16, m)), np.zeros((16, n))
+    plan = tlqr.tlqr_plan_create(p)
+    try:
+        with pytest.raises(tlqr.TLQRError) as e:
+            tlqr.tlqr_kkt_residual_noalloc(plan, n, m, d, x, u, y)
+        assert e.value.code == tlqr.TLQR_ERR_ARG
+        prob = tlqr.make_problem(d)
+        prob.mem = tlqr.TLQR_MEM_DEVICE           # a false claim: these are host arrays
+        stats = np.zeros(2)
+        rc = tlqr.lib().tlqr_kkt_residual_noalloc(plan, n, m, ctypes.byref(prob), tlqr._ptr(x), tlqr._ptr(u),
+                                                  tlqr._ptr(y), tlqr._ptr(stats), None)
+        assert rc == tlqr.TLQR_ERR_ARG
+    finally:
+        tlqr.tlqr_plan_destroy(plan)

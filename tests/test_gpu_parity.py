@@ -119,6 +119,103 @@ def test_batched_condense(n, m, withM):
             assert np.abs(g.cpu().numpy()[t] - w).max() <= 1e-10 * max(1.0, np.abs(w).max())
 
 
+@pytest.mark.parametrize("n,m", [(4, 2), (12, 4), (16, 4), (32, 8), (5, 3)])
+@pytest.mark.parametrize("precision", [MIXED, MIXED | tlqr.TLQR_BATCHED_GENERIC])
+def test_batched_condense_mixed(n, m, precision):
+    """The condensation in FP32, through the compile-time-(n, m) kernel the
+    solver runs for these sizes and through the run-time-n kernel."""
+    rng = inputs.rng_for(310 + n * m)
+    count = 45
+    A = rng.standard_normal((count, n, n)); B = rng.standard_normal((count, n, m)) / np.sqrt(n)
+    H = rng.standard_normal((count, m, m)); R = np.eye(m) + H @ H.transpose(0, 2, 1) / m
+    M = 0.3 * rng.standard_normal((count, n, m))
+    Dg = rng.standard_normal((count, n, n)); D = 0.1 * Dg @ Dg.transpose(0, 2, 1) / n
+    outs = [dev(np.zeros((count, n, n))) for _ in range(3)]
+    tlqr.tlqr_batched_condense(dev(A), dev(B), dev(R), dev(M), dev(D), *outs, precision)
+    for t in range(count):
+        want = ops.condense(A[t], B[t], R[t], M[t], D[t])
+        for g, w in zip(outs, want):
+            assert np.abs(g.cpu().numpy()[t] - w).max() <= 2e-5 * max(1.0, np.abs(w).max())
+
+
+def _psd(rng, count, n, k=None, s=1.0):
+    G = rng.standard_normal((count, n, k or n))
+    return s * G @ G.transpose(0, 2, 1) / n
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 12, 16, 32])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_batched_expand(n, precision):
+    """eq. (value-reconstruction) through the expansion kernel against the oracle."""
+    rng = inputs.rng_for(500 + n)
+    count = 37
+    Ar = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    Cr = _psd(rng, count, n)
+    Pt = _psd(rng, count, n) + 0.5 * np.eye(n)
+    Pk = _psd(rng, count, n) + 0.2 * np.eye(n)
+    Pj = dev(np.zeros((count, n, n)))
+    tlqr.tlqr_batched_expand(dev(Ar), dev(Cr), dev(Pt), dev(Pk), Pj, precision)
+    ref = np.stack([ops.expand_compress((Ar[t], Cr[t], Pt[t]), Pk[t]) for t in range(count)])
+    tol = 1e-10 if precision == FP64 else 2e-4
+    assert np.abs(Pj.cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (4, 2), (6, 2), (12, 4), (16, 4), (32, 8), (5, 3)])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+@pytest.mark.parametrize("extras", ["none", "M_Delta"])
+def test_batched_local_factor(n, m, precision, extras):
+    """eq. (FW), (factor-local): K and T = F^{-1} A_cl against the oracle, with
+    and without M and Delta (the F = I + Delta P solve)."""
+    rng = inputs.rng_for(600 + 7 * n + m)
+    count = 41
+    P = _psd(rng, count, n) + np.eye(n)
+    A = 0.95 * rng.standard_normal((count, n, n)) / np.sqrt(n)
+    B = rng.standard_normal((count, n, m)) / np.sqrt(n)
+    H = rng.standard_normal((count, m, m)); R = np.eye(m) + H @ H.transpose(0, 2, 1) / m
+    M = 0.3 * rng.standard_normal((count, n, m)) if extras == "M_Delta" else None
+    D = _psd(rng, count, n, 2, 0.3) if extras == "M_Delta" else None
+    K, T = dev(np.zeros((count, m, n))), dev(np.zeros((count, n, n)))
+    tlqr.tlqr_batched_local_factor(dev(P), dev(A), dev(B), dev(R), dev(M), dev(D), K, T, precision)
+    tol = 1e-10 if precision == FP64 else 2e-4
+    Kg, Tg = K.cpu().numpy(), T.cpu().numpy()
+    for t in range(count):
+        lf = ops.local_factor(P[t], A[t], B[t], R[t], None if M is None else M[t], None if D is None else D[t])
+        assert np.abs(Kg[t] - lf["K"]).max() <= tol * max(1.0, np.abs(lf["K"]).max())
+        assert np.abs(Tg[t] - lf["T"]).max() <= tol * max(1.0, np.abs(lf["T"]).max())
+
+
+@pytest.mark.parametrize("n", [1, 4, 12, 16, 32])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_batched_compose_T(n, precision):
+    """eq. (transition-compose): T_k T_j by the composite-transition kernel."""
+    rng = inputs.rng_for(700 + n)
+    count = 37
+    Tk = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    Tj = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    out = dev(np.zeros((count, n, n)))
+    tlqr.tlqr_batched_compose_T(dev(Tk), dev(Tj), out, precision)
+    ref = np.stack([ops.transition_compose(Tk[t], np.zeros(n), Tj[t], np.zeros(n))[0] for t in range(count)])
+    tol = 1e-12 if precision == FP64 else 1e-5
+    assert np.abs(out.cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [4, 12, 16, 32])
+def test_batched_fixed_and_generic_kernels_agree(n):
+    """The compile-time-n group kernels (Gauss-Jordan solves, tensor-core
+    products at n = 32) and the run-time-n warp kernels (LU) give the same rake
+    fold and compression in FP32 up to rounding."""
+    rng = inputs.rng_for(800 + n)
+    count = 29
+    A = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    C, U, P = _psd(rng, count, n), _psd(rng, count, n) + 0.5 * np.eye(n), -_psd(rng, count, n, 1, 0.05)
+    outs = []
+    for prec in (MIXED, MIXED | tlqr.TLQR_BATCHED_GENERIC):
+        o = dev(np.zeros((count, n, n)))
+        tlqr.tlqr_batched_tau(dev(A), dev(C), dev(P), dev(U), o, prec)
+        outs.append(o.cpu().numpy())
+    assert np.abs(outs[0] - outs[1]).max() <= 2e-4 * np.abs(outs[1]).max()
+
+
 def test_batched_compose_associativity():
     """eq. (node-aware-associativity) evaluated by the GPU compress kernel."""
     rng = inputs.rng_for(401)
@@ -273,6 +370,40 @@ def test_lifted_node_controls_on_gpu():
     scale = max(np.abs(ref["x"]).max(), np.abs(ref["v"]).max(), np.abs(ref["y"]).max())
     for a, b in ((x, ref["x"]), (v, ref["v"]), (y, ref["y"])):
         assert np.abs(a - b).max() <= 1e-10 * scale
+
+
+@pytest.mark.parametrize("with_delta", [False, True])
+def test_lifted_node_controls_on_device(with_delta):
+    """Prop. 2 with the data on the GPU: device lifting equals the host lifting
+    entry for entry (pure copies), and device lifting -> GPU edge-form solve ->
+    device projection equals the dense node-control KKT solution."""
+    from oracle import dense
+    from tests.test_boundary_cpu import node_control_instance
+    rng = inputs.rng_for(83)
+    p, _ = inputs.permute_labels(inputs.random_recursive(80, rng), rng)
+    n, m = 3, 2
+    nd = node_control_instance(rng, p, n, m, with_delta)
+    host = tlqr.tlqr_lift_node_controls(p, n, m, nd)
+    devnd = {k: (None if v is None else dev(v)) for k, v in nd.items()}
+    L = tlqr.tlqr_lift_node_controls_device(p, n, m, devnd)
+    np.testing.assert_array_equal(L["parent"], host["parent"])
+    np.testing.assert_array_equal(L["map"], host["map"])
+    for k in ("Q", "q", "M", "R", "r", "A", "B", "c", "Delta"):
+        np.testing.assert_array_equal(L[k].cpu().numpy(), host[k])
+    Nl, s = len(L["parent"]), n + m
+    S = tlqr.TreeLQR(L["parent"], s, m, FP64, has_M=True, has_delta=True)
+    try:
+        x = torch.zeros((Nl, s), dtype=torch.float64, device="cuda")
+        u = torch.zeros((Nl, m), dtype=torch.float64, device="cuda")
+        y = torch.zeros((Nl, s), dtype=torch.float64, device="cuda")
+        tlqr.tlqr_solve(S.f, {k: L[k] for k in ("Q", "q", "M", "R", "r", "A", "B", "c", "Delta")}, x, u, y)
+    finally:
+        S.close()
+    xv, vv, yv = tlqr.tlqr_project_lifted_device(len(p), n, m, L["map"], x, u, y)
+    ref = dense.dense_solve_node_control(p, n, m, nd)
+    scale = max(np.abs(ref["x"]).max(), np.abs(ref["v"]).max(), np.abs(ref["y"]).max())
+    for a, b in ((xv, ref["x"]), (vv, ref["v"]), (yv, ref["y"])):
+        assert np.abs(a.cpu().numpy() - b).max() <= 1e-10 * scale
 
 
 def test_gpu_residual_matches_oracle_residual():
