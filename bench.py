@@ -75,7 +75,10 @@ def parse():
     ap.add_argument("--count", type=int, default=1024, help="batch: number of trees")
     ap.add_argument("--kappa", type=float, default=1e2, help="spine: condition number of R")
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests")
-    ap.add_argument("--requests", type=int, default=32, help="serve: requests per arrival rate")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per arrival rate")
+    ap.add_argument("--serve-mode", default="ipm", choices=["ipm", "perturb"],
+                    help="serve: each request is a box-constrained interior-point solve with a 20-Newton-solve "
+                         "budget (ipm), or 20 solves with randomly perturbed barrier-like diagonals (perturb)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--ref-seconds", type=float, default=180.0,
                     help="reference arm: CPU seconds for warm-up + timed steps together")
@@ -106,9 +109,10 @@ class ServeTraffic:
     (and the factor's captured graphs) stay the same across its solves."""
 
     def __init__(self, device, seed=inputs.BASE_SEED + 4, topologies=16, n=6, m=2, iterations=20,
-                 lo=500, hi=50000):
+                 lo=500, hi=50000, ipm=True):
         rng = inputs.rng_for(seed)
         self.device, self.seed, self.n, self.m, self.iterations = device, seed, n, m, iterations
+        self.ipm = ipm
         self.trees = [inputs.driving_tree(rng, int(rng.integers(lo, hi + 1))) for _ in range(topologies)]
         self.rng = rng
 
@@ -135,8 +139,24 @@ class ServeTraffic:
                 live["q"].normal_(generator=g)
                 live["r"].normal_(generator=g).mul_(nr[:, None])
             return live
-        return serve.Request(parent=parent, n=n, m=m, iterations=self.iterations, data=data, precision=precision,
-                             tag=(k, t))
+        if not self.ipm:
+            return serve.Request(parent=parent, n=n, m=m, iterations=self.iterations, data=data,
+                                 precision=precision, tag=(k, t))
+
+        # interior-point request: control bounds +-(0.3 + U[0, 1]) on every nonroot edge, solved by the
+        # primal-dual driver with a budget of `iterations` Newton solves (each a fresh tree KKT system)
+        def box(stream):
+            with torch.cuda.stream(stream):
+                lo = -(0.3 + torch.rand((N, m), generator=g, dtype=torch.float64, device=self.device))
+                hi = 0.3 + torch.rand((N, m), generator=g, dtype=torch.float64, device=self.device)
+                lo[~nr] = -float("inf")
+                hi[~nr] = float("inf")
+            return lo, hi
+
+        def first(it, stream):
+            return base
+        return serve.Request(parent=parent, n=n, m=m, iterations=self.iterations, data=first, precision=precision,
+                             tag=(k, t), bounds=box)
 
 
 def run_serve(args, rank, world, dist):
@@ -148,7 +168,7 @@ def run_serve(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = tlqr.TLQR_PREC_MIXED if args.mode == "mixed" else tlqr.TLQR_PREC_FP64
-    traffic = ServeTraffic(dev)
+    traffic = ServeTraffic(dev, ipm=args.serve_mode == "ipm")
     slots = args.slots
     srv = serve.Server(slots=slots)
     k = 0
@@ -169,7 +189,16 @@ def run_serve(args, rank, world, dist):
     srv.drain()
     span = time.perf_counter() - t0
     errors = [repr(r.error) for r in warm + burst if r.error is not None]
-    nodes = sum(r.N * r.iterations for r in burst)
+
+    def solves(r):                              # Newton solves a request ran (IPM requests may stop early)
+        if r.bounds is None:
+            return r.iterations
+        return sum(i.get("iterations", r.iterations) for i in r.infos)
+
+    def eta_of(i):
+        return i.get("eta", i.get("last_eta"))
+
+    nodes = sum(r.N * solves(r) for r in burst)
     capacity_rps = len(burst) / span
     value = nodes / span
     rates = []
@@ -192,8 +221,12 @@ def run_serve(args, rank, world, dist):
         errors += [repr(r.error) for r in reqs if r.error is not None]
         summ = serve.latency_summary(reqs)
         summ.update({"rate_factor": fct, "rate_rps": lam,
-                     "throughput_nodes_s": sum(r.N * r.iterations for r in reqs) / (t_end - t_start),
-                     "max_eta": max((i["eta"] for r in reqs for i in r.infos), default=None)})
+                     "throughput_nodes_s": sum(r.N * solves(r) for r in reqs) / (t_end - t_start),
+                     "max_eta": max((eta_of(i) for r in reqs for i in r.infos if eta_of(i) is not None),
+                                    default=None),
+                     "ipm_iterations_p50": float(np.median([i.get("iterations", traffic.iterations)
+                                                            for r in reqs for i in r.infos]))
+                     if traffic.ipm else None})
         rates.append(summ)
     stats = dict(srv.stats)
     peak = srv.peak
@@ -208,7 +241,9 @@ def run_serve(args, rank, world, dist):
         "config": {"workload": "serve_driving_trees_n6_m2", "description": WORKLOADS["serve"], "slots": slots,
                    "requests_per_rate": args.requests, "iterations_per_request": traffic.iterations,
                    "topologies": len(traffic.trees), "precision": args.mode,
-                   "step": "one request (20 solves, each factor + solve + refinement to eta <= 1e-8)"},
+                   "step": ("one request: a box-constrained problem solved by the interior-point driver with "
+                            "a budget of 20 Newton solves (each factor + solve + refinement)") if traffic.ipm else
+                           "one request (20 solves, each factor + solve + refinement to eta <= 1e-8)"},
         "capacity_rps": capacity_rps, "burst_latency": serve.latency_summary(burst),
         "serving": rates, "server_stats": stats, "peak_admitted_bytes": peak, "errors": errors[:5],
     }
@@ -680,7 +715,10 @@ def run_ours(args, rank, world, dist):
         tlqr.tlqr_profile_mask(solver.f, ())
         return ts, tlqr.tlqr_profile_read(solver.f)
 
-    solver = tlqr.TreeLQR(w.parent, n, m, prec, has_delta=has_delta, forest=forest)
+    # execution shape chosen by the autotuner for this workload (committed table), mixed precision only
+    from paper_2608_01332_b300 import autotune
+    tuned = autotune.tuned_options(args.workload) if mixed and args.total is None else {}
+    solver = tlqr.TreeLQR(w.parent, n, m, prec, has_delta=has_delta, forest=forest, **tuned)
     stats = solver.stats()
 
     def solve():
@@ -690,9 +728,15 @@ def run_ours(args, rank, world, dist):
     for _ in range(max(3, args.warmup)):
         solve()
     _, prof_all = timed(solver, 1, solve, tlqr.KERNEL_KINDS)
-    dominant = max(prof_all, key=lambda k: prof_all[k]["ms"])
+    # the dominant kernel among those with an algorithmic work model (per_unit)
+    modeled = [k for k in prof_all if per_unit(k, n, m, 4 if mixed else 8)[0] is not None]
+    dominant = max(modeled, key=lambda k: prof_all[k]["ms"])
     with ClockSampler(local) as clk:
-        ts, prof = timed(solver, args.steps, solve, (dominant,))
+        # the headline: K steps with no event inside the step; then the same K
+        # steps again with CUDA events around each launch of the dominant kernel,
+        # for its roofline (events in the launch graph lengthen the step)
+        ts, prof_plain = timed(solver, args.steps, solve, ())
+        ts_k, prof = timed(solver, args.steps, solve, (dominant,))
     info = tlqr.tlqr_last_info(solver.f)
     tot_ms = sum(ts)
     if dist is not None:
@@ -701,7 +745,7 @@ def run_ours(args, rank, world, dist):
         tot_ms = float(t.item())
     ms_per_step = tot_ms / args.steps
     value = world * N / (ms_per_step / 1e3)
-    gpu_launches = int(sum(p["launches"] for p in prof.values()))
+    gpu_launches = int(sum(p["launches"] for p in prof_plain.values()))
     # accuracy of the last timed solution (per tree for a batch)
     res = tlqr.tlqr_kkt_residual(solver.f, dd, x, u, y)
     tree_eta = tlqr.tlqr_tree_residuals(solver.f, stats["n_trees"])[1]
@@ -724,6 +768,26 @@ def run_ours(args, rank, world, dist):
                                                                   stream=stream))
     split = {"factor_ms": float(np.median(ts_f)), "solve_rhs_ms": float(np.median(ts_s)),
              "note": "medians; solve_rhs = one pass through the factors without refinement"}
+    # several right-hand sides with one factor: a panel of 8 against 8 separate passes
+    multi = None
+    if N <= 200_000:
+        K = 8
+        qk = dd["q"].unsqueeze(0).repeat(K, 1, 1).contiguous()
+        rk = dd["r"].unsqueeze(0).repeat(K, 1, 1).contiguous()
+        ck = dd["c"].unsqueeze(0).repeat(K, 1, 1).contiguous()
+        qk += torch.randn_like(qk); ck += torch.randn_like(ck)
+        xk, uk, yk = torch.empty_like(qk), torch.empty_like(rk), torch.empty_like(qk)
+        ts_p, _ = timed(solver, K_split, lambda: tlqr.tlqr_solve_rhs_panel(solver.f, qk, rk, ck, xk, uk, yk,
+                                                                          stream=stream))
+
+        def one_by_one():
+            for k in range(K):
+                tlqr.tlqr_solve_rhs(solver.f, qk[k], rk[k], ck[k], xk[k], uk[k], yk[k], stream=stream)
+        ts_o, _ = timed(solver, K_split, one_by_one)
+        multi = {"nrhs": K, "panel_ms": float(np.median(ts_p)), "one_by_one_ms": float(np.median(ts_o)),
+                 "speedup": float(np.median(ts_o) / np.median(ts_p)),
+                 "note": "one pass through the factors per right-hand side (no refinement), medians"}
+        del qk, rk, ck, xk, uk, yk
 
     # per-round roofline of the factorisation (one profiled step, launches timed one by one)
     wbytes = 4 if mixed else 8
@@ -796,7 +860,10 @@ def run_ours(args, rank, world, dist):
             roof = {"bound": "alu", "achieved": flops / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                     "frac": flops / peak_alu, "traffic": None, "peak_source": peak_alu_src}
         roof.update({"kernel": f"k_{dominant}", "launches": pd["timed"], "units": pd["units"],
-                     "avg_launch_ms": pd["ms"] / pd["timed"], "flops_per_unit": fl, "bytes_per_unit": by})
+                     "avg_launch_ms": pd["ms"] / pd["timed"], "flops_per_unit": fl, "bytes_per_unit": by,
+                     "timing": "CUDA events around each launch of the kernel on its stream, over a second timed "
+                               "pass of the same K steps (the headline steps run without events)",
+                     "instrumented_ms_per_step": sum(ts_k) / len(ts_k)})
         bpo = NCU_BYTES_PER_OP.get((dominant, n, m, args.mode))
         if bpo is not None:
             roof["traffic"] = bpo * pd["units"] / pd["timed"]
@@ -804,6 +871,7 @@ def run_ours(args, rank, world, dist):
                                     "operations per launch (bytes per launch)")
 
     cfg = {"workload": w.name, "N": N, "n": n, "m": m, "precision": args.mode, "rounds": stats["rounds"],
+           "execution": tuned or "library defaults",
            "height": stats["height"], "trees": stats["n_trees"], "description": WORKLOADS[args.workload],
            "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"}
     if args.workload == "spine":
@@ -819,6 +887,7 @@ def run_ours(args, rank, world, dist):
         "eta": res["eta"], "refine_steps": info["refine_steps"] if mixed else 0,
         "tree_eta": {"max": float(tree_eta.max()), "p50": float(np.percentile(tree_eta, 50))} if forest else None,
         "factor_solve": split,
+        "multi_rhs": multi,
         "plain_fp64": fp64,
         "e2e": e2e,
         "gpu_launches": gpu_launches,

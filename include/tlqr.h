@@ -102,7 +102,17 @@ typedef struct {
   int32_t test_withhold; /* testing failure detection only: 1 = the first operation of
                             the level-asynchronous launch never signals completion, so
                             the waits that depend on it run out (TLQR_ERR_TIMEOUT)    */
-  int32_t reserved[3];
+  int32_t tail_ops;      /* right-hand-side passes: the rounds from the first one after
+                            which every phase holds at most this many operations run in
+                            one single-block launch per pass (0 = default 128, < 0 =
+                            none; compile-time-n kernels only)                      */
+  int32_t async_solve;   /* right-hand-side passes (compile-time-n kernels): 1 = every
+                            round of the affine pass in one level-asynchronous launch
+                            and every round of the state pass in another (the
+                            dependency DAG of eq. (earliest-level) applied to the
+                            passes of Sec. VI-VII); 0 (default) or < 0 = round by
+                            round with the single-block tail of tail_ops            */
+  int32_t reserved[1];
 } tlqr_options;
 
 #define TLQR_MAX_DIM 64
@@ -193,21 +203,28 @@ int tlqr_factor_create(const tlqr_plan_t *plan, const tlqr_options *opts, tlqr_f
  * staging area of the problem's size. */
 int tlqr_factor_workspace_bytes(const tlqr_plan_t *plan, const tlqr_options *opts, size_t *bytes);
 
-/* The operation list of the level-asynchronous factorisation tail that a
- * factor object with state dimension n and tlqr_options.async_ops = async_ops
- * would run for this plan (host only, for inspection and testing).  counts[4]
- * receives the first asynchronous round (0-based; = rounds when there is
- * none), the padded operation count P, the flag count and the number of
+/* An operation list of the level-asynchronous launches that a factor object
+ * with state dimension n would run for this plan (host only, for inspection
+ * and testing): which = 0 the factorisation tail for tlqr_options.async_ops =
+ * async_ops, 1 the affine pass of a right-hand side, 2 its state pass.
+ * counts[4] receives the first asynchronous round (0-based; = rounds when there
+ * is none), the padded operation count P, the flag count and the number of
  * dependency levels.  When `kind` is non-NULL the host arrays receive, per
- * position p < P: kind[p] (0 rake, 1 absorption, 2 compression, 3 expansion),
+ * position p < P: kind[p] (0 rake, 1 absorption, 2 compression, 3 expansion
+ * -- their affine-pass counterparts for which = 1 -- and for which = 2: 4 offset
+ * composition, 5 state expansion of a compressed centre, 6 of a raked leaf),
  * node[p] (raked leaf, absorbing parent or compressed centre; -1 for a padding
  * slot), round[p] (1-based structural round), dep_flag[3p..3p+2] (flag
  * indices, -1 = none), dep_target[3p..3p+2] (the value each flag must reach;
  * flag q < P is the completion flag of position q, flags >= P count the
  * finished rakes of one sibling segment) and signal[p] (the counter a rake
  * increments, else -1).  Errors: TLQR_ERR_ARG, TLQR_ERR_OOM. */
-int tlqr_async_schedule(const tlqr_plan_t *plan, int32_t n, int32_t async_ops, int32_t *counts, int32_t *kind,
-                        int32_t *node, int32_t *round, int32_t *dep_flag, int32_t *dep_target, int32_t *signal);
+int tlqr_async_schedule(const tlqr_plan_t *plan, int32_t n, int32_t which, int32_t async_ops, int32_t *counts,
+                        int32_t *kind, int32_t *node, int32_t *round, int32_t *dep_flag, int32_t *dep_target,
+                        int32_t *signal);
+
+/* The options a factor object was created with (defaults filled in). */
+int tlqr_factor_options(const tlqr_factor_t *f, tlqr_options *out);
 
 /* dims[3] = {N, n, m} of a factor object (host array). */
 int tlqr_factor_dims(const tlqr_factor_t *f, int32_t *dims);
@@ -240,6 +257,19 @@ int tlqr_factor(tlqr_factor_t *f, const tlqr_problem *prob, void *stream);
  * (refinement needs the problem's matrices: use tlqr_solve). */
 int tlqr_solve_rhs(tlqr_factor_t *f, int32_t mem, const double *q, const double *r, const double *c,
                    double *x, double *u, double *y, void *stream);
+
+/* Several right-hand sides with the stored factorisation (factor reuse across
+ * Newton right-hand sides, Sec. VI): q [nrhs][N][n], r [nrhs][N][m], c
+ * [nrhs][N][n] in, x, u, y of the same shapes out, all device pointers.  With
+ * the compile-time-(n, m) kernels the right-hand sides run as panels of up to
+ * 8: every local operation loads its factor block once and applies it to the
+ * whole panel (an n x n block times an n x k panel instead of k matrix-vector
+ * products), in the launches of one right-hand side.  Otherwise they are solved
+ * one by one.  Each result equals tlqr_solve_rhs of that right-hand side alone (one
+ * pass through the factors, no refinement); the first panel call allocates the
+ * panel vectors once.  Synchronises `stream` to report a status. */
+int tlqr_solve_rhs_panel(tlqr_factor_t *f, int32_t nrhs, const double *q, const double *r, const double *c,
+                         double *x, double *u, double *y, void *stream);
 
 /* One-shot solve = tlqr_factor + tlqr_solve_rhs, and in MIXED precision the
  * iterative refinement: the FP64 KKT residual of eq. (kkt) is re-solved through
@@ -323,8 +353,10 @@ int tlqr_last_info(const tlqr_factor_t *f, tlqr_info *out);
 
 /* ------------------------------------------------------------- profiling */
 /* Kernel kinds launched by the library (one per step of Alg. 1 above).
- * TLQR_K_AFF_TAIL / TLQR_K_STATE_TAIL: the single-block kernels that run the
- * late rounds of the affine and state passes; TLQR_K_FACTOR_TAIL: the
+ * TLQR_K_AFF_TAIL / TLQR_K_STATE_TAIL: the launches that run several rounds
+ * of the affine and state passes at once (the single-block kernels of the late
+ * rounds, or with async_solve = 1 one level-asynchronous launch per pass);
+ * TLQR_K_FACTOR_TAIL: the
  * persistent level-asynchronous launch of the late factorisation rounds (see
  * tlqr_options.async_ops; its units are the operations of its list). */
 enum {
@@ -478,7 +510,13 @@ int tlqr_project_lifted_device(int32_t N, int32_t n, int32_t m, const int32_t *m
  * R~ = R + diag(S), r~ = r - S u - mu / s_lo + mu / s_hi, S = l_lo / s_lo +
  * l_hi / s_hi (tlqr_solve on `f`, in its precision), steps to the fraction tau
  * of the boundary and sets mu = sigma * mean(l s); it stops after a full Newton
- * step once mean(l s) <= tol.  Device arrays: prob (mem must be
+ * step once mean(l s) <= tol.  With a MIXED factor object the Newton systems
+ * are solved in FP32 + refinement until the barrier terms l / s exceed 1e6
+ * (they grow like 1 / mu; past that the FP32 factors stop resolving the step on
+ * the active bounds, although each solve still meets its normwise tolerance)
+ * or a solve fails, and from then on with an FP64 factor object of the same
+ * plan, created on first need and freed on return.  Device arrays: prob (mem
+ * must be
  * TLQR_MEM_DEVICE), u_lo, u_hi [N][m]; outputs x, u, y [N][n|m|n] and the
  * multipliers lam_lo, lam_hi [N][m] (zero where a bound is absent).  f must be
  * a factor object of `plan`.  The call allocates one device workspace for its
@@ -491,6 +529,10 @@ typedef struct {
   double sigma;          /* centring factor in (0, 1), default 0.1 */
   double tau;            /* fraction to the boundary in (0, 1), default 0.995 */
   double tol;            /* target mean complementarity, default 1e-9 */
+  int32_t no_fp64_fallback; /* 1: never allocate the FP64 factor object; a MIXED Newton
+                               solve whose refinement stalls is used as it stands
+                               (an inexact Newton step) -- for callers that budget
+                               device memory per request */
 } tlqr_ipm_options;
 
 typedef struct {
@@ -498,11 +540,36 @@ typedef struct {
   double mu, mean_gap;   /* last barrier parameter and mean l s */
   double last_alpha;     /* step length of the last iteration */
   double last_eta;       /* backward error of the last Newton solve (MIXED) */
+  int32_t fp64_solves;   /* Newton systems re-solved in FP64 (MIXED factor objects) */
 } tlqr_ipm_info;
 
 int tlqr_ipm_box(const tlqr_plan_t *plan, tlqr_factor_t *f, const tlqr_problem *prob, const double *u_lo,
                  const double *u_hi, const tlqr_ipm_options *opts, double *x, double *u, double *y,
                  double *lam_lo, double *lam_hi, tlqr_ipm_info *info, void *stream);
+
+/* ------------------------------------------------------------- autotuner */
+/* Pick the execution shape for one plan and problem by timing it on the
+ * current device: every combination of async_ops in {-1 (off), 256, 1024,
+ * 4096} with the right-hand-side passes level-asynchronous (async_solve = 1)
+ * or round by round with a single-block tail of tail_ops in {-1 (none), 64,
+ * 128, 512}.  Each
+ * candidate gets a factor object of its own (created and freed in turn, so
+ * only one workspace is held at a time), one warm-up tlqr_solve and `trials`
+ * timed ones (CUDA events on `stream`, median).  *best receives `base` with the
+ * fastest candidate's three fields; table (may be NULL) up to max_entries
+ * rows, *n_entries the number written.  prob: device data (mem must be
+ * TLQR_MEM_DEVICE).  The call allocates x, u, y for the trials.  Errors:
+ * TLQR_ERR_ARG, TLQR_ERR_OOM, TLQR_ERR_NO_CONVERGENCE (no candidate finished),
+ * and the first hard error of a candidate. */
+typedef struct {
+  int32_t async_ops, async_solve, tail_ops;
+  int32_t status;        /* TLQR_OK or the candidate's error */
+  double ms;             /* median time of one tlqr_solve, -1 when it failed */
+} tlqr_autotune_entry;
+
+int tlqr_autotune(const tlqr_plan_t *plan, const tlqr_options *base, const tlqr_problem *prob, int32_t trials,
+                  tlqr_options *best, tlqr_autotune_entry *table, int32_t max_entries, int32_t *n_entries,
+                  void *stream);
 
 #ifdef __cplusplus
 }

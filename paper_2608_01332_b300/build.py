@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtlqr.so")
-SOURCES = ["tlqr.cu", "planner.cpp", "lifting.cpp", "lifting_device.cu", "noalloc.cu", "ipm.cu", "peaks.cu"]
+SOURCES = ["tlqr.cu", "planner.cpp", "lifting.cpp", "lifting_device.cu", "noalloc.cu", "ipm.cu", "peaks.cu", "autotune.cpp"]
 HEADERS = ["kernels.cuh", "fixed.cuh", "smallmat.cuh", "residual.cuh", "residual_nodes.cuh", "mma32.cuh", "plan.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -601,6 +601,8 @@ __global__ void kf_compress(Ws<T> w, int begin, int count) {
 // leave, and returns -- the context stays usable and the host reports
 // TLQR_ERR_TIMEOUT.
 enum : int { AK_RAKE = 0, AK_ABSORB = 1, AK_COMPRESS = 2, AK_EXPAND = 3 };
+// kinds of the state pass (kf_async_vec); the affine pass reuses the four above
+enum : int { SK_COMPOSE = 4, SK_EXPAND_C = 5, SK_EXPAND_R = 6 };
 constexpr int kAsyncPad = 0x0fffffff;       // index field of a padding slot
 
 struct AsyncArgs {
@@ -633,6 +635,45 @@ __device__ __forceinline__ int ld_volatile(const int* p) {
   return v;
 }
 
+// Wait until the operation at `pos` may start: every lane polls every one of
+// its dependency flags with ld.acquire.gpu itself.  Returns true (uniformly in
+// the warp) when a wait ran out or another warp gave up: the caller returns.
+__device__ __forceinline__ bool async_wait(const AsyncArgs& a, int pos, int* status) {
+  bool gave_up = false;
+#pragma unroll 1
+  for (int d = 0; d < 3 && !gave_up; ++d) {
+    const int f = a.dep_flag[3 * pos + d];
+    if (f < 0) continue;
+    const int target = a.dep_target[3 * pos + d];
+    int polls = 0;
+    while (ld_acquire_gpu(a.flags + f) < target) {
+      if (++polls > a.spin_limit || ld_volatile(a.abort)) { gave_up = true; break; }
+      if (polls > 16) __nanosleep(polls < 128 ? 32 : 256);
+    }
+  }
+  if (__any_sync(TLQR_FULL_MASK, gave_up)) {
+    if ((threadIdx.x & 31) == 0) {
+      atomicCAS(status, 0, ST_TIMEOUT);
+      atomicExch(a.abort, 1);
+    }
+    return true;
+  }
+  return false;
+}
+
+// Publish the completion of the operation at `pos`: every lane's writes are
+// fenced, then the group's first lane releases the flag (and a rake adds to
+// its segment's counter).
+__device__ __forceinline__ void async_publish(const AsyncArgs& a, int pos, bool valid, int gl) {
+  __threadfence();
+  __syncwarp();
+  if (valid && gl == 0 && pos != a.withhold) {
+    st_release_gpu(a.flags + pos, 1);
+    const int sig = a.signal[pos];
+    if (sig >= 0) red_release_add_gpu(a.flags + sig, 1);
+  }
+}
+
 template <typename T, int N>
 struct AsyncSmem {
   static constexpr int bytes = TauSmem<T, N>::bytes > CompSmem<T, N>::bytes ? TauSmem<T, N>::bytes
@@ -657,26 +698,7 @@ __global__ void kf_async(Ws<T> w, AsyncArgs a) {
     const int kind = word >> 28;                       // one kind per warp (host padding)
     int idx = word & kAsyncPad;
     const bool valid = idx != kAsyncPad;
-    // wait for the operation's inputs: every lane acquires every flag itself
-    bool gave_up = false;
-#pragma unroll 1
-    for (int d = 0; d < 3 && !gave_up; ++d) {
-      const int f = a.dep_flag[3 * pos + d];
-      if (f < 0) continue;
-      const int target = a.dep_target[3 * pos + d];
-      int polls = 0;
-      while (ld_acquire_gpu(a.flags + f) < target) {
-        if (++polls > a.spin_limit || ld_volatile(a.abort)) { gave_up = true; break; }
-        __nanosleep(polls < 64 ? 32 : 256);
-      }
-    }
-    if (__any_sync(TLQR_FULL_MASK, gave_up)) {
-      if (lane == 0) {
-        atomicCAS(w.status, 0, ST_TIMEOUT);
-        atomicExch(a.abort, 1);
-      }
-      return;
-    }
+    if (async_wait(a, pos, w.status)) return;
     // a padding group repeats the warp's first operation and stores nothing
     const int idx0 = __shfl_sync(TLQR_FULL_MASK, idx, 0);
     if (!valid) idx = idx0;
@@ -703,16 +725,10 @@ __global__ void kf_async(Ws<T> w, AsyncArgs a) {
       ok = tau_group<T, N>(g, w.U + (size_t)k * NN, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm);
     }
     if (!ok && valid && gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
-    // publish: every lane's writes, then the release by the group's first lane
-    __threadfence();
-    __syncwarp();
-    if (valid && gl == 0 && pos != a.withhold) {
-      st_release_gpu(a.flags + pos, 1);
-      const int sig = a.signal[pos];
-      if (sig >= 0) red_release_add_gpu(a.flags + sig, 1);
-    }
+    async_publish(a, pos, valid, gl);
   }
 }
+
 
 // ---------------------------------------------------------------- composite transitions
 // Tr_j <- T_k ; T_k <- T_k T_j  (eq. transition-compose), one group per compression.
@@ -765,42 +781,59 @@ __device__ __forceinline__ void vec_load(T (&v)[N], const T* src) {
   for (int c = 0; c < N; ++c) v[c] = src[c];
 }
 
-// contribution cv_rr = T_j^T h_j + z_j  (eq. affine-rake)
+// contribution cv_rr = T_j^T h_j + z_j  (eq. affine-rake).  Every vector op
+// below loads its block row or column once and applies it to the w.nrhs
+// right-hand sides of a panel.
 template <typename T, int N>
 __device__ __forceinline__ void aff_rake_op(const Ws<T>& w, int rr, bool valid, int gl) {
   const int j = w.rake_leaf[rr], r = gl < N ? gl : 0;
   const T* Tj = w.Tm + (size_t)j * N * N;
-  T h[N];
-  vec_load(h, w.h + (size_t)j * N);
-  T s = w.z[(size_t)j * N + r];
+  T col[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) s = fma(Tj[t * N + r], h[t], s);
-  if (valid && gl < N) w.cv[(size_t)rr * N + r] = s;
+  for (int t = 0; t < N; ++t) col[t] = Tj[t * N + r];
+  for (int k = 0; k < w.nrhs; ++k) {
+    const Ws<T> v = w.rhs(k);
+    T h[N];
+    vec_load(h, v.h + (size_t)j * N);
+    T s = v.z[(size_t)j * N + r];
+#pragma unroll
+    for (int t = 0; t < N; ++t) s = fma(col[t], h[t], s);
+    if (valid && gl < N) v.cv[(size_t)rr * N + r] = s;
+  }
 }
 // h_i += sum of the segment's contributions, in sibling order
 template <typename T, int N>
 __device__ __forceinline__ void aff_absorb_op(const Ws<T>& w, int sidx, bool valid, int gl) {
   const int i = w.seg_parent[sidx], b = w.seg_start[sidx], e = w.seg_start[sidx + 1], r = gl < N ? gl : 0;
-  T acc = w.cv[(size_t)b * N + r];
-  for (int t = b + 1; t < e; ++t) acc += w.cv[(size_t)t * N + r];
-  if (valid && gl < N) w.h[(size_t)i * N + r] += acc;
+  for (int k = 0; k < w.nrhs; ++k) {
+    const Ws<T> v = w.rhs(k);
+    T acc = v.cv[(size_t)b * N + r];
+    for (int t = b + 1; t < e; ++t) acc += v.cv[(size_t)t * N + r];
+    if (valid && gl < N) v.h[(size_t)i * N + r] += acc;
+  }
 }
 // s_j = h_j + z_k ; z_k <- z_j + T_j^T s_j  (eq. affine-compose)
 template <typename T, int N>
 __device__ __forceinline__ void aff_compress_op(const Ws<T>& w, int rr, bool valid, int gl) {
   const int j = w.comp_j[rr], k = w.comp_k[rr], r = gl < N ? gl : 0;
   const T* Tj = w.Tm + (size_t)j * N * N;
-  T sv[N];
+  T col[N];
 #pragma unroll
-  for (int c = 0; c < N; ++c) sv[c] = w.h[(size_t)j * N + c] + w.z[(size_t)k * N + c];
-  T acc = w.z[(size_t)j * N + r];
+  for (int t = 0; t < N; ++t) col[t] = Tj[t * N + r];
+  for (int q = 0; q < w.nrhs; ++q) {
+    const Ws<T> v = w.rhs(q);
+    T sv[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) acc = fma(Tj[t * N + r], sv[t], acc);
-  const T sr = w.h[(size_t)j * N + r] + w.z[(size_t)k * N + r];
-  __syncwarp();
-  if (valid && gl < N) {
-    w.s[(size_t)j * N + r] = sr;
-    w.z[(size_t)k * N + r] = acc;
+    for (int c = 0; c < N; ++c) sv[c] = v.h[(size_t)j * N + c] + v.z[(size_t)k * N + c];
+    T acc = v.z[(size_t)j * N + r];
+#pragma unroll
+    for (int t = 0; t < N; ++t) acc = fma(col[t], sv[t], acc);
+    const T sr = v.h[(size_t)j * N + r] + v.z[(size_t)k * N + r];
+    __syncwarp();
+    if (valid && gl < N) {
+      v.s[(size_t)j * N + r] = sr;
+      v.z[(size_t)k * N + r] = acc;
+    }
   }
 }
 // p_j = Tr_j^T p_k + s_j  (affine expansion)
@@ -808,25 +841,37 @@ template <typename T, int N>
 __device__ __forceinline__ void aff_expand_op(const Ws<T>& w, int rr, bool valid, int gl) {
   const int j = w.comp_j[rr], k = w.comp_k[rr], r = gl < N ? gl : 0;
   const T* Trj = w.Tr + (size_t)j * N * N;
-  T p[N];
-  vec_load(p, w.h + (size_t)k * N);
-  T acc = w.s[(size_t)j * N + r];
+  T col[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) acc = fma(Trj[t * N + r], p[t], acc);
-  if (valid && gl < N) w.h[(size_t)j * N + r] = acc;
+  for (int t = 0; t < N; ++t) col[t] = Trj[t * N + r];
+  for (int q = 0; q < w.nrhs; ++q) {
+    const Ws<T> v = w.rhs(q);
+    T p[N];
+    vec_load(p, v.h + (size_t)k * N);
+    T acc = v.s[(size_t)j * N + r];
+#pragma unroll
+    for (int t = 0; t < N; ++t) acc = fma(col[t], p[t], acc);
+    if (valid && gl < N) v.h[(size_t)j * N + r] = acc;
+  }
 }
 // b_k <- Tr_j b_j + b_k  (state-map composition of the offsets)
 template <typename T, int N>
 __device__ __forceinline__ void state_compress_op(const Ws<T>& w, int rr, bool valid, int gl) {
   const int j = w.comp_j[rr], k = w.comp_k[rr], r = gl < N ? gl : 0;
   const T* Trj = w.Tr + (size_t)j * N * N + r * N;
-  T b[N];
-  vec_load(b, w.bv + (size_t)j * N);
-  T acc = w.bv[(size_t)k * N + r];
+  T row[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) acc = fma(Trj[t], b[t], acc);
-  __syncwarp();
-  if (valid && gl < N) w.bv[(size_t)k * N + r] = acc;
+  for (int t = 0; t < N; ++t) row[t] = Trj[t];
+  for (int q = 0; q < w.nrhs; ++q) {
+    const Ws<T> v = w.rhs(q);
+    T b[N];
+    vec_load(b, v.bv + (size_t)j * N);
+    T acc = v.bv[(size_t)k * N + r];
+#pragma unroll
+    for (int t = 0; t < N; ++t) acc = fma(row[t], b[t], acc);
+    __syncwarp();
+    if (valid && gl < N) v.bv[(size_t)k * N + r] = acc;
+  }
 }
 // x_j = T_j x_i + b_j  (state expansion)
 template <typename T, int N>
@@ -834,12 +879,18 @@ __device__ __forceinline__ void state_expand_op(const Ws<T>& w, const int* nodes
                                                 bool valid, int gl) {
   const int j = nodes[rr], i = from[rr], r = gl < N ? gl : 0;
   const T* Tj = w.Tm + (size_t)j * N * N + r * N;
-  T x[N];
-  vec_load(x, w.xs + (size_t)i * N);
-  T acc = w.bv[(size_t)j * N + r];
+  T row[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) acc = fma(Tj[t], x[t], acc);
-  if (valid && gl < N) w.xs[(size_t)j * N + r] = acc;
+  for (int t = 0; t < N; ++t) row[t] = Tj[t];
+  for (int q = 0; q < w.nrhs; ++q) {
+    const Ws<T> v = w.rhs(q);
+    T x[N];
+    vec_load(x, v.xs + (size_t)i * N);
+    T acc = v.bv[(size_t)j * N + r];
+#pragma unroll
+    for (int t = 0; t < N; ++t) acc = fma(row[t], x[t], acc);
+    if (valid && gl < N) v.xs[(size_t)j * N + r] = acc;
+  }
 }
 
 template <typename T, int N>
@@ -847,6 +898,12 @@ __global__ void kf_aff_rake(Ws<T> w, int begin, int count) {
   int op;
   const Grp g = group_of<T, N>(count, &op);
   aff_rake_op<T, N>(w, begin + op, g.valid, g.gl);
+}
+template <typename T, int N>
+__global__ void kf_aff_absorb(Ws<T> w, int begin, int count) {
+  int op;
+  const Grp g = group_of<T, N>(count, &op);
+  aff_absorb_op<T, N>(w, begin + op, g.valid, g.gl);
 }
 template <typename T, int N>
 __global__ void kf_aff_compress(Ws<T> w, int begin, int count) {
@@ -873,6 +930,42 @@ __global__ void kf_state_expand(Ws<T> w, const int* nodes, const int* from, int 
   state_expand_op<T, N>(w, nodes, from, begin + op, g.valid, g.gl);
 }
 
+// Right-hand-side passes, level-asynchronous: the affine pass (kinds AK_*: its
+// dependency structure is that of the factorisation, on h for U, z for the
+// edge slots and s for the tape) or the state pass (kinds SK_*), all rounds in
+// one launch.  The operations are the O(n^2) vector maps of the per-round
+// kernels; no shared memory.
+template <typename T, int N>
+__global__ void kf_async_vec(Ws<T> w, AsyncArgs a) {
+  constexpr int G = D<T, N>::G, OPS = D<T, N>::OPS;
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1), gsub = lane / G;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(a.counter, OPS);
+    base = __shfl_sync(TLQR_FULL_MASK, base, 0);
+    if (base >= a.n_ops) break;
+    const int pos = base + gsub;
+    const int word = a.op[pos];
+    const int kind = word >> 28;
+    int idx = word & kAsyncPad;
+    const bool valid = idx != kAsyncPad;
+    if (async_wait(a, pos, w.status)) return;
+    const int idx0 = __shfl_sync(TLQR_FULL_MASK, idx, 0);
+    if (!valid) idx = idx0;
+    switch (kind) {
+      case AK_RAKE: aff_rake_op<T, N>(w, idx, valid, gl); break;
+      case AK_ABSORB: aff_absorb_op<T, N>(w, idx, valid, gl); break;
+      case AK_COMPRESS: aff_compress_op<T, N>(w, idx, valid, gl); break;
+      case AK_EXPAND: aff_expand_op<T, N>(w, idx, valid, gl); break;
+      case SK_COMPOSE: state_compress_op<T, N>(w, idx, valid, gl); break;
+      case SK_EXPAND_C: state_expand_op<T, N>(w, w.comp_j, w.comp_i, idx, valid, gl); break;
+      default: state_expand_op<T, N>(w, w.rake_leaf, w.rake_parent, idx, valid, gl); break;
+    }
+    async_publish(a, pos, valid, gl);
+  }
+}
+
 // ---------------------------------------------------------------- tail kernels
 // The late structural rounds hold few operations each; running them as one
 // launch per phase costs a kernel launch per handful of operations.  A tail
@@ -880,6 +973,10 @@ __global__ void kf_state_expand(Ws<T> w, const int* nodes, const int* from, int 
 // inside ONE block: its groups stride over each phase's operations and the
 // phases are separated by __syncthreads().  No block waits for another.
 struct RoundDesc { int rb, re, sb, se, cb, ce; };
+
+// Threads of the single-block tail kernels; __launch_bounds__ keeps their
+// register use within one block of this size.
+constexpr int kTailBlock = 1024;
 
 // Loop `count` operations over the block's groups with uniform trip counts.
 #define TLQR_BLOCK_OPS(count, ...)                                             \
@@ -896,7 +993,7 @@ struct RoundDesc { int rb, re, sb, se, cb, ce; };
 // Affine pass tail: forward rounds r0..R-1 (rake, absorb, compress), then the
 // backward rounds R-1..r0 (expand).
 template <typename T, int N>
-__global__ void kf_aff_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
+__global__ void __launch_bounds__(kTailBlock) kf_aff_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
   constexpr int G = D<T, N>::G;
   const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
   for (int r = r0; r < R; ++r) {
@@ -918,7 +1015,7 @@ __global__ void kf_aff_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
 // State pass tail: forward compositions r0..R-1, then expansion R-1..r0
 // (compressed centres before the leaves raked in the same round).
 template <typename T, int N>
-__global__ void kf_state_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
+__global__ void __launch_bounds__(kTailBlock) kf_state_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
   constexpr int G = D<T, N>::G;
   const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
   for (int r = r0; r < R; ++r) {
@@ -1353,35 +1450,39 @@ __global__ void kf_aff_init(Ws<T> w, int count) {
   T *sA = sW + N * LD, *sK = sA + N * LD, *sB = sK + M * LD, *vc = sB + N * MLD, *vw = vc + LD, *vr = vw + LD;
   const int gl = g.gl, r = gl < N ? gl : 0;
   const bool is_root = node_is_root(w, j);
-  if (g.valid && gl < N) w.h[(size_t)j * N + r] = (T)w.q[(size_t)j * N + r];
   const size_t oj = (size_t)j * NN, om = (size_t)j * NM;
   const bool dnz = w.has_delta && w.dflag[j];
   stage<T, T, N, N, LD, G>(sW, dnz ? w.W + oj : w.U + oj, gl);
   stage<T, double, N, N, LD, G>(sA, w.A + oj, gl);
   stage<T, T, M, N, LD, G>(sK, w.K + om, gl);
   stage<T, double, N, M, MLD, G>(sB, w.B + om, gl);
-  if (gl < N) vc[gl] = (T)w.c[(size_t)j * N + gl];
-  if (gl < M) vr[gl] = (T)w.r[(size_t)j * M + gl];
-  if (gl >= N && gl < LD) vc[gl] = T(0);
-  __syncwarp();
-  T row[N], cv[N];
-  row_load<T, N>(row, sW + r * LD);
-  row_load<T, N>(cv, vc);
-  T wr = T(0);
+  for (int k = 0; k < w.nrhs; ++k) {           // right-hand sides of a panel, blocks staged once
+    const Ws<T> q = w.rhs(k);
+    if (g.valid && gl < N) q.h[(size_t)j * N + r] = (T)q.q[(size_t)j * N + r];
+    if (gl < N) vc[gl] = (T)q.c[(size_t)j * N + gl];
+    if (gl < M) vr[gl] = (T)q.r[(size_t)j * M + gl];
+    if (gl >= N && gl < LD) vc[gl] = T(0);
+    __syncwarp();
+    T row[N], cv[N];
+    row_load<T, N>(row, sW + r * LD);
+    row_load<T, N>(cv, vc);
+    T wr = T(0);
 #pragma unroll
-  for (int t = 0; t < N; ++t) wr = fma(row[t], cv[t], wr);     // w = W c
-  if (gl < N) vw[gl] = wr;
-  __syncwarp();
-  T wv[N], v[M];
-  row_load<T, N>(wv, vw);
-  row_load<T, M>(v, vr);
-  row_mm<T, N, M, MLD>(v, wv, sB);              // v = r + B^T w
-  T z = T(0);
+    for (int t = 0; t < N; ++t) wr = fma(row[t], cv[t], wr);     // w = W c
+    if (gl < N) vw[gl] = wr;
+    __syncwarp();
+    T wv[N], v[M];
+    row_load<T, N>(wv, vw);
+    row_load<T, M>(v, vr);
+    row_mm<T, N, M, MLD>(v, wv, sB);              // v = r + B^T w
+    T z = T(0);
 #pragma unroll
-  for (int a = 0; a < M; ++a) z = fma(sK[a * LD + r], v[a], z);
+    for (int a = 0; a < M; ++a) z = fma(sK[a * LD + r], v[a], z);
 #pragma unroll
-  for (int t = 0; t < N; ++t) z = fma(sA[t * LD + r], wv[t], z);
-  if (g.valid && !is_root && gl < N) w.z[(size_t)j * N + r] = z;
+    for (int t = 0; t < N; ++t) z = fma(sA[t * LD + r], wv[t], z);
+    if (g.valid && !is_root && gl < N) q.z[(size_t)j * N + r] = z;
+    __syncwarp();
+  }
 }
 
 template <typename T, int N, int M>
@@ -1414,86 +1515,90 @@ __global__ void kf_local_solve(Ws<T> w, int count) {
     stage<T, double, N, N, LD, G>(sD, w.Delta + oj, gl);
     stage<T, T, N, N, LD, G>(sFi, w.Finv + oj, gl);
   }
-  if (gl < LD) vp[gl] = gl < N ? w.h[(size_t)j * N + gl] : T(0);
-  if (gl < M) vr[gl] = (T)w.r[(size_t)j * M + gl];
-  __syncwarp();
-  T p[N];
-  row_load<T, N>(p, vp);
-  T pr = p[0];
+  for (int kq = 0; kq < w.nrhs; ++kq) {         // right-hand sides of a panel, blocks staged once
+    const Ws<T> q = w.rhs(kq);
+    if (gl < LD) vp[gl] = gl < N ? q.h[(size_t)j * N + gl] : T(0);
+    if (gl < M) vr[gl] = (T)q.r[(size_t)j * M + gl];
+    __syncwarp();
+    T p[N];
+    row_load<T, N>(p, vp);
+    T pr = p[0];
 #pragma unroll
-  for (int t = 0; t < N; ++t) pr = (t == r) ? p[t] : pr;
-  T fr = -(T)w.c[(size_t)j * N + r];
-  if (dnz) {
-    T dr[N];
-    row_load<T, N>(dr, sD + r * LD);
+    for (int t = 0; t < N; ++t) pr = (t == r) ? p[t] : pr;
+    T fr = -(T)q.c[(size_t)j * N + r];
+    if (dnz) {
+      T dr[N];
+      row_load<T, N>(dr, sD + r * LD);
 #pragma unroll
-    for (int t = 0; t < N; ++t) fr = fma(dr[t], p[t], fr);   // f = Delta p - c
-  }
-  if (gl < LD) vf[gl] = gl < N ? fr : T(0);
-  __syncwarp();
-  T f[N];
-  row_load<T, N>(f, vf);
-  // root: x = -F^{-1} f ; others: g = p - W f
-  T xr = -fr;
-  if (dnz) {
-    T fi[N];
-    row_load<T, N>(fi, sFi + r * LD);
-    xr = T(0);
-#pragma unroll
-    for (int t = 0; t < N; ++t) xr = fma(-fi[t], f[t], xr);
-  }
-  T wrow[N];
-  row_load<T, N>(wrow, sW + r * LD);
-  T gr = pr;
-#pragma unroll
-  for (int t = 0; t < N; ++t) gr = fma(-wrow[t], f[t], gr);
-  if (gl < LD) vg[gl] = gl < N ? gr : T(0);
-  __syncwarp();
-  // k = -G^{-1}(r + B^T g) (every lane)
-  T gv[N], k[M];
-  row_load<T, N>(gv, vg);
-  row_load<T, M>(k, vr);
-  row_mm<T, N, M, MLD>(k, gv, sB);
-  T Lg[M][M];
-#pragma unroll
-  for (int a = 0; a < M; ++a) {
-    T row[M];
-    row_load<T, M>(row, sL + a * MLD);
-#pragma unroll
-    for (int b = 0; b < M; ++b) Lg[a][b] = is_root ? ((a == b) ? T(1) : T(0)) : row[b];
-  }
-  chol_solve_reg<T, M>(Lg, k);
-#pragma unroll
-  for (int a = 0; a < M; ++a) k[a] = -k[a];
-  // b = F^{-1}(B k - f)
-  T brow[M];
-  row_load<T, M>(brow, sB + r * MLD);
-  T tr = -fr;
-#pragma unroll
-  for (int a = 0; a < M; ++a) tr = fma(brow[a], k[a], tr);
-  if (gl < LD) vt[gl] = gl < N ? tr : T(0);
-  __syncwarp();
-  T b = tr;
-  if (dnz) {
-    T tv[N], fi[N];
-    row_load<T, N>(tv, vt);
-    row_load<T, N>(fi, sFi + r * LD);
-    b = T(0);
-#pragma unroll
-    for (int t = 0; t < N; ++t) b = fma(fi[t], tv[t], b);
-  }
-  if (g.valid) {
-    if (is_root) {
-      if (gl < N) w.xs[(size_t)j * N + r] = xr;
-    } else {
-      if (gl < M) {
-        T kk = k[0];
-#pragma unroll
-        for (int a = 0; a < M; ++a) kk = (a == gl) ? k[a] : kk;
-        w.kv[(size_t)j * M + gl] = kk;
-      }
-      if (gl < N) w.bv[(size_t)j * N + r] = b;
+      for (int t = 0; t < N; ++t) fr = fma(dr[t], p[t], fr);   // f = Delta p - c
     }
+    if (gl < LD) vf[gl] = gl < N ? fr : T(0);
+    __syncwarp();
+    T f[N];
+    row_load<T, N>(f, vf);
+    // root: x = -F^{-1} f ; others: g = p - W f
+    T xr = -fr;
+    if (dnz) {
+      T fi[N];
+      row_load<T, N>(fi, sFi + r * LD);
+      xr = T(0);
+#pragma unroll
+      for (int t = 0; t < N; ++t) xr = fma(-fi[t], f[t], xr);
+    }
+    T wrow[N];
+    row_load<T, N>(wrow, sW + r * LD);
+    T gr = pr;
+#pragma unroll
+    for (int t = 0; t < N; ++t) gr = fma(-wrow[t], f[t], gr);
+    if (gl < LD) vg[gl] = gl < N ? gr : T(0);
+    __syncwarp();
+    // k = -G^{-1}(r + B^T g) (every lane)
+    T gv[N], k[M];
+    row_load<T, N>(gv, vg);
+    row_load<T, M>(k, vr);
+    row_mm<T, N, M, MLD>(k, gv, sB);
+    T Lg[M][M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      T row[M];
+      row_load<T, M>(row, sL + a * MLD);
+#pragma unroll
+      for (int b = 0; b < M; ++b) Lg[a][b] = is_root ? ((a == b) ? T(1) : T(0)) : row[b];
+    }
+    chol_solve_reg<T, M>(Lg, k);
+#pragma unroll
+    for (int a = 0; a < M; ++a) k[a] = -k[a];
+    // b = F^{-1}(B k - f)
+    T brow[M];
+    row_load<T, M>(brow, sB + r * MLD);
+    T tr = -fr;
+#pragma unroll
+    for (int a = 0; a < M; ++a) tr = fma(brow[a], k[a], tr);
+    if (gl < LD) vt[gl] = gl < N ? tr : T(0);
+    __syncwarp();
+    T b = tr;
+    if (dnz) {
+      T tv[N], fi[N];
+      row_load<T, N>(tv, vt);
+      row_load<T, N>(fi, sFi + r * LD);
+      b = T(0);
+#pragma unroll
+      for (int t = 0; t < N; ++t) b = fma(fi[t], tv[t], b);
+    }
+    if (g.valid) {
+      if (is_root) {
+        if (gl < N) q.xs[(size_t)j * N + r] = xr;
+      } else {
+        if (gl < M) {
+          T kk = k[0];
+#pragma unroll
+          for (int a = 0; a < M; ++a) kk = (a == gl) ? k[a] : kk;
+          q.kv[(size_t)j * M + gl] = kk;
+        }
+        if (gl < N) q.bv[(size_t)j * N + r] = b;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1504,37 +1609,41 @@ __global__ void kf_recover(Ws<T> w, double* x, double* u, double* y, int accumul
   int j;
   const Grp g = group_of<T, N>(count, &j);
   const int gl = g.gl, r = gl < N ? gl : 0;
-  T xv[N];
+  for (int kq = 0; kq < w.nrhs; ++kq) {         // right-hand sides of a panel
+    const Ws<T> q = w.rhs(kq);
+    double *qx = x + (size_t)kq * w.sv, *qu = u + (size_t)kq * w.sm, *qy = y + (size_t)kq * w.sv;
+    T xv[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) xv[t] = w.xs[(size_t)j * N + t];
-  T xr = xv[0];
+    for (int t = 0; t < N; ++t) xv[t] = q.xs[(size_t)j * N + t];
+    T xr = xv[0];
 #pragma unroll
-  for (int t = 0; t < N; ++t) xr = (t == r) ? xv[t] : xr;
-  T yr = w.h[(size_t)j * N + r];
+    for (int t = 0; t < N; ++t) xr = (t == r) ? xv[t] : xr;
+    T yr = q.h[(size_t)j * N + r];
 #pragma unroll
-  for (int t = 0; t < N; ++t) yr = fma(w.U[(size_t)j * NN + t * N + r], xv[t], yr);   // P symmetric
-  bool bad = !tfinite(xr) || !tfinite(yr);
-  const bool nonroot = !node_is_root(w, j);
-  T ur = T(0);
-  if (nonroot && gl < M) {
-    const int par = w.parent[j];
-    ur = w.kv[(size_t)j * M + gl];
+    for (int t = 0; t < N; ++t) yr = fma(w.U[(size_t)j * NN + t * N + r], xv[t], yr);   // P symmetric
+    bool bad = !tfinite(xr) || !tfinite(yr);
+    const bool nonroot = !node_is_root(w, j);
+    T ur = T(0);
+    if (nonroot && gl < M) {
+      const int par = w.parent[j];
+      ur = q.kv[(size_t)j * M + gl];
 #pragma unroll
-    for (int t = 0; t < N; ++t) ur = fma(w.K[(size_t)j * NM + gl * N + t], w.xs[(size_t)par * N + t], ur);
-    bad |= !tfinite(ur);
-  }
-  if (g.valid) {
-    if (gl < N) {
-      const size_t o = (size_t)j * N + r;
-      if (accumulate) { x[o] += (double)xr; y[o] += (double)yr; }
-      else { x[o] = (double)xr; y[o] = (double)yr; }
+      for (int t = 0; t < N; ++t) ur = fma(w.K[(size_t)j * NM + gl * N + t], q.xs[(size_t)par * N + t], ur);
+      bad |= !tfinite(ur);
     }
-    if (gl < M) {
-      const size_t o = (size_t)j * M + gl;
-      if (nonroot) { if (accumulate) u[o] += (double)ur; else u[o] = (double)ur; }
-      else if (!accumulate) u[o] = 0.0;
+    if (g.valid) {
+      if (gl < N) {
+        const size_t o = (size_t)j * N + r;
+        if (accumulate) { qx[o] += (double)xr; qy[o] += (double)yr; }
+        else { qx[o] = (double)xr; qy[o] = (double)yr; }
+      }
+      if (gl < M) {
+        const size_t o = (size_t)j * M + gl;
+        if (nonroot) { if (accumulate) qu[o] += (double)ur; else qu[o] = (double)ur; }
+        else if (!accumulate) qu[o] = 0.0;
+      }
+      if (bad) atomicCAS(w.status, 0, ST_NONFINITE);
     }
-    if (bad) atomicCAS(w.status, 0, ST_NONFINITE);
   }
 }
 

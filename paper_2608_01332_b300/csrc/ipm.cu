@@ -11,7 +11,8 @@
 // (its captured launch graphs are reused: the buffers do not move).  The
 // multiplier steps follow from linearising l s = mu; the step length keeps
 // slacks and multipliers positive (fraction to the boundary tau); then
-// mu <- sigma * mean(l s).  Everything per component runs in device kernels;
+// mu <- sigma * mean(l s).  At convergence the multipliers are recovered from
+// the control rows of the KKT system.  Everything per component runs in device kernels;
 // the host reads two numbers per iteration (step length and gap).
 #include <cuda_runtime.h>
 
@@ -35,7 +36,24 @@ struct Ipm {
   double *l_lo, *l_hi, *du, *dl_lo, *dl_hi;
   unsigned long long* alpha_bits;  // step length (bits of a positive double, atomicMin)
   double* gap;                     // sum of l s over the bounded components
+  double* gap_part;                // [gridDim.x] per-block partial sums (fixed order: deterministic)
+  unsigned long long* smax_bits;   // largest barrier term l / s after the step (atomicMax of bits)
+  const int* parent;               // [N] the plan's parent array
 };
+
+// Block sum of one double per thread in a fixed order (shuffles, then warp
+// partials by thread 0); returns the total in thread 0.
+__device__ double block_sum(double v) {
+  __shared__ double part[32];
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) t += part[w];
+  return t;
+}
 
 __device__ __forceinline__ bool bounded(double b) { return isfinite(b); }
 
@@ -60,10 +78,7 @@ __global__ void k_ipm_init(Ipm a, double mu0) {
 
 // R~, r~ of the Newton system; also resets the step length and the gap.
 __global__ void k_ipm_form(Ipm a, double mu) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.alpha_bits = (unsigned long long)__double_as_longlong(1.0);
-    *a.gap = 0.0;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.alpha_bits = (unsigned long long)__double_as_longlong(1.0);
   const int m = a.m;
   const size_t total = (size_t)a.N * m;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -82,6 +97,7 @@ __global__ void k_ipm_form(Ipm a, double mu) {
 // Step directions of u and the multipliers, and the largest step that keeps
 // every slack and multiplier positive (times tau).
 __global__ void k_ipm_step(Ipm a, double mu, double tau) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.smax_bits = 0ull;
   double amin = 1.0;
   const size_t total = (size_t)a.N * a.m;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -114,7 +130,7 @@ __global__ void k_ipm_step(Ipm a, double mu, double tau) {
 // Take the step and sum the new complementarity gap.
 __global__ void k_ipm_update(Ipm a) {
   const double alpha = __longlong_as_double((long long)*a.alpha_bits);
-  double g = 0.0;
+  double g = 0.0, smax = 0.0;
   const size_t total = (size_t)a.N * a.m;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(t / a.m);
@@ -122,16 +138,68 @@ __global__ void k_ipm_update(Ipm a) {
     const bool on = a.edge[j], hl = on && bounded(lo), hh = on && bounded(hi);
     const double u = on ? a.u[t] + alpha * a.du[t] : 0.0;
     a.u[t] = u;
-    if (hl) { a.l_lo[t] += alpha * a.dl_lo[t]; g += a.l_lo[t] * (u - lo); }
-    if (hh) { a.l_hi[t] += alpha * a.dl_hi[t]; g += a.l_hi[t] * (hi - u); }
+    if (hl) {
+      a.l_lo[t] += alpha * a.dl_lo[t];
+      g += a.l_lo[t] * (u - lo);
+      smax = fmax(smax, a.l_lo[t] / (u - lo));
+    }
+    if (hh) {
+      a.l_hi[t] += alpha * a.dl_hi[t];
+      g += a.l_hi[t] * (hi - u);
+      smax = fmax(smax, a.l_hi[t] / (hi - u));
+    }
   }
+  for (int off = 16; off; off >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+  if ((threadIdx.x & 31) == 0 && smax > 0.0)
+    atomicMax(a.smax_bits, (unsigned long long)__double_as_longlong(isnan(smax) ? INFINITY : smax));
   const size_t nx = (size_t)a.N * a.n;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nx; t += (size_t)gridDim.x * blockDim.x) {
     a.x[t] += alpha * (a.xp[t] - a.x[t]);
     a.y[t] += alpha * (a.yp[t] - a.y[t]);
   }
-  for (int off = 16; off; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
-  if ((threadIdx.x & 31) == 0 && g != 0.0) atomicAdd(a.gap, g);
+  const double b = block_sum(g);
+  if (threadIdx.x == 0) a.gap_part[blockIdx.x] = b;
+}
+
+// Dual recovery at convergence: each control row of eq. (kkt) with the bound
+// multipliers, g - l_lo + l_hi = 0 with g = R u + r + M^T x_parent + B^T y, fixes
+// l_lo - l_hi = g; split by sign (l_lo = max(g, 0), l_hi = max(-g, 0) where the
+// bound exists).  The updated multipliers of the last Newton step carry the
+// rounding of the barrier terms l / s ~ 1 / tol on the active rows; these
+// satisfy stationarity to ordinary rounding, and l s stays at the scale of the
+// final gap (g vanishes on inactive rows, s on active ones).
+__global__ void k_ipm_duals(Ipm a, const double* M, const double* B) {
+  const int n = a.n, m = a.m;
+  const size_t total = (size_t)a.N * m;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / m), c = (int)(t - (size_t)j * m);
+    if (!a.edge[j]) continue;
+    const int i = a.parent[j];
+    double g = a.r[t];
+    for (int b = 0; b < m; ++b) g += a.R[(size_t)j * m * m + (size_t)c * m + b] * a.u[(size_t)j * m + b];
+    for (int q = 0; q < n; ++q) {
+      g += B[(size_t)j * n * m + (size_t)q * m + c] * a.y[(size_t)j * n + q];
+      if (M) g += M[(size_t)j * n * m + (size_t)q * m + c] * a.x[(size_t)i * n + q];
+    }
+    const bool hl = bounded(a.lo[t]), hh = bounded(a.hi[t]);
+    if (hl) a.l_lo[t] = g > 0 ? g : 0.0;
+    if (hh) a.l_hi[t] = g < 0 ? -g : 0.0;
+  }
+}
+
+// The gap: the block partials summed in block order by one thread.
+__global__ void k_ipm_gap(Ipm a, int parts) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double g = 0.0;
+    for (int t = 0; t < parts; ++t) g += a.gap_part[t];
+    *a.gap = g;
+  }
+}
+
+// An FP64 factor object can stand in for a MIXED one.
+bool o64_possible(const tlqr_factor_t* f) {
+  tlqr_options o{};
+  return tlqr_factor_options(f, &o) == TLQR_OK && o.precision == TLQR_PREC_MIXED;
 }
 
 bool device_ptr(const void* p) {
@@ -143,6 +211,10 @@ bool device_ptr(const void* p) {
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
+
+// Largest barrier term l / s at which a MIXED factor object still solves the
+// Newton systems; beyond it the driver switches to FP64.
+constexpr double kIpmSwitch = 1e6;
 
 }  // namespace
 
@@ -185,9 +257,18 @@ extern "C" int tlqr_ipm_box(const tlqr_plan_t* plan, tlqr_factor_t* f, const tlq
   }
   // one workspace allocation for the whole run
   const size_t nm = N * m, nn = N * n;
-  const size_t doubles = N * m * m + 5 * nm + 2 * nn + 2;
+  int dev_id = 0, sms = 1;
+  cudaGetDevice(&dev_id);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+  const int threads = 256;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((std::max(nm, nn) + threads - 1) / threads,
+                                                                (size_t)sms * 8));
+  const size_t doubles = N * m * m + 5 * nm + 2 * nn + 3 + (size_t)blocks;
   unsigned char* ws = nullptr;
-  if (cudaMalloc((void**)&ws, doubles * sizeof(double) + N)) { cudaGetLastError(); return TLQR_ERR_OOM; }
+  if (cudaMalloc((void**)&ws, doubles * sizeof(double) + N * sizeof(int) + N)) {
+    cudaGetLastError();
+    return TLQR_ERR_OOM;
+  }
   double* d = reinterpret_cast<double*>(ws);
   Ipm a{};
   a.N = (int)N; a.n = n; a.m = m;
@@ -202,17 +283,16 @@ extern "C" int tlqr_ipm_box(const tlqr_plan_t* plan, tlqr_factor_t* f, const tlq
   a.dl_hi = d; d += nm;
   a.gap = d; d += 1;
   a.alpha_bits = reinterpret_cast<unsigned long long*>(d); d += 1;
-  a.edge = reinterpret_cast<unsigned char*>(d);
+  a.gap_part = d; d += blocks;
+  a.smax_bits = reinterpret_cast<unsigned long long*>(d); d += 1;
+  a.parent = reinterpret_cast<const int*>(d);
+  a.edge = reinterpret_cast<unsigned char*>(d) + N * sizeof(int);
   a.x = x; a.u = u; a.y = y; a.l_lo = lam_lo; a.l_hi = lam_hi;
   int rc = TLQR_OK;
   auto fail = [&](int code) { cudaFree(ws); return code; };
-  if (cudaMemcpyAsync((void*)a.edge, edge.data(), N, cudaMemcpyHostToDevice, st)) return fail(TLQR_ERR_CUDA);
-  int dev_id = 0, sms = 1;
-  cudaGetDevice(&dev_id);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
-  const int threads = 256;
-  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((std::max(nm, nn) + threads - 1) / threads,
-                                                                (size_t)sms * 8));
+  if (cudaMemcpyAsync((void*)a.edge, edge.data(), N, cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync((void*)a.parent, plan->parent.data(), N * sizeof(int), cudaMemcpyHostToDevice, st))
+    return fail(TLQR_ERR_CUDA);
   k_ipm_init<<<blocks, threads, 0, st>>>(a, o.mu0);
   if (cudaGetLastError()) return fail(TLQR_ERR_CUDA);
   tlqr_problem pt = *prob;
@@ -222,27 +302,75 @@ extern "C" int tlqr_ipm_box(const tlqr_plan_t* plan, tlqr_factor_t* f, const tlq
   sol.mem = TLQR_MEM_DEVICE;
   sol.x = a.xp; sol.u = a.up; sol.y = a.yp;
   double mu = o.mu0, mean_gap = INFINITY, alpha = 0.0;
-  int it = 0;
+  int it = 0, fp64_solves = 0;
   tlqr_info last{};
+  // Near the solution the barrier terms S grow like 1 / mu, and a Newton system
+  // can become too ill-conditioned for FP32 factors plus refinement; such a
+  // system is solved again with an FP64 factor object of the same plan
+  // (created once, on first need).
+  tlqr_factor_t* f64 = nullptr;
+  auto fail64 = [&](int code) { if (f64) tlqr_factor_destroy(f64); return fail(code); };
+  bool use64 = false;                        // MIXED: Newton systems now solved in FP64
+  const bool mixed = o64_possible(f), allow64 = !(opts && opts->no_fp64_fallback);
+  auto make64 = [&]() -> int {
+    if (f64) return TLQR_OK;
+    tlqr_options o64{};
+    if (tlqr_factor_options(f, &o64)) return TLQR_ERR_ARG;
+    o64.precision = TLQR_PREC_FP64;
+    return tlqr_factor_create(plan, &o64, &f64);
+  };
   for (it = 1; it <= o.max_iter; ++it) {
     k_ipm_form<<<blocks, threads, 0, st>>>(a, mu);
-    if (cudaGetLastError()) return fail(TLQR_ERR_CUDA);
-    if ((rc = tlqr_solve(f, &pt, &sol, stream))) return fail(rc);
-    tlqr_last_info(f, &last);
+    if (cudaGetLastError()) return fail64(TLQR_ERR_CUDA);
+    if (use64) {
+      if ((rc = make64())) return fail64(rc);
+      rc = tlqr_solve(f64, &pt, &sol, stream);
+      last = tlqr_info{};
+      ++fp64_solves;
+    } else {
+      rc = tlqr_solve(f, &pt, &sol, stream);
+      tlqr_last_info(f, &last);
+    }
+    const bool precision_failure =
+        rc == TLQR_ERR_NO_CONVERGENCE || rc == TLQR_ERR_NOT_PD || rc == TLQR_ERR_NONFINITE || rc == TLQR_ERR_SINGULAR;
+    if (rc == TLQR_ERR_NO_CONVERGENCE && opts && opts->no_fp64_fallback) {
+      rc = TLQR_OK;                           // inexact Newton step at the accuracy refinement reached
+    } else if (precision_failure && !use64 && mixed && allow64) {
+      if ((rc = make64())) return fail64(rc);
+      rc = tlqr_solve(f64, &pt, &sol, stream);
+      last = tlqr_info{};
+      ++fp64_solves;
+      use64 = true;
+    }
+    if (rc) return fail64(rc);
     k_ipm_step<<<blocks, threads, 0, st>>>(a, mu, o.tau);
     k_ipm_update<<<blocks, threads, 0, st>>>(a);
-    if (cudaGetLastError()) return fail(TLQR_ERR_CUDA);
+    k_ipm_gap<<<1, 32, 0, st>>>(a, blocks);
+    if (cudaGetLastError()) return fail64(TLQR_ERR_CUDA);
     double h[2] = {0, 0};
-    unsigned long long ab = 0;
+    unsigned long long ab = 0, sb = 0;
     if (cudaMemcpyAsync(&ab, a.alpha_bits, sizeof(ab), cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(&sb, a.smax_bits, sizeof(sb), cudaMemcpyDeviceToHost, st) ||
         cudaMemcpyAsync(h, a.gap, sizeof(double), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
-      return fail(TLQR_ERR_CUDA);
+      return fail64(TLQR_ERR_CUDA);
     std::memcpy(&alpha, &ab, sizeof(alpha));
+    double smax = 0.0;
+    std::memcpy(&smax, &sb, sizeof(smax));
+    // FP32 factors stop resolving the Newton step on the active bounds once the
+    // barrier terms l / s reach ~1e6 (measured: the step length then collapses
+    // although each solve still meets its normwise tolerance); from there on
+    // the Newton systems are solved in FP64
+    if (mixed && allow64 && smax > kIpmSwitch) use64 = true;
     mean_gap = n_ineq ? h[0] / (double)n_ineq : 0.0;
-    if (!std::isfinite(mean_gap)) return fail(TLQR_ERR_NONFINITE);
+    if (!std::isfinite(mean_gap)) return fail64(TLQR_ERR_NONFINITE);
     // stop after a full Newton step: the linear KKT rows then hold to solve accuracy
     if (mean_gap <= o.tol && alpha >= 1.0) break;
     mu = o.sigma * mean_gap;
+  }
+  const bool converged = mean_gap <= o.tol && alpha >= 1.0;
+  if (converged) {
+    k_ipm_duals<<<blocks, threads, 0, st>>>(a, prob->M, prob->B);
+    if (cudaGetLastError() || cudaStreamSynchronize(st)) return fail64(TLQR_ERR_CUDA);
   }
   if (info) {
     info->iterations = std::min(it, o.max_iter);
@@ -250,7 +378,9 @@ extern "C" int tlqr_ipm_box(const tlqr_plan_t* plan, tlqr_factor_t* f, const tlq
     info->mean_gap = mean_gap;
     info->last_alpha = alpha;
     info->last_eta = last.eta;
+    info->fp64_solves = fp64_solves;
   }
+  if (f64) tlqr_factor_destroy(f64);
   cudaFree(ws);
-  return (mean_gap <= o.tol && alpha >= 1.0) ? TLQR_OK : TLQR_ERR_NO_CONVERGENCE;
+  return converged ? TLQR_OK : TLQR_ERR_NO_CONVERGENCE;
 }

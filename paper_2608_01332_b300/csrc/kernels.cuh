@@ -47,6 +47,21 @@ struct Ws {
   // solve workspace
   T *h, *z, *s, *cv, *bv, *kv, *xs;
   int* status;
+  // panel solves: nrhs right-hand sides at once; every vector above (and q, r,
+  // c) is [nrhs][..] with these strides between right-hand sides
+  int nrhs;
+  size_t sv, sm, scv;          // n-vectors (N n), m-vectors (N m), rake contributions (rakes n)
+  // the same workspace seen from right-hand side k of the panel
+  __host__ __device__ Ws rhs(int k) const {
+    Ws v = *this;
+    if (k) {
+      const size_t ov = (size_t)k * sv, om = (size_t)k * sm, oc = (size_t)k * scv;
+      v.q = q + ov; v.c = c + ov; v.r = r + om;
+      v.h = h + ov; v.z = z + ov; v.s = s + ov; v.bv = bv + ov; v.xs = xs + ov;
+      v.kv = kv + om; v.cv = cv + oc;
+    }
+    return v;
+  }
 };
 
 // A node is a root (of its tree in a forest) when its parent is -1.  Batched

@@ -35,8 +35,9 @@ using namespace tlqr;
 namespace {
 
 constexpr int kMaxWarpsPerBlock = 8;
-constexpr int kTailOps = 512;        // per-phase operation count below which rounds join the tail kernel
-constexpr int kTailThreads = 1024;
+constexpr int kTailOps = 128;        // per-phase operation count below which rounds join the tail kernel
+constexpr int kTailThreads = fx::kTailBlock;
+constexpr int kPanel = 8;            // right-hand sides per panel of tlqr_solve_rhs_panel
 constexpr int kAsyncOps = 1024;     // default: rounds with at most this many operations run level-asynchronously
 constexpr int kSpinLimit = 1 << 22;  // polls of one dependency wait (with backoff: about a second) before TIMEOUT
 constexpr size_t kSmemBudget = 200 * 1024;
@@ -319,6 +320,108 @@ AsyncPlan build_async(const tlqr_plan_t* P, int r0, int ops_per_warp) {
   return A;
 }
 
+// Operation list of the level-asynchronous state pass (fx::kf_async_vec, state
+// kinds): the offset compositions b_k <- Tr_j b_j + b_k of every compression in
+// forward round order, then per round in reverse order the state expansions
+// x_j = T_j x_i + b_j of the compressed centres and of the raked leaves.
+//   composition of j (into k)   <- last writers of b_j and b_k
+//   expansion of j (from i)     <- last writer of b_j, the expansion that wrote x_i
+// (b comes from the local solve and x of a root from the root solve, both in
+// earlier launches).  Sorted and padded as build_async.
+AsyncPlan build_async_state(const tlqr_plan_t* P, int ops_per_warp) {
+  AsyncPlan A;
+  const int R = (int)P->rounds.size();
+  A.r0 = 0;
+  if (R == 0) return A;
+  struct Op { int kind, idx, level; int dep[2]; };
+  std::vector<Op> ops;
+  const int N = P->N;
+  std::vector<int> lastB(N, -1), lastX(N, -1);
+  auto level_of = [&](const Op& o) {
+    int l = 0;
+    for (int d : o.dep) if (d >= 0) l = std::max(l, ops[d].level);
+    return l + 1;
+  };
+  for (int r = 0; r < R; ++r) {
+    const tlqr_round& rd = P->rounds[r];
+    for (int c = rd.comp_begin; c < rd.comp_end; ++c) {
+      const int j = P->comp_j[c], k = P->comp_k[c];
+      Op o{fx::SK_COMPOSE, c, 0, {lastB[j], lastB[k]}};
+      o.level = level_of(o);
+      lastB[k] = (int)ops.size();
+      ops.push_back(o);
+    }
+  }
+  for (int r = R - 1; r >= 0; --r) {
+    const tlqr_round& rd = P->rounds[r];
+    for (int c = rd.comp_begin; c < rd.comp_end; ++c) {
+      const int j = P->comp_j[c], i = P->comp_i[c];
+      Op o{fx::SK_EXPAND_C, c, 0, {lastB[j], lastX[i]}};
+      o.level = level_of(o);
+      lastX[j] = (int)ops.size();
+      ops.push_back(o);
+    }
+    for (int t = rd.rake_begin; t < rd.rake_end; ++t) {
+      const int j = P->rake_leaf[t], i = P->rake_parent[t];
+      Op o{fx::SK_EXPAND_R, t, 0, {lastB[j], lastX[i]}};
+      o.level = level_of(o);
+      lastX[j] = (int)ops.size();
+      ops.push_back(o);
+    }
+  }
+  std::vector<int> order(ops.size());
+  for (size_t t = 0; t < ops.size(); ++t) order[t] = (int)t;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return ops[a].level != ops[b].level ? ops[a].level < ops[b].level : ops[a].kind < ops[b].kind;
+  });
+  std::vector<int> pos_of(ops.size(), -1), slot_op;
+  for (size_t t = 0; t < order.size(); ++t) {
+    const Op& o = ops[order[t]];
+    if (t > 0) {
+      const Op& prev = ops[order[t - 1]];
+      if (prev.level != o.level || prev.kind != o.kind)
+        while (slot_op.size() % ops_per_warp) slot_op.push_back(-1);
+    }
+    pos_of[order[t]] = (int)slot_op.size();
+    slot_op.push_back(order[t]);
+    A.levels = std::max(A.levels, o.level);
+  }
+  while (slot_op.size() % ops_per_warp) slot_op.push_back(-1);
+  A.n_ops = (int)slot_op.size();
+  A.n_flags = A.n_ops;
+  A.op.assign(A.n_ops, 0);
+  A.dep_flag.assign(3 * (size_t)A.n_ops, -1);
+  A.dep_target.assign(3 * (size_t)A.n_ops, 0);
+  A.signal.assign(A.n_ops, -1);
+  int last_kind = 0;
+  for (int p = 0; p < A.n_ops; ++p) {
+    const int id = slot_op[p];
+    if (id < 0) { A.op[p] = (last_kind << 28) | fx::kAsyncPad; continue; }
+    const Op& o = ops[id];
+    last_kind = o.kind;
+    A.op[p] = (o.kind << 28) | o.idx;
+    for (int d = 0; d < 2; ++d)
+      if (o.dep[d] >= 0) {
+        A.dep_flag[3 * (size_t)p + d] = pos_of[o.dep[d]];
+        A.dep_target[3 * (size_t)p + d] = 1;
+      }
+  }
+  return A;
+}
+
+// Solve-pass vectors of a panel of right-hand sides ([nrhs][..] each).
+struct PanelBufs {
+  void *h = nullptr, *z = nullptr, *s = nullptr, *cv = nullptr, *bv = nullptr, *kv = nullptr, *xs = nullptr;
+};
+
+// One level-asynchronous operation list on the device.
+struct DevAsync {
+  AsyncPlan plan;                  // host copy; plan.n_ops == 0: not used
+  int *op = nullptr, *dep_flag = nullptr, *dep_target = nullptr, *signal = nullptr;
+  int* flags = nullptr;            // [n_flags] flags, then the work counter and the abort word
+  int blocks = 0;                  // persistent grid
+};
+
 struct DevPlan {
   int *rake_leaf = nullptr, *rake_parent = nullptr, *seg_parent = nullptr, *seg_start = nullptr;
   int *comp_j = nullptr, *comp_i = nullptr, *comp_k = nullptr;
@@ -370,11 +473,12 @@ struct tlqr_factor_t {
   fx::RoundDesc* d_rounds = nullptr;  // device copy of the plan's rounds
   int sms = 0;                     // streaming multiprocessors of the factor's device
   int tail_r0 = 0;                 // first round handled by the single-block tail kernels
-  // level-asynchronous factorisation tail (compile-time-n kernels only)
-  AsyncPlan async;                 // host copy of the operation list; async.r0 == rounds: none
-  int *a_op = nullptr, *a_dep_flag = nullptr, *a_dep_target = nullptr, *a_signal = nullptr;
-  int* a_flags = nullptr;          // [n_flags] flags, then the work counter and the abort word
-  int async_blocks = 0;            // persistent grid of kf_async
+  // level-asynchronous launches (compile-time-n kernels only): the factorisation
+  // tail, and the affine and state passes of every right-hand side
+  DevAsync fa, aa, sa;
+  // panel solves: vectors for up to kPanel right-hand sides (one lazy allocation)
+  PanelBufs panel;
+  void* panel_mem = nullptr;
 
   template <typename T>
   Ws<T> ws(const tlqr_problem& p) const {
@@ -392,6 +496,10 @@ struct tlqr_factor_t {
     w.dflag = dflag;
     w.h = (T*)h; w.z = (T*)z; w.s = (T*)s; w.cv = (T*)cv; w.bv = (T*)bv; w.kv = (T*)kv; w.xs = (T*)xs;
     w.status = status;
+    w.nrhs = 1;
+    w.sv = (size_t)P->N * opt.n;
+    w.sm = (size_t)P->N * opt.m;
+    w.scv = std::max<size_t>(1, P->rake_leaf.size()) * opt.n;
     return w;
   }
   ~tlqr_factor_t() {
@@ -400,6 +508,7 @@ struct tlqr_factor_t {
     for (auto& g : g_solve) g.clear();
     for (auto& g : g_resid) g.clear();
     for (void* p : allocs) cudaFree(p);
+    if (panel_mem) cudaFree(panel_mem);
     if (h_maxes) cudaFreeHost(h_maxes);
     if (h_status) cudaFreeHost(h_status);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -479,12 +588,13 @@ void carve_factor(tlqr_factor_t* f, Carve& c) {
   f->dp.child_list = ints(P->child_list);
   f->dp.tree = P->n_trees > 1 ? ints(P->tree_of) : nullptr;
   f->d_rounds = reinterpret_cast<fx::RoundDesc*>(c.take<int>(6 * P->rounds.size(), sizeof(int)));
-  if (f->async.n_ops > 0) {
-    f->a_op = ints(f->async.op);
-    f->a_dep_flag = ints(f->async.dep_flag);
-    f->a_dep_target = ints(f->async.dep_target);
-    f->a_signal = ints(f->async.signal);
-    f->a_flags = c.take<int>((size_t)f->async.n_flags + 2, sizeof(int));
+  for (DevAsync* d : {&f->fa, &f->aa, &f->sa}) {
+    if (d->plan.n_ops == 0) continue;
+    d->op = ints(d->plan.op);
+    d->dep_flag = ints(d->plan.dep_flag);
+    d->dep_target = ints(d->plan.dep_target);
+    d->signal = ints(d->plan.signal);
+    d->flags = c.take<int>((size_t)d->plan.n_flags + 2, sizeof(int));
   }
   const size_t N = P->N, n = f->opt.n, m = f->opt.m, nn = n * n, nm = n * m, mm = m * m;
   const size_t nrake = std::max<size_t>(1, P->rake_leaf.size());
@@ -531,19 +641,21 @@ int upload_plan(tlqr_factor_t* f) {
   up(P->child_list, f->dp.child_list);
   if (P->n_trees > 1) up(P->tree_of, f->dp.tree);
   up(round_table(P), reinterpret_cast<int*>(f->d_rounds));
-  if (f->async.n_ops > 0) {
-    up(f->async.op, f->a_op);
-    up(f->async.dep_flag, f->a_dep_flag);
-    up(f->async.dep_target, f->a_dep_target);
-    up(f->async.signal, f->a_signal);
+  for (DevAsync* d : {&f->fa, &f->aa, &f->sa}) {
+    if (d->plan.n_ops == 0) continue;
+    up(d->plan.op, d->op);
+    up(d->plan.dep_flag, d->dep_flag);
+    up(d->plan.dep_target, d->dep_target);
+    up(d->plan.signal, d->signal);
   }
-  // tail: the longest suffix of rounds whose phases each hold at most kTailOps operations
+  // tail: the longest suffix of rounds whose phases each hold at most tail_ops operations
   const int R = (int)P->rounds.size();
+  const int tail_ops = f->opt.tail_ops > 0 ? f->opt.tail_ops : f->opt.tail_ops < 0 ? 0 : kTailOps;
   f->tail_r0 = R;
-  while (f->tail_r0 > 0) {
+  while (tail_ops > 0 && f->tail_r0 > 0) {
     const tlqr_round& r = P->rounds[f->tail_r0 - 1];
     const int mx = std::max({r.rake_end - r.rake_begin, r.seg_end - r.seg_begin, r.comp_end - r.comp_begin});
-    if (mx > kTailOps) break;
+    if (mx > tail_ops) break;
     --f->tail_r0;
   }
   if (err != cudaSuccess) return TLQR_ERR_CUDA;
@@ -595,29 +707,31 @@ cudaError_t launch_split(Recorder* rc, const SplitList& L, int sms, cudaStream_t
   return e;
 }
 
-// One persistent launch of the level-asynchronous factorisation tail.
-template <typename T, int N>
-cudaError_t launch_async(tlqr_factor_t* f, Recorder* rc, const Ws<T>& w, cudaStream_t st) {
-  const AsyncPlan& A = f->async;
-  cudaError_t e = cudaMemsetAsync(f->a_flags, 0, ((size_t)A.n_flags + 2) * sizeof(int), st);
+// One persistent launch of a level-asynchronous operation list: reset its
+// flags, counter and abort word, then run `kernel` (kf_async for the
+// factorisation tail, kf_async_vec for a right-hand-side pass).
+template <typename T, int N, typename Kernel>
+cudaError_t launch_async(tlqr_factor_t* f, Recorder* rc, int kind, Kernel kernel, const DevAsync& d, size_t smem,
+                         const Ws<T>& w, cudaStream_t st) {
+  const AsyncPlan& A = d.plan;
+  cudaError_t e = cudaMemsetAsync(d.flags, 0, ((size_t)A.n_flags + 2) * sizeof(int), st);
   if (e) return e;
   fx::AsyncArgs a{};
-  a.op = f->a_op; a.dep_flag = f->a_dep_flag; a.dep_target = f->a_dep_target; a.signal = f->a_signal;
-  a.flags = f->a_flags; a.counter = f->a_flags + A.n_flags; a.abort = f->a_flags + A.n_flags + 1;
+  a.op = d.op; a.dep_flag = d.dep_flag; a.dep_target = d.dep_target; a.signal = d.signal;
+  a.flags = d.flags; a.counter = d.flags + A.n_flags; a.abort = d.flags + A.n_flags + 1;
   a.n_ops = A.n_ops;
   a.spin_limit = f->opt.spin_limit > 0 ? f->opt.spin_limit : kSpinLimit;
-  a.withhold = f->opt.test_withhold ? 0 : -1;
+  a.withhold = (f->opt.test_withhold && &d == &f->fa) ? 0 : -1;
   constexpr int gpb = 128 / fx::D<T, N>::G;
-  const size_t smem = (size_t)fx::AsyncSmem<T, N>::bytes * gpb;
-  if (!(rc && rc->capture) && (e = ensure_smem(fx::kf_async<T, N>, smem))) return e;
-  const int blocks = std::max(1, std::min((A.n_ops + gpb - 1) / gpb, f->async_blocks));
-  const bool timed = rc && (rc->mask >> TLQR_K_FACTOR_TAIL) & 1u;
-  EvPair ev{TLQR_K_FACTOR_TAIL, nullptr, nullptr, A.n_ops};
+  if (!(rc && rc->capture) && smem > 0 && (e = ensure_smem(kernel, smem))) return e;
+  const int blocks = std::max(1, std::min((A.n_ops + gpb - 1) / gpb, d.blocks));
+  const bool timed = rc && (rc->mask >> kind) & 1u;
+  EvPair ev{kind, nullptr, nullptr, A.n_ops};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  fx::kf_async<T, N><<<blocks, 128, smem, st>>>(w, a);
+  kernel<<<blocks, 128, smem, st>>>(w, a);
   e = cudaGetLastError();
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
-  if (rc) { rc->launches[TLQR_K_FACTOR_TAIL]++; rc->units[TLQR_K_FACTOR_TAIL] += A.n_ops; }
+  if (rc) { rc->launches[kind]++; rc->units[kind] += A.n_ops; }
   return e;
 }
 
@@ -641,7 +755,7 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
   }
   const int R = (int)P->rounds.size();
   // rounds [RA, R) and their expansions run in the level-asynchronous kernel
-  const int RA = (NF > 0 && f->async.n_ops > 0) ? f->async.r0 : R;
+  const int RA = (NF > 0 && f->fa.plan.n_ops > 0) ? f->fa.plan.r0 : R;
   for (int ri = 0; ri < RA; ++ri) {
     const tlqr_round& rd = P->rounds[ri];
     const int nr = rd.rake_end - rd.rake_begin, ns = rd.seg_end - rd.seg_begin, nc = rd.comp_end - rd.comp_begin;
@@ -661,7 +775,9 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
     }
   }
   if constexpr (NF > 0) {
-    if (RA < R && (e = launch_async<T, NX>(f, rc, w, st))) return e;
+    if (RA < R && (e = launch_async<T, NX>(f, rc, TLQR_K_FACTOR_TAIL, fx::kf_async<T, NX>, f->fa,
+                                            (size_t)fx::AsyncSmem<T, NX>::bytes * (128 / G), w, st)))
+      return e;
   }
   for (int ri = RA - 1; ri >= 0; --ri) {
     const tlqr_round* it = &P->rounds[ri];
@@ -697,11 +813,17 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
 // Right-hand-side sequence (Alg. 1 steps 4-6).
 template <typename T, int NF, int MF>
 cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const double* r, const double* c,
-                      double* x, double* u, double* y, int accumulate, cudaStream_t st) {
+                      double* x, double* u, double* y, int accumulate, cudaStream_t st, int nrhs = 1,
+                      const PanelBufs* pb = nullptr) {
   const tlqr_plan_t* P = f->plan;
   tlqr_problem p = f->dprob;
   p.q = q; p.r = r; p.c = c;
-  const Ws<T> w = f->ws<T>(p);
+  Ws<T> w = f->ws<T>(p);
+  if (pb) {                                   // a panel: nrhs right-hand sides, [nrhs][..] vectors
+    w.nrhs = nrhs;
+    w.h = (T*)pb->h; w.z = (T*)pb->z; w.s = (T*)pb->s; w.cv = (T*)pb->cv;
+    w.bv = (T*)pb->bv; w.kv = (T*)pb->kv; w.xs = (T*)pb->xs;
+  }
   const WarpBytes wb = warp_bytes(f->opt.n, f->opt.m, sizeof(T));
   constexpr int NX = NF > 0 ? NF : 4;
   constexpr int MX = MF > 0 ? MF : 2;
@@ -711,6 +833,29 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
     if ((e = launch_groups(rc, TLQR_K_AFF_INIT, fx::kf_aff_init<T, NX, MX>, P->N, G, fx::AiSmem<T, NX, MX>::bytes, st, w, P->N))) return e;
   } else if ((e = launch_warps(rc, TLQR_K_AFF_INIT, k_aff_init<T>, P->N, wb.aff_init, st, w, (int)wb.aff_init))) {
     return e;
+  }
+  auto local_solve = [&]() -> cudaError_t {
+    if constexpr (MF > 0)
+      return launch_groups(rc, TLQR_K_LOCAL_SOLVE, fx::kf_local_solve<T, NX, MX>, P->N, G,
+                           fx::LsSmem<T, NX, MX>::bytes, st, w, P->N);
+    return launch_warps(rc, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w, (int)wb.local_solve);
+  };
+  auto recover = [&]() -> cudaError_t {
+    if constexpr (MF > 0)
+      return launch_groups(rc, TLQR_K_RECOVER, fx::kf_recover<T, NX, MX>, P->N, G, 0, st, w, x, u, y, accumulate,
+                           P->N);
+    return launch_warps(rc, TLQR_K_RECOVER, k_recover<T>, P->N, wb.recover, st, w, x, u, y, accumulate,
+                        (int)wb.recover);
+  };
+  if constexpr (NF > 0) {
+    if (f->aa.plan.n_ops > 0) {
+      // every round of the affine pass in one level-asynchronous launch, the local
+      // solves, every round of the state pass in a second one, the recovery
+      if ((e = launch_async<T, NX>(f, rc, TLQR_K_AFF_TAIL, fx::kf_async_vec<T, NX>, f->aa, 0, w, st))) return e;
+      if ((e = local_solve())) return e;
+      if ((e = launch_async<T, NX>(f, rc, TLQR_K_STATE_TAIL, fx::kf_async_vec<T, NX>, f->sa, 0, w, st))) return e;
+      return recover();
+    }
   }
   const int R = (int)P->rounds.size();
   const int r_tail = NF > 0 ? f->tail_r0 : R;     // rounds [r_tail, R) run in the tail kernel
@@ -723,7 +868,12 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
                                  (int)wb.vec1))) {
       return e;
     }
-    if ((e = launch_warps(rc, TLQR_K_AFF_ABSORB, k_aff_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) return e;
+    if constexpr (NF > 0) {
+      if ((e = launch_groups(rc, TLQR_K_AFF_ABSORB, fx::kf_aff_absorb<T, NX>, ns, G, 0, st, w, rd.seg_begin, ns)))
+        return e;
+    } else if ((e = launch_warps(rc, TLQR_K_AFF_ABSORB, k_aff_absorb<T>, ns, 0, st, w, rd.seg_begin, ns))) {
+      return e;
+    }
     if constexpr (NF > 0) {
       if ((e = launch_groups(rc, TLQR_K_AFF_COMPRESS, fx::kf_aff_compress<T, NX>, nc, G, 0, st, w, rd.comp_begin,
                              nc))) return e;
@@ -747,12 +897,7 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
       return e;
     }
   }
-  if constexpr (MF > 0) {
-    if ((e = launch_groups(rc, TLQR_K_LOCAL_SOLVE, fx::kf_local_solve<T, NX, MX>, P->N, G, fx::LsSmem<T, NX, MX>::bytes, st, w, P->N))) return e;
-  } else if ((e = launch_warps(rc, TLQR_K_LOCAL_SOLVE, k_local_solve<T>, P->N, wb.local_solve, st, w,
-                               (int)wb.local_solve))) {
-    return e;
-  }
+  if ((e = local_solve())) return e;
   for (int ri = 0; ri < r_tail; ++ri) {
     const tlqr_round& rd = P->rounds[ri];
     const int nc = rd.comp_end - rd.comp_begin;
@@ -785,9 +930,7 @@ cudaError_t run_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const dou
                             nr, (int)wb.vec1))) return e;
     }
   }
-  if constexpr (MF > 0)
-    return launch_groups(rc, TLQR_K_RECOVER, fx::kf_recover<T, NX, MX>, P->N, G, 0, st, w, x, u, y, accumulate, P->N);
-  return launch_warps(rc, TLQR_K_RECOVER, k_recover<T>, P->N, wb.recover, st, w, x, u, y, accumulate, (int)wb.recover);
+  return recover();
 }
 
 // FP64 keeps the run-time-n kernels at n = 32 (a row of 32 doubles per lane
@@ -813,13 +956,15 @@ cudaError_t dispatch_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& 
 }
 template <typename T>
 cudaError_t dispatch_solve(tlqr_factor_t* f, Recorder* rc, const double* q, const double* r, const double* c,
-                           double* x, double* u, double* y, int accumulate, cudaStream_t st) {
+                           double* x, double* u, double* y, int accumulate, cudaStream_t st, int nrhs = 1,
+                           const PanelBufs* pb = nullptr) {
 #define X(n_, m_)                                                   \
   if constexpr (fixed_for<T>(n_))                                   \
-    if (f->fixed_n == n_ && f->fixed_m == m_) return run_solve<T, n_, m_>(f, rc, q, r, c, x, u, y, accumulate, st);
+    if (f->fixed_n == n_ && f->fixed_m == m_)                       \
+      return run_solve<T, n_, m_>(f, rc, q, r, c, x, u, y, accumulate, st, nrhs, pb);
   TLQR_FIXED_CASES(X)
 #undef X
-  return run_solve<T, 0, 0>(f, rc, q, r, c, x, u, y, accumulate, st);
+  return run_solve<T, 0, 0>(f, rc, q, r, c, x, u, y, accumulate, st, nrhs, pb);
 }
 
 bool has_fixed_kernels(int n) { return n == 4 || n == 6 || n == 8 || n == 12 || n == 16 || n == 32; }
@@ -1173,16 +1318,26 @@ int async_occupancy() {
   }
   return std::max(1, b);
 }
+template <typename T, int N>
+int async_vec_occupancy() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fx::kf_async_vec<T, N>, 128, 0) != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return std::max(1, b);
+}
+// vec = false: kf_async; true: kf_async_vec
 template <typename T>
-int async_occupancy_n(int n) {
+int async_occupancy_n(int n, bool vec) {
   switch (n) {
-    case 4: return async_occupancy<T, 4>();
-    case 6: return async_occupancy<T, 6>();
-    case 8: return async_occupancy<T, 8>();
-    case 12: return async_occupancy<T, 12>();
-    case 16: return async_occupancy<T, 16>();
+    case 4: return vec ? async_vec_occupancy<T, 4>() : async_occupancy<T, 4>();
+    case 6: return vec ? async_vec_occupancy<T, 6>() : async_occupancy<T, 6>();
+    case 8: return vec ? async_vec_occupancy<T, 8>() : async_occupancy<T, 8>();
+    case 12: return vec ? async_vec_occupancy<T, 12>() : async_occupancy<T, 12>();
+    case 16: return vec ? async_vec_occupancy<T, 16>() : async_occupancy<T, 16>();
     case 32:
-      if constexpr (fixed_for<T>(32)) return async_occupancy<T, 32>();
+      if constexpr (fixed_for<T>(32)) return vec ? async_vec_occupancy<T, 32>() : async_occupancy<T, 32>();
       return 1;
     default: return 1;
   }
@@ -1232,22 +1387,30 @@ int select_kernels(tlqr_factor_t* f) {
   // the run-time-n kernels keep all 32 lanes busy and are faster there.
   if (f->ts == 8 && (n == 6 || n == 12 || n == 32)) f->fixed_n = 0;
   f->fixed_m = (f->fixed_n && has_fixed_pair(n, m)) ? m : 0;
-  f->async = AsyncPlan{};
-  f->async.r0 = (int)f->plan->rounds.size();
-  if (f->fixed_n > 0 && o.async_ops >= 0) {
-    const int thr = o.async_ops > 0 ? o.async_ops : kAsyncOps;
-    int r0 = (int)f->plan->rounds.size();
-    while (r0 > 0) {
-      const tlqr_round& r = f->plan->rounds[r0 - 1];
-      if ((r.rake_end - r.rake_begin) + (r.comp_end - r.comp_begin) > thr) break;
-      --r0;
+  f->fa = DevAsync{};
+  f->aa = DevAsync{};
+  f->sa = DevAsync{};
+  f->fa.plan.r0 = (int)f->plan->rounds.size();
+  const int G = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+  try {
+    if (f->fixed_n > 0 && o.async_ops >= 0) {
+      const int thr = o.async_ops > 0 ? o.async_ops : kAsyncOps;
+      int r0 = (int)f->plan->rounds.size();
+      while (r0 > 0) {
+        const tlqr_round& r = f->plan->rounds[r0 - 1];
+        if ((r.rake_end - r.rake_begin) + (r.comp_end - r.comp_begin) > thr) break;
+        --r0;
+      }
+      f->fa.plan = build_async(f->plan, r0, 32 / G);
     }
-    const int G = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
-    try {
-      f->async = build_async(f->plan, r0, 32 / G);
-    } catch (const std::bad_alloc&) {
-      return 1;
+    // right-hand-side passes: the affine pass has the dependency structure of the
+    // whole factorisation (every round), the state pass its own list
+    if (f->fixed_n > 0 && o.async_solve > 0 && !f->plan->rounds.empty()) {
+      f->aa.plan = build_async(f->plan, 0, 32 / G);
+      f->sa.plan = build_async_state(f->plan, 32 / G);
     }
+  } catch (const std::bad_alloc&) {
+    return 1;
   }
   return 0;
 }
@@ -1349,8 +1512,12 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
     delete f;
     return TLQR_ERR_CUDA;
   }
-  if (f->async.n_ops > 0)
-    f->async_blocks = f->sms * (f->ts == 8 ? async_occupancy_n<double>(n) : async_occupancy_n<float>(n));
+  if (f->fa.plan.n_ops > 0)
+    f->fa.blocks = f->sms * (f->ts == 8 ? async_occupancy_n<double>(n, false) : async_occupancy_n<float>(n, false));
+  if (f->aa.plan.n_ops > 0) {
+    f->aa.blocks = f->sa.blocks =
+        f->sms * (f->ts == 8 ? async_occupancy_n<double>(n, true) : async_occupancy_n<float>(n, true));
+  }
   Carve sizing;
   carve_factor(f, sizing);
   void* arena = nullptr;
@@ -1394,13 +1561,13 @@ extern "C" int tlqr_factor_workspace_bytes(const tlqr_plan_t* plan, const tlqr_o
   return TLQR_OK;
 }
 
-extern "C" int tlqr_async_schedule(const tlqr_plan_t* plan, int32_t n, int32_t async_ops, int32_t* counts,
-                                   int32_t* kind, int32_t* node, int32_t* round, int32_t* dep_flag,
+extern "C" int tlqr_async_schedule(const tlqr_plan_t* plan, int32_t n, int32_t which, int32_t async_ops,
+                                   int32_t* counts, int32_t* kind, int32_t* node, int32_t* round, int32_t* dep_flag,
                                    int32_t* dep_target, int32_t* signal) {
-  if (!plan || !counts || n < 1 || n > TLQR_MAX_DIM) return TLQR_ERR_ARG;
+  if (!plan || !counts || n < 1 || n > TLQR_MAX_DIM || which < 0 || which > 2) return TLQR_ERR_ARG;
   const int R = (int)plan->rounds.size();
-  int r0 = R;
-  if (async_ops >= 0) {
+  int r0 = which == 0 ? R : 0;
+  if (which == 0 && async_ops >= 0) {
     const int thr = async_ops > 0 ? async_ops : kAsyncOps;
     while (r0 > 0) {
       const tlqr_round& r = plan->rounds[r0 - 1];
@@ -1411,7 +1578,7 @@ extern "C" int tlqr_async_schedule(const tlqr_plan_t* plan, int32_t n, int32_t a
   const int G = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
   AsyncPlan A;
   try {
-    A = build_async(plan, r0, 32 / G);
+    A = which == 2 ? build_async_state(plan, 32 / G) : build_async(plan, r0, 32 / G);
   } catch (const std::bad_alloc&) {
     return TLQR_ERR_OOM;
   }
@@ -1425,7 +1592,7 @@ extern "C" int tlqr_async_schedule(const tlqr_plan_t* plan, int32_t n, int32_t a
     kind[p] = k;
     int v = -1, rr = 0;
     if (idx != fx::kAsyncPad) {
-      if (k == fx::AK_RAKE) { v = plan->rake_leaf[idx]; rr = plan->round_of_node[v]; }
+      if (k == fx::AK_RAKE || k == fx::SK_EXPAND_R) { v = plan->rake_leaf[idx]; rr = plan->round_of_node[v]; }
       else if (k == fx::AK_ABSORB) { v = plan->seg_parent[idx]; rr = seg_round[idx]; }
       else { v = plan->comp_j[idx]; rr = plan->round_of_node[v]; }
     }
@@ -1437,6 +1604,12 @@ extern "C" int tlqr_async_schedule(const tlqr_plan_t* plan, int32_t n, int32_t a
     }
     if (signal) signal[p] = A.signal[p];
   }
+  return TLQR_OK;
+}
+
+extern "C" int tlqr_factor_options(const tlqr_factor_t* f, tlqr_options* out) {
+  if (!f || !out) return TLQR_ERR_ARG;
+  *out = f->opt;
   return TLQR_OK;
 }
 
@@ -1494,6 +1667,54 @@ extern "C" int tlqr_solve_rhs(tlqr_factor_t* f, int32_t mem, const double* q, co
   if (!e) e = cudaStreamSynchronize(st);
   f->prof.harvest();
   return e ? TLQR_ERR_CUDA : TLQR_OK;
+}
+
+extern "C" int tlqr_solve_rhs_panel(tlqr_factor_t* f, int32_t nrhs, const double* q, const double* r,
+                                    const double* c, double* x, double* u, double* y, void* stream) {
+  if (!f || nrhs < 1 || !q || !r || !c || !x || !u || !y) return TLQR_ERR_ARG;
+  if (!f->factored) return TLQR_ERR_STATE;
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  const size_t sv = N * n, sm = N * m;
+  // the panel kernels: compile-time (n, m)
+  const bool panel = f->fixed_m > 0;
+  if (!panel) {
+    for (int k = 0; k < nrhs; ++k)
+      if (solve_impl(f, q + k * sv, r + k * sm, c + k * sv, x + k * sv, u + k * sm, y + k * sv, 0, st))
+        return TLQR_ERR_CUDA;
+  } else {
+    if (!f->panel_mem) {
+      const size_t ts = f->ts, nrake = std::max<size_t>(1, f->plan->rake_leaf.size());
+      Carve c0;
+      const size_t sizes[7] = {sv, sv, sv, nrake * n, sv, sm, sv};
+      for (size_t b : sizes) c0.take(b * kPanel * ts);
+      void* mem = nullptr;
+      if (cudaMalloc(&mem, c0.off)) { cudaGetLastError(); return TLQR_ERR_OOM; }
+      f->panel_mem = mem;
+      Carve c1;
+      c1.base = static_cast<unsigned char*>(mem);
+      void** slots[7] = {&f->panel.h, &f->panel.z, &f->panel.s, &f->panel.cv, &f->panel.bv, &f->panel.kv,
+                         &f->panel.xs};
+      for (int t = 0; t < 7; ++t) *slots[t] = c1.take(sizes[t] * kPanel * ts);
+    }
+    for (int k0 = 0; k0 < nrhs; k0 += kPanel) {
+      const int kc = std::min(kPanel, nrhs - k0);
+      Recorder rcd;
+      rcd.mask = f->prof.mask;
+      rcd.pool = &f->prof.pool;
+      cudaError_t e = f->ts == 8
+          ? dispatch_solve<double>(f, &rcd, q + k0 * sv, r + k0 * sm, c + k0 * sv, x + k0 * sv, u + k0 * sm,
+                                   y + k0 * sv, 0, st, kc, &f->panel)
+          : dispatch_solve<float>(f, &rcd, q + k0 * sv, r + k0 * sm, c + k0 * sv, x + k0 * sv, u + k0 * sm,
+                                  y + k0 * sv, 0, st, kc, &f->panel);
+      f->prof.add(rcd, true);
+      if (e) return TLQR_ERR_CUDA;
+    }
+  }
+  int rc = read_status(f, st);
+  f->prof.harvest();
+  return rc;
 }
 
 namespace {

@@ -54,6 +54,13 @@ def problem_bytes(N: int, n: int, m: int, has_delta: bool) -> int:
     return 8 * N * per
 
 
+def ipm_bytes(N: int, n: int, m: int) -> int:
+    """Device bytes of an interior-point request beyond its problem and solution:
+    bounds and multipliers ([N][m] each) and the driver's workspace (Newton
+    system R~, r~, the Newton point and the step directions)."""
+    return 8 * N * (4 * m + m * m + 5 * m + 2 * n) + N
+
+
 def solution_bytes(N: int, n: int, m: int) -> int:
     return 8 * N * (2 * n + m)
 
@@ -61,7 +68,12 @@ def solution_bytes(N: int, n: int, m: int) -> int:
 @dataclass
 class Request:
     """parent: topology; data(it, stream) -> problem dict of device tensors
-    for solve `it` (0 <= it < iterations), created on `stream`."""
+    for solve `it` (0 <= it < iterations), created on `stream`.
+
+    With bounds(stream) -> (u_lo, u_hi) set, the request is one box-constrained
+    problem solved by the interior-point driver (tlqr_ipm_box) with a budget of
+    `iterations` Newton solves; data(0, stream) gives its data and each Newton
+    system is formed on the device by the driver itself."""
     parent: np.ndarray
     n: int
     m: int
@@ -70,6 +82,7 @@ class Request:
     precision: int = tlqr.TLQR_PREC_MIXED
     has_delta: bool = False
     tag: object = None
+    bounds: Callable | None = None
     # filled by the server
     arrival: float = 0.0
     admitted: float = 0.0
@@ -132,6 +145,23 @@ class TlqrBackend:
         with self.torch.cuda.stream(stream):
             tlqr.tlqr_solve(f, data, x, u, y, stream=stream)
         return tlqr.tlqr_last_info(f)
+
+    def ipm(self, plan, f, data, lo, hi, x, u, y, max_iter, stream):
+        """Interior-point driver with a fixed Newton budget; reaching the budget
+        before the gap tolerance is a normal end for a real-time request."""
+        t = self.torch
+        t.cuda.set_device(self.device)
+        ll, lh = t.zeros_like(u), t.zeros_like(u)
+        with t.cuda.stream(stream):
+            try:
+                info = tlqr.tlqr_ipm_box(plan, f, data, lo, hi, x, u, y, ll, lh, max_iter=max_iter,
+                                         no_fp64_fallback=True, stream=stream)
+                info["budget_exhausted"] = False
+            except tlqr.TLQRError as e:
+                if e.code != 8:                     # TLQR_ERR_NO_CONVERGENCE: the budget ran out
+                    raise
+                info = {"budget_exhausted": True}
+        return info
 
     def synchronize(self, stream):
         stream.synchronize()
@@ -250,6 +280,8 @@ class Server:
                 key, ent, opts = req._prep
                 okey = (key, req.n, req.m, req.precision, req.has_delta)
                 bufs = solution_bytes(req.N, req.n, req.m) + problem_bytes(req.N, req.n, req.m, req.has_delta)
+                if req.bounds is not None:
+                    bufs += ipm_bytes(req.N, req.n, req.m)
                 reuse = bool(self.idle.get(okey))
                 wbytes = 0 if reuse else self.backend.workspace_bytes(ent[0], opts)
                 need = wbytes + bufs
@@ -295,9 +327,14 @@ class Server:
                 if factor is None:
                     factor = self.backend.create_factor(ent[0], opts)
                 x, u, y = self.backend.outputs(req)
-                for it in range(req.iterations):
-                    data = req.data(it, stream)
-                    req.infos.append(self.backend.solve(factor, data, x, u, y, stream))
+                if req.bounds is not None:
+                    lo, hi = req.bounds(stream)
+                    req.infos.append(self.backend.ipm(ent[0], factor, req.data(0, stream), lo, hi, x, u, y,
+                                                      req.iterations, stream))
+                else:
+                    for it in range(req.iterations):
+                        data = req.data(it, stream)
+                        req.infos.append(self.backend.solve(factor, data, x, u, y, stream))
                 self.backend.synchronize(stream)
                 req.x, req.u, req.y = x, u, y
             except BaseException as e:

@@ -43,7 +43,7 @@ class tlqr_options(ctypes.Structure):
     _fields_ = [("n", _i32), ("m", _i32), ("precision", _i32), ("has_M", _i32), ("has_delta", _i32),
                 ("max_refine", _i32), ("refine_tol", ctypes.c_double), ("use_graphs", _i32),
                 ("generic_kernels", _i32), ("async_ops", _i32), ("spin_limit", _i32), ("test_withhold", _i32),
-                ("reserved", _i32 * 3)]
+                ("tail_ops", _i32), ("async_solve", _i32), ("reserved", _i32 * 1)]
 
 
 class tlqr_problem(ctypes.Structure):
@@ -57,12 +57,17 @@ class tlqr_solution(ctypes.Structure):
 
 class tlqr_ipm_options(ctypes.Structure):
     _fields_ = [("max_iter", _i32), ("mu0", ctypes.c_double), ("sigma", ctypes.c_double), ("tau", ctypes.c_double),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("no_fp64_fallback", _i32)]
 
 
 class tlqr_ipm_info(ctypes.Structure):
     _fields_ = [("iterations", _i32), ("mu", ctypes.c_double), ("mean_gap", ctypes.c_double),
-                ("last_alpha", ctypes.c_double), ("last_eta", ctypes.c_double)]
+                ("last_alpha", ctypes.c_double), ("last_eta", ctypes.c_double), ("fp64_solves", _i32)]
+
+
+class tlqr_autotune_entry(ctypes.Structure):
+    _fields_ = [("async_ops", _i32), ("async_solve", _i32), ("tail_ops", _i32), ("status", _i32),
+                ("ms", ctypes.c_double)]
 
 
 class tlqr_plan_stats_t(ctypes.Structure):
@@ -89,7 +94,8 @@ EXPORTS = ["tlqr_plan_create", "tlqr_plan_create_forest", "tlqr_plan_destroy", "
            "tlqr_kkt_residual_noalloc", "tlqr_profile_launches", "tlqr_tree_residuals",
            "tlqr_factor_workspace_bytes", "tlqr_factor_bytes", "tlqr_async_schedule", "tlqr_solve_adjoint",
            "tlqr_lift_node_controls_device", "tlqr_project_lifted_device", "tlqr_factor_dims", "tlqr_ipm_box",
-           "tlqr_pipe_peak"]
+           "tlqr_pipe_peak", "tlqr_solve_rhs_panel",
+           "tlqr_factor_options", "tlqr_autotune"]
 
 KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
                 "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
@@ -131,11 +137,16 @@ def lib():
                                                      + [_ip, _vp])
         L.tlqr_project_lifted_device.argtypes = [_i32, _i32, _i32, _ip] + [_dp] * 6 + [_vp]
         L.tlqr_factor_dims.argtypes = [_vp, _ip]
+        L.tlqr_autotune.argtypes = [_vp, ctypes.POINTER(tlqr_options), ctypes.POINTER(tlqr_problem), _i32,
+                                    ctypes.POINTER(tlqr_options), ctypes.POINTER(tlqr_autotune_entry), _i32, _ip,
+                                    _vp]
+        L.tlqr_factor_options.argtypes = [_vp, ctypes.POINTER(tlqr_options)]
+        L.tlqr_solve_rhs_panel.argtypes = [_vp, _i32] + [_dp] * 6 + [_vp]
         L.tlqr_pipe_peak.argtypes = [_i32, _dp, _vp]
         L.tlqr_ipm_box.argtypes = ([_vp, _vp, ctypes.POINTER(tlqr_problem), _dp, _dp, ctypes.POINTER(tlqr_ipm_options)]
                                    + [_dp] * 5 + [ctypes.POINTER(tlqr_ipm_info), _vp])
         L.tlqr_solve_adjoint.argtypes = [_vp, _i32] + [_dp] * 6 + [_vp]
-        L.tlqr_async_schedule.argtypes = [_vp, _i32, _i32] + [_ip] * 7
+        L.tlqr_async_schedule.argtypes = [_vp, _i32, _i32, _i32] + [_ip] * 7
         L.tlqr_batched_expand.argtypes = [_i32, _i32] + [_dp] * 5 + [_i32, _vp]
         L.tlqr_batched_local_factor.argtypes = [_i32, _i32, _i32] + [_dp] * 8 + [_i32, _vp]
         L.tlqr_batched_compose_T.argtypes = [_i32, _i32] + [_dp] * 3 + [_i32, _vp]
@@ -249,8 +260,9 @@ def tlqr_plan_schedule(plan, N: int):
 
 def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
                  refine_tol=1e-8, use_graphs=True, generic_kernels=False, async_ops=0, spin_limit=0,
-                 test_withhold=False) -> tlqr_options:
+                 test_withhold=False, tail_ops=0, async_solve=0) -> tlqr_options:
     o = tlqr_options()
+    o.tail_ops, o.async_solve = int(tail_ops), int(async_solve)
     o.generic_kernels = int(bool(generic_kernels))
     o.async_ops, o.spin_limit, o.test_withhold = int(async_ops), int(spin_limit), int(bool(test_withhold))
     o.n, o.m, o.precision = int(n), int(m), int(precision)
@@ -314,6 +326,12 @@ def tlqr_solve_rhs(f, q, r, c, x, u, y, stream=None) -> None:
                                 _stream(stream)), "tlqr_solve_rhs")
 
 
+def tlqr_solve_rhs_panel(f, q, r, c, x, u, y, stream=None) -> None:
+    """nrhs right-hand sides at once: q, c, x, y [nrhs, N, n]; r, u [nrhs, N, m] (CUDA tensors)."""
+    _check(lib().tlqr_solve_rhs_panel(f, int(q.shape[0]), *[_ptr(a) for a in (q, r, c, x, u, y)], _stream(stream)),
+           "tlqr_solve_rhs_panel")
+
+
 def tlqr_solve_adjoint(f, xbar, ubar, ybar, qbar, rbar, cbar, stream=None) -> None:
     """Gradient of a loss with respect to (q, r, c) from its gradient with respect to (x, u, y)."""
     mem = _mem_all([xbar, ubar, ybar, qbar, rbar, cbar])
@@ -328,6 +346,19 @@ def tlqr_pipe_peak(precision, stream=None) -> float:
     return v.value
 
 
+def tlqr_autotune(plan, opts: tlqr_options, data: dict, trials: int = 5, stream=None):
+    """Time the candidate execution shapes; returns (best options, table rows)."""
+    p = make_problem(data)
+    best = tlqr_options()
+    table = (tlqr_autotune_entry * 32)()
+    cnt = np.zeros(1, dtype=np.int32)
+    _check(lib().tlqr_autotune(plan, ctypes.byref(opts), ctypes.byref(p), int(trials), ctypes.byref(best), table,
+                               32, _iptr(cnt), _stream(stream)), "tlqr_autotune")
+    rows = [dict(async_ops=t.async_ops, async_solve=t.async_solve, tail_ops=t.tail_ops, status=t.status, ms=t.ms)
+            for t in table[:int(cnt[0])]]
+    return best, rows
+
+
 def tlqr_factor_dims(f):
     d = np.zeros(3, dtype=np.int32)
     _check(lib().tlqr_factor_dims(f, _iptr(d)), "tlqr_factor_dims")
@@ -335,16 +366,16 @@ def tlqr_factor_dims(f):
 
 
 def tlqr_ipm_box(plan, f, data: dict, u_lo, u_hi, x, u, y, lam_lo, lam_hi, max_iter=0, mu0=0.0, sigma=0.0, tau=0.0,
-                 tol=0.0, stream=None) -> dict:
+                 tol=0.0, no_fp64_fallback=False, stream=None) -> dict:
     """Box-constrained tree LQR by the primal-dual interior-point driver (device arrays)."""
     p = make_problem(data)
-    o = tlqr_ipm_options(int(max_iter), float(mu0), float(sigma), float(tau), float(tol))
+    o = tlqr_ipm_options(int(max_iter), float(mu0), float(sigma), float(tau), float(tol), int(bool(no_fp64_fallback)))
     info = tlqr_ipm_info()
     _check(lib().tlqr_ipm_box(plan, f, ctypes.byref(p), _ptr(u_lo), _ptr(u_hi), ctypes.byref(o), _ptr(x), _ptr(u),
                               _ptr(y), _ptr(lam_lo), _ptr(lam_hi), ctypes.byref(info), _stream(stream)),
            "tlqr_ipm_box")
     return dict(iterations=info.iterations, mu=info.mu, mean_gap=info.mean_gap, last_alpha=info.last_alpha,
-                last_eta=info.last_eta)
+                last_eta=info.last_eta, fp64_solves=info.fp64_solves)
 
 
 def tlqr_get_PK(f, P, K, stream=None) -> None:
@@ -453,19 +484,20 @@ def tlqr_batched_compose_T(Tk, Tj, out, precision=TLQR_PREC_FP64, stream=None) -
            "tlqr_batched_compose_T")
 
 
-def tlqr_async_schedule(plan, n: int, async_ops: int = 0) -> dict:
-    """Operation list of the level-asynchronous factorisation tail (host only)."""
+def tlqr_async_schedule(plan, n: int, async_ops: int = 0, which: int = 0) -> dict:
+    """Operation list of a level-asynchronous launch (host only): which = 0 the
+    factorisation tail, 1 the affine pass, 2 the state pass."""
     counts = np.zeros(4, dtype=np.int32)
     ip = lambda a: a.ctypes.data_as(ctypes.POINTER(_i32))
     L = lib()
     nul = ctypes.POINTER(_i32)()
-    _check(L.tlqr_async_schedule(plan, int(n), int(async_ops), ip(counts), nul, nul, nul, nul, nul, nul),
+    _check(L.tlqr_async_schedule(plan, int(n), int(which), int(async_ops), ip(counts), nul, nul, nul, nul, nul, nul),
            "tlqr_async_schedule")
     P = int(counts[1])
     out = dict(r0=int(counts[0]), n_ops=P, n_flags=int(counts[2]), levels=int(counts[3]))
     arr = {k: np.zeros(max(1, P) * (3 if k.startswith("dep") else 1), dtype=np.int32)
            for k in ("kind", "node", "round", "dep_flag", "dep_target", "signal")}
-    _check(L.tlqr_async_schedule(plan, int(n), int(async_ops), ip(counts), *[ip(arr[k]) for k in
+    _check(L.tlqr_async_schedule(plan, int(n), int(which), int(async_ops), ip(counts), *[ip(arr[k]) for k in
                                  ("kind", "node", "round", "dep_flag", "dep_target", "signal")]),
            "tlqr_async_schedule")
     for k, v in arr.items():

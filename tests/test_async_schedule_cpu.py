@@ -21,6 +21,7 @@ from oracle import plan as oplan
 from paper_2608_01332_b300 import inputs, tlqr
 
 RAKE, ABSORB, COMPRESS, EXPAND = 0, 1, 2, 3
+COMPOSE_S, EXPAND_C, EXPAND_R = 4, 5, 6           # state pass
 
 
 def _reference(parent, r0):
@@ -94,7 +95,39 @@ def _hazards(parent, r0):
     return need
 
 
-def _check_hazards_implied(parent, s):
+def _state_hazards(parent):
+    """The state pass in the reference order: offset compositions b_k <- Tr_j
+    b_j + b_k in forward round order, then per round in reverse order the
+    state expansions x_j = T_j x_i + b_j of the compressed centres and then of
+    the raked leaves; b and a root's x exist before the pass."""
+    rounds = oplan.structural_schedule(parent)
+    writer, readers, need = {}, defaultdict(list), defaultdict(set)
+
+    def read(key, d):
+        if d in writer:
+            need[key].add(writer[d])
+        readers[d].append(key)
+
+    def write(key, d):
+        need[key].update(r for r in readers[d] if r != key)
+        readers[d] = []
+        writer[d] = key
+
+    for rd in rounds:
+        for j, i, k in rd["compresses"]:
+            key = (COMPOSE_S, j)
+            read(key, ("b", j)); read(key, ("b", k)); write(key, ("b", k))
+    for rd in reversed(rounds):
+        for j, i, k in rd["compresses"]:
+            key = (EXPAND_C, j)
+            read(key, ("b", j)); read(key, ("x", i)); write(key, ("x", j))
+        for j, i in rd["rakes"]:
+            key = (EXPAND_R, j)
+            read(key, ("b", j)); read(key, ("x", i)); write(key, ("x", j))
+    return need
+
+
+def _check_hazards_implied(parent, s, need=None):
     """Every hazard of the reference order is an ancestor in the list's DAG."""
     P = s["n_ops"]
     kind, node, rnd = s["kind"], s["node"], s["round"]
@@ -120,7 +153,10 @@ def _check_hazards_implied(parent, s):
             for q in preds:
                 a |= anc[q] | (1 << q)
         anc[p] = a
-    for key, want in _hazards(parent, s["r0"]).items():
+    if need is None:
+        need = _hazards(parent, s["r0"])
+    assert sorted(pos_of) == sorted(set(need) | {k for k in pos_of})
+    for key, want in need.items():
         p = pos_of[key]
         for w in want:
             assert (anc[p] >> pos_of[w]) & 1, f"{key} may run before {w}"
@@ -246,3 +282,56 @@ def test_async_levels_at_most_twice_the_rounds():
     finally:
         tlqr.tlqr_plan_destroy(plan)
     assert 0 < s["levels"] <= 4 * R
+
+
+@pytest.mark.parametrize("tree", _trees(), ids=lambda t: t[0])
+@pytest.mark.parametrize("n", [4, 12, 32])
+def test_state_pass_list(tree, n):
+    """The state pass's list: every operation of the reference once, every
+    hazard implied by the DAG, one kind per warp, dependencies on earlier
+    warps only, and an adversarial execution that never stalls."""
+    name, parent = tree
+    forest = (np.asarray(parent) < 0).sum() > 1
+    plan = tlqr.tlqr_plan_create_forest(parent) if forest else tlqr.tlqr_plan_create(parent)
+    try:
+        s = tlqr.tlqr_async_schedule(plan, n, which=2)
+        a = tlqr.tlqr_async_schedule(plan, n, which=1)
+        f = tlqr.tlqr_async_schedule(plan, n, async_ops=1 << 30, which=0)
+    finally:
+        tlqr.tlqr_plan_destroy(plan)
+    # the affine pass runs the factorisation's list over every round
+    for k in ("kind", "node", "round", "dep_flag", "dep_target", "signal"):
+        np.testing.assert_array_equal(a[k], f[k])
+    need = _state_hazards(parent)
+    P = s["n_ops"]
+    G = 4 if n <= 4 else 8 if n <= 8 else 16 if n <= 16 else 32
+    W = 32 // G
+    keys = sorted((int(s["kind"][p]), int(s["node"][p])) for p in range(P) if s["node"][p] >= 0)
+    assert keys == sorted(need)
+    for b in range(0, P, W):
+        assert len(set(s["kind"][b:b + W].tolist())) == 1 and s["node"][b] >= 0
+        for p in range(b, b + W):
+            assert all(f < b for f in s["dep_flag"][p] if f >= 0)
+    _check_hazards_implied(parent, s, need)
+    # execute latest-ready-first under the list's own flags: everything runs
+    done = np.zeros(P, dtype=bool)
+    ready = [p for p in range(P) if s["node"][p] >= 0 and all(f < 0 for f in s["dep_flag"][p])]
+    waiting = defaultdict(list)
+    missing = {}
+    for p in range(P):
+        if s["node"][p] < 0:
+            continue
+        fl = [int(f) for f in s["dep_flag"][p] if f >= 0]
+        missing[p] = len(fl)
+        for f in fl:
+            waiting[f].append(p)
+    count = 0
+    while ready:
+        p = ready.pop(int(np.argmax(ready)))
+        done[p] = True
+        count += 1
+        for q in waiting[p]:
+            missing[q] -= 1
+            if missing[q] == 0:
+                ready.append(q)
+    assert count == len(missing)

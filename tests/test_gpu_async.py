@@ -115,3 +115,40 @@ def test_async_wait_that_runs_out_reports_timeout_and_context_survives(n, m):
     out, _ = solve(p, n, m, data, MIXED, async_ops=1 << 30)
     ref = riccati.tree_riccati(p, n, m, data)
     assert riccati.forward_error(out, ref, p) <= 1e-6
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_async_solve_passes_match_round_by_round(case, precision):
+    """The affine and state passes of the right-hand side, each one
+    level-asynchronous launch over every round, give the solution of the
+    round-by-round passes (same per-operation arithmetic)."""
+    name, p, n, m, d, forest = case
+    if precision == FP64 and n == 32:
+        pytest.skip("FP64 at n = 32 runs the run-time-n kernels")
+    a, _ = solve(p, n, m, d, precision, forest=forest, async_ops=-1, async_solve=1)
+    b, _ = solve(p, n, m, d, precision, forest=forest, async_ops=-1, async_solve=-1)
+    tol = 1e-12 if precision == FP64 else 1e-9
+    for k in ("x", "u", "y"):
+        assert np.abs(a[k] - b[k]).max() <= tol * max(1.0, np.abs(b[k]).max()), k
+
+
+def test_async_solve_is_two_launches_per_pass():
+    rng = inputs.rng_for(904)
+    p = inputs.long_trunk_tree(rng, trunk=300, total=3000)
+    n, m = 12, 4
+    d = {k: dev(v) for k, v in inputs.problem_data(p, n, m, rng).items()}
+    N = len(p)
+    s = tlqr.TreeLQR(p, n, m, MIXED, use_graphs=False, async_solve=1)
+    try:
+        tlqr.tlqr_factor(s.f, d)
+        tlqr.tlqr_profile_read(s.f)
+        out = [torch.zeros(sh, dtype=torch.float64, device="cuda") for sh in ((N, n), (N, m), (N, n))]
+        tlqr.tlqr_solve_rhs(s.f, d["q"], d["r"], d["c"], *out)
+        torch.cuda.synchronize()
+        prof = tlqr.tlqr_profile_read(s.f)
+    finally:
+        s.close()
+    assert prof["aff_tail"]["launches"] == 1 and prof["state_tail"]["launches"] == 1
+    for k in ("aff_rake", "aff_absorb", "aff_compress", "aff_expand", "state_compress", "state_expand"):
+        assert prof[k]["launches"] == 0, k

@@ -139,7 +139,7 @@ def test_batch_full_size_mixed(batch):
         assert riccati.forward_error(got, ref, p) <= 1e-6, t
 
 
-@pytest.mark.parametrize("kappa", [1e2, 1e8])
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6, 1e8])
 def test_spine_full_size(kappa):
     w = inputs.spine_hybrid_device("cuda", kappa_R=kappa)
     N = len(w.parent)
@@ -170,3 +170,18 @@ def test_spine_full_size(kappa):
         if checked == 40:
             break
     assert checked >= 20
+
+
+def test_spine_n32_mixed_elementwise_against_the_oracle():
+    """The n = 32 mixed path (3xTF32 tensor-core block products, Gauss-Jordan
+    eliminations, float-float refinement) on a 2^14-node spine hybrid: x, u and
+    y element by element against the FP64 oracle's whole-tree solve."""
+    w = inputs.spine_hybrid_device("cuda", N=1 << 14, spine=1 << 10)
+    out = solve(w, MIXED, want_PK=False)
+    assert out["info"]["eta"] <= 1e-8
+    d = host(w.data, np.arange(len(w.parent)))
+    ref = riccati.tree_riccati(w.parent, w.n, w.m, d)
+    got = {k: out[k].cpu().numpy() for k in ("x", "u", "y")}
+    assert riccati.forward_error(got, ref, w.parent) <= 1e-6
+    for k in ("x", "u", "y"):
+        assert np.abs(got[k] - ref[k]).max() <= 1e-6 * max(1.0, np.abs(ref[k]).max()), k

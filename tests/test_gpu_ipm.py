@@ -78,8 +78,8 @@ def test_ipm_on_a_driving_tree(precision):
     nonroot = np.asarray(p) >= 0
     assert np.all(got["u"][nonroot] >= lo[nonroot]) and np.all(got["u"][nonroot] <= hi[nonroot])
     assert np.all(got["lam_lo"] >= 0) and np.all(got["lam_hi"] >= 0)
-    comp = np.maximum(np.abs(got["lam_lo"] * (got["u"] - lo))[nonroot].max(),
-                      np.abs(got["lam_hi"] * (hi - got["u"]))[nonroot].max())
+    comp = np.maximum(np.abs(got["lam_lo"][nonroot] * (got["u"][nonroot] - lo[nonroot])).max(),
+                      np.abs(got["lam_hi"][nonroot] * (hi[nonroot] - got["u"][nonroot])).max())
     assert comp <= 1e-8
     active = ((np.abs(got["u"] - lo) < 1e-6) | (np.abs(got["u"] - hi) < 1e-6))[nonroot]
     assert active.sum() > 10
@@ -88,7 +88,7 @@ def test_ipm_on_a_driving_tree(precision):
     d2["r"] = d["r"] - got["lam_lo"] + got["lam_hi"]
     d2["r"][~nonroot] = 0.0
     res = riccati.kkt_residual(p, n, m, d2, got["x"], got["u"], got["y"])
-    # the last Newton matrix holds l / s ~ 1 / tol on the diagonal of active rows, so
-    # those rows carry a rounding error of about eps / tol relative to the data
-    assert res["eta"] <= 1e-6
+    # the multipliers are recovered from the control rows at convergence: stationarity
+    # holds to rounding, complementarity at the gap's scale (checked above)
+    assert res["eta"] <= 1e-12
     assert info["iterations"] < 60

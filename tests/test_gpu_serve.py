@@ -16,9 +16,14 @@ import bench  # noqa: E402
 
 
 @pytest.mark.parametrize("precision", [tlqr.TLQR_PREC_MIXED, tlqr.TLQR_PREC_FP64])
-def test_alone_equals_in_the_mix(precision):
+@pytest.mark.parametrize("mode", ["perturb", "ipm"])
+def test_alone_equals_in_the_mix(precision, mode):
+    """Every request of a concurrent mix equals the same request run alone,
+    bitwise: perturbed-data re-solves, and interior-point requests (whose
+    Newton systems the driver forms on the device)."""
     dev = torch.device("cuda", 0)
-    traffic = bench.ServeTraffic(dev, topologies=5, iterations=4, lo=300, hi=6000)
+    traffic = bench.ServeTraffic(dev, topologies=5, iterations=4 if mode == "perturb" else 12, lo=300, hi=6000,
+                                 ipm=mode == "ipm")
     topo = [k % 5 for k in range(14)]
     srv = serve.Server(slots=4)
     mix = [srv.submit(traffic.request(k, precision, t=topo[k])) for k in range(14)]
@@ -34,6 +39,8 @@ def test_alone_equals_in_the_mix(precision):
         assert a.error is None
         for name in ("x", "u", "y"):
             assert torch.equal(getattr(r, name), getattr(a, name)), (k, name)
-        if precision == tlqr.TLQR_PREC_MIXED:
+        if mode == "ipm":
+            assert r.infos == a.infos
+        elif precision == tlqr.TLQR_PREC_MIXED:
             assert max(i["eta"] for i in r.infos) <= 1e-8
             assert [i["refine_steps"] for i in r.infos] == [i["refine_steps"] for i in a.infos]
