@@ -96,12 +96,16 @@ typedef struct {
                             launch ordered by the dependency levels of
                             eq. (earliest-level) instead of round by round.
                             0 = the library's default (1024), < 0 = off            */
-  int32_t spin_limit;    /* polls of one dependency wait of that launch before it
+  int32_t spin_limit;    /* polls of one dependency wait of that launch, and of one
+                            mbarrier wait of the node-organised residual, before it
                             gives up with TLQR_ERR_TIMEOUT (0 = default, about a
-                            second with backoff)                                   */
-  int32_t test_withhold; /* testing failure detection only: 1 = the first operation of
-                            the level-asynchronous launch never signals completion, so
-                            the waits that depend on it run out (TLQR_ERR_TIMEOUT)    */
+                            second or more)                                        */
+  int32_t test_withhold; /* testing failure detection only (bits): 1 = the first
+                            operation of the level-asynchronous launch never signals
+                            completion, so the waits that depend on it run out; 2 = the
+                            node-organised residual announces its first node's bulk
+                            copies and issues none, so that mbarrier wait runs out.
+                            Either way the call returns TLQR_ERR_TIMEOUT              */
   int32_t tail_ops;      /* right-hand-side passes: the rounds from the first one after
                             which every phase holds at most this many operations run in
                             one single-block launch per pass (0 = default 128, < 0 =
@@ -112,7 +116,11 @@ typedef struct {
                             dependency DAG of eq. (earliest-level) applied to the
                             passes of Sec. VI-VII); 0 (default) or < 0 = round by
                             round with the single-block tail of tail_ops            */
-  int32_t reserved[1];
+  int32_t residual;      /* MIXED refinement residual kernels: 1 = one KKT row per
+                            thread; 2 = one node per lane group, the node's FP64
+                            blocks staged by bulk copies (TMA), compile-time (n, m)
+                            and 16-byte aligned matrix arrays only (else 1);
+                            0 = the library's choice for n                       */
 } tlqr_options;
 
 #define TLQR_MAX_DIM 64
@@ -552,17 +560,18 @@ int tlqr_ipm_box(const tlqr_plan_t *plan, tlqr_factor_t *f, const tlqr_problem *
  * current device: every combination of async_ops in {-1 (off), 256, 1024,
  * 4096} with the right-hand-side passes level-asynchronous (async_solve = 1)
  * or round by round with a single-block tail of tail_ops in {-1 (none), 64,
- * 128, 512}.  Each
+ * 128, 512}; then, in mixed precision with base->residual = 0, the fastest
+ * of those with residual = 1 and residual = 2.  Each
  * candidate gets a factor object of its own (created and freed in turn, so
  * only one workspace is held at a time), one warm-up tlqr_solve and `trials`
  * timed ones (CUDA events on `stream`, median).  *best receives `base` with the
- * fastest candidate's three fields; table (may be NULL) up to max_entries
+ * fastest candidate's four fields; table (may be NULL) up to max_entries
  * rows, *n_entries the number written.  prob: device data (mem must be
  * TLQR_MEM_DEVICE).  The call allocates x, u, y for the trials.  Errors:
  * TLQR_ERR_ARG, TLQR_ERR_OOM, TLQR_ERR_NO_CONVERGENCE (no candidate finished),
  * and the first hard error of a candidate. */
 typedef struct {
-  int32_t async_ops, async_solve, tail_ops;
+  int32_t async_ops, async_solve, tail_ops, residual;
   int32_t status;        /* TLQR_OK or the candidate's error */
   double ms;             /* median time of one tlqr_solve, -1 when it failed */
 } tlqr_autotune_entry;

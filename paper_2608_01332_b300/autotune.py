@@ -4,8 +4,8 @@
 
 For each workload (the seeded synthetic trees of the benchmark: long_trunk,
 batch, spine, serve) this calls tlqr_autotune on a B300 in mixed precision
-and records the fastest (async_ops, async_solve, tail_ops) with the timing of
-every candidate.  bench.py reads the committed table (autotune_table.json next
+and records the fastest (async_ops, async_solve, tail_ops, residual) with the
+timing of every candidate.  bench.py reads the committed table (autotune_table.json next
 to this file) and creates its solver with the chosen options.
 """
 from __future__ import annotations
@@ -28,9 +28,10 @@ def load_table(path: str = TABLE) -> dict:
 
 
 def tuned_options(workload: str, path: str = TABLE) -> dict:
-    """Options chosen for a workload: dict(async_ops, async_solve, tail_ops), or {}."""
+    """Options chosen for a workload: dict(async_ops, async_solve, tail_ops[, residual]), or {}."""
     e = load_table(path).get(workload)
-    return {k: int(e["best"][k]) for k in ("async_ops", "async_solve", "tail_ops")} if e else {}
+    return {k: int(v) for k, v in e["best"].items()
+            if k in ("async_ops", "async_solve", "tail_ops", "residual")} if e else {}
 
 
 def main(argv=None):
@@ -73,7 +74,7 @@ def main(argv=None):
         table[name] = {"workload": w.name, "N": len(w.parent), "n": w.n, "m": w.m, "precision": "mixed",
                        "gpu": torch.cuda.get_device_name(dev),
                        "best": {"async_ops": best.async_ops, "async_solve": best.async_solve,
-                                "tail_ops": best.tail_ops},
+                                "tail_ops": best.tail_ops, "residual": best.residual},
                        "candidates": rows}
         print(json.dumps({name: table[name]["best"], "ms": min(r["ms"] for r in rows if r["ms"] > 0)}), flush=True)
         del data, w

@@ -6,6 +6,8 @@
 // single-block tail of tail_ops operations (or none).  Each candidate is a factor object
 // of its own; one full tlqr_solve (factor, solve, refinement) warms it up and
 // the median of `trials` timed solves (CUDA events on `stream`) scores it.
+// In mixed precision the refinement's residual kernels (row per thread, or
+// node-organised with bulk-copy staging) are then tried on the fastest shape.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,12 +24,14 @@ extern "C" int tlqr_autotune(const tlqr_plan_t* plan, const tlqr_options* base, 
   int rc = tlqr_plan_stats(plan, &ps);
   if (rc) return rc;
   const size_t N = (size_t)ps.N, n = (size_t)base->n, m = (size_t)base->m;
-  struct Cand { int32_t async_ops, async_solve, tail_ops; };
+  struct Cand { int32_t async_ops, async_solve, tail_ops, residual; };
   std::vector<Cand> cands;
   for (int32_t a : {-1, 256, 1024, 4096}) {
-    cands.push_back({a, 1, 0});
-    for (int32_t t : {-1, 64, 128, 512}) cands.push_back({a, -1, t});
+    cands.push_back({a, 1, 0, base->residual});
+    for (int32_t t : {-1, 64, 128, 512}) cands.push_back({a, -1, t, base->residual});
   }
+  const size_t n_shapes = cands.size();
+  const bool tune_residual = base->precision == TLQR_PREC_MIXED && base->residual == 0;
   cudaStream_t st = (cudaStream_t)stream;
   double *x = nullptr, *u = nullptr, *y = nullptr;
   if (cudaMalloc((void**)&x, N * n * sizeof(double)) || cudaMalloc((void**)&u, N * m * sizeof(double)) ||
@@ -45,11 +49,18 @@ extern "C" int tlqr_autotune(const tlqr_plan_t* plan, const tlqr_options* base, 
   double best_ms = 0;
   int count = 0;
   *best = *base;
-  for (const Cand& c : cands) {
+  for (size_t ci = 0;; ++ci) {
+    if (ci == n_shapes && tune_residual && best_ms > 0) {
+      // second stage: the residual kernels on the fastest shape
+      for (int32_t r : {1, 2}) cands.push_back({best->async_ops, best->async_solve, best->tail_ops, r});
+    }
+    if (ci >= cands.size()) break;
+    const Cand c = cands[ci];
     tlqr_options o = *base;
     o.async_ops = c.async_ops;
     o.async_solve = c.async_solve;
     o.tail_ops = c.tail_ops;
+    o.residual = c.residual;
     tlqr_factor_t* f = nullptr;
     double ms = -1.0;
     int status = tlqr_factor_create(plan, &o, &f);
@@ -75,6 +86,7 @@ extern "C" int tlqr_autotune(const tlqr_plan_t* plan, const tlqr_options* base, 
       table[count].async_ops = c.async_ops;
       table[count].async_solve = c.async_solve;
       table[count].tail_ops = c.tail_ops;
+      table[count].residual = c.residual;
       table[count].status = status;
       table[count].ms = ms;
     }

@@ -349,13 +349,47 @@ __device__ __forceinline__ void zero(T (&a)[N]) {
 // sm (group): U, A, Y matrices + the Gauss-Jordan broadcast rows.
 template <typename T, int N>
 struct TauSmem {
-  static constexpr int elems = 3 * D<T, N>::MAT + GjBuf<T, N, N>::elems;
+  // U, A, Y; on the tensor-core path A stays in global memory (fewer bytes per
+  // warp, more resident warps)
+  static constexpr int mats = kTensorCores<T, N> ? 2 : 3;
+  static constexpr int elems = mats * D<T, N>::MAT + GjBuf<T, N, N>::elems;
   static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
-template <typename T, int N, typename S>
-__device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag, const S* Cg, const S* Pg, T* out,
+// Tensor-core version (n = 32, FP32): U and C staged, C U on the tensor
+// cores, A read from global memory twice -- rows for the elimination's
+// right-hand side and as the transposed left operand of the last product -- so
+// that a warp holds two staged matrices instead of three.
+template <typename T, int N>
+__device__ __forceinline__ bool tau_group_tc(const Grp& g, const T* Ug, const T* Ag, const T* Cg, const T* Pg, T* out,
+                                             T* sm) {
+  using Dm = D<T, N>;
+  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT;
+  T *sU = sm, *sY = sm + MAT, *bc = sm + 2 * MAT;
+  gload<T, N, N, LD, G>(sU, Ug, g.gl);
+  gload<T, N, N, LD, G>(sY, Cg, g.gl);      // C staged in sY
+  __syncwarp();
+  const int r = g.gl < N ? g.gl : 0;
+  T x[N], b[N];
+  tc::gemm32<false, false>(sY, LD, sU, LD, nullptr, 0, sY, LD, true);   // C U over C
+  row_load<T, N>(x, sY + r * LD);
+#pragma unroll
+  for (int c = 0; c < N; ++c) x[c] += (c == r) ? T(1) : T(0);
+  grow_load<T, N>(b, Ag + r * N);               // row r of A (right-hand side)
+  __syncwarp();
+  int kpos;
+  const bool ok = ggj<T, N, G, N>(x, b, g.gl, bc, kpos);   // Y = (I + C U)^{-1} A, row kpos in b
+  if (g.gl < N) row_store<T, N>(sY + kpos * LD, b);
+  __syncwarp();
+  tc::gemm32<false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, true);   // Z = U Y over U
+  tc::gemm32<true, false>(Ag, N, sU, LD, Pg, N, out, N, g.valid);      // P + A^T Z
+  return ok;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ bool tau_group(const Grp& g, const T* Ug, const T* Ag, const T* Cg, const T* Pg, T* out,
                                           T* sm) {
+  if constexpr (kTensorCores<T, N>) return tau_group_tc<T, N>(g, Ug, Ag, Cg, Pg, out, sm);
   using Dm = D<T, N>;
   constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT;
   T *sU = sm, *sA = sm + MAT, *sY = sm + 2 * MAT, *bc = sm + 3 * MAT;
@@ -365,12 +399,7 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   __syncwarp();
   const int r = g.gl < N ? g.gl : 0;
   T x[N], b[N];
-  if constexpr (kTensorCores<T, N>) {
-    tc::gemm32<false, false>(sY, LD, sU, LD, nullptr, 0, sY, LD, true);   // C U over C
-    row_load<T, N>(x, sY + r * LD);
-#pragma unroll
-    for (int c = 0; c < N; ++c) x[c] += (c == r) ? T(1) : T(0);
-  } else {
+  {
     T crow[N];
     row_load<T, N>(crow, sY + r * LD);
     zero(x);
@@ -384,11 +413,6 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   const bool ok = ggj<T, N, G, N>(x, b, g.gl, bc, kpos);   // Y = (I + C U)^{-1} A, row kpos in b
   if (g.gl < N) row_store<T, N>(sY + kpos * LD, b);
   __syncwarp();
-  if constexpr (kTensorCores<T, N> && std::is_same<S, T>::value) {
-    tc::gemm32<false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, true);   // Z = U Y over U
-    tc::gemm32<true, false>(sA, LD, sU, LD, Pg, N, out, N, g.valid);     // P + A^T Z
-    return ok;
-  }
   T z[N];
   {
     T urow[N];
@@ -400,19 +424,20 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const S* Ug, const S* Ag
   if (g.gl < N) row_store<T, N>(sU + r * LD, z); // Z over U
   __syncwarp();
   T o[N];
-  if constexpr (std::is_same<S, T>::value) {
-    grow_load<T, N>(o, Pg + r * N);
-  } else {
-#pragma unroll
-    for (int j = 0; j < N; ++j) o[j] = (T)Pg[r * N + j];
-  }
+  grow_load<T, N>(o, Pg + r * N);
   col_mm<T, N, N, LD, LD>(o, sA, r, sU);        // P + A^T Z
   if (g.valid && g.gl < N) grow_store<T, N>(out + r * N, o);
   return ok;
 }
 
+// 128-thread blocks; resident blocks per SM the register budget must allow:
+// five for the n = 32 tensor-core version (two staged matrices per warp, so
+// shared memory allows five) and for FP64, eight for the FP32 group kernels
 template <typename T, int N>
-__global__ void kf_rake(Ws<T> w, int begin, int count) {
+constexpr int kRakeBlocks = (sizeof(T) == 8 || N >= 32) ? 5 : 8;
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128, kRakeBlocks<T, N>) kf_rake(Ws<T> w, int begin, int count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int op;
   const Grp g = group_of<T, N>(count, &op);
@@ -424,7 +449,7 @@ __global__ void kf_rake(Ws<T> w, int begin, int count) {
 }
 
 template <typename T, int N>
-__global__ void kf_expand(Ws<T> w, int begin, int count) {
+__global__ void __launch_bounds__(128, kRakeBlocks<T, N>) kf_expand(Ws<T> w, int begin, int count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int op;
   const Grp g = group_of<T, N>(count, &op);
@@ -445,12 +470,71 @@ struct CompSmem {
   // odd number of vectors (conflict-free row stores)
   static constexpr int YW = D<T, N>::NV * D<T, N>::W;
   static constexpr int LD2 = (2 * D<T, N>::NV + 1) * D<T, N>::W;
-  static constexpr int elems = 4 * D<T, N>::MAT + N * LD2 + GjBuf<T, N, 2 * YW>::elems;
+  // P~, A_l, C_l, A_r; on the tensor-core path A_l and A_r stay in global memory
+  static constexpr int mats = kTensorCores<T, N> ? 2 : 4;
+  static constexpr int elems = mats * D<T, N>::MAT + N * LD2 + GjBuf<T, N, 2 * YW>::elems;
   static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
+// Tensor-core compression (n = 32, FP32): P~ and C_l staged, the block products
+// on the tensor cores, A_l and A_r read from global memory (so a warp holds two
+// staged matrices and the [Y1 | Y2] panel instead of four and the panel).  The
+// order keeps every read ahead of the write that replaces it: A_l (slot j) is
+// last read by P_new, before the tape overwrites slot j; A_r (slot k) is last
+// read by A_new, which replaces it.
+template <typename T, int N>
+__device__ __forceinline__ bool compress_op_tc(const Ws<T>& w, int rr, const Grp& g, T* sm) {
+  using Dm = D<T, N>;
+  constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, LD2 = CompSmem<T, N>::LD2, YW = CompSmem<T, N>::YW;
+  constexpr int NN = N * N;
+  T *sPt = sm, *sCl = sm + MAT, *sY = sm + 2 * MAT, *bc = sm + 2 * MAT + N * LD2;
+  const int j = w.comp_j[rr], k = w.comp_k[rr];
+  const size_t oj = (size_t)j * NN, ok_ = (size_t)k * NN;
+  const T *Al = w.Ea + oj, *Ar = w.Ea + ok_;
+  const int gl = g.gl, r = gl < N ? gl : 0;
+#pragma unroll
+  for (int e = gl; e < NN; e += G) {
+    const int a = e / N, c = e - (e / N) * N;
+    sPt[a * LD + c] = w.Ep[ok_ + e] + w.U[oj + e];                     // P~ = P_r + U_j
+  }
+  gload<T, N, N, LD, G>(sCl, w.Ec + oj, gl);
+  __syncwarp();
+  tc::gemm32<false, false>(sCl, LD, sPt, LD, nullptr, 0, sY, LD2, true);   // C_l P~ -> Y1 columns
+  tc::gemm32<false, true>(sCl, LD, Ar, N, nullptr, 0, sY + YW, LD2, true);  // C_l A_r^T -> Y2 columns
+  T s[N], b[2 * YW], t1[N], t2[N];
+  row_load<T, N>(s, sY + r * LD2);
+#pragma unroll
+  for (int c = 0; c < N; ++c) s[c] += (c == r) ? T(1) : T(0);         // S = I + C_l P~
+  grow_load<T, N>(t1, Al + r * N);
+  row_load<T, N>(t2, sY + r * LD2 + YW);
+#pragma unroll
+  for (int c = 0; c < 2 * YW; ++c) b[c] = c < N ? t1[c] : (c >= YW && c < YW + N) ? t2[c - YW] : T(0);
+  __syncwarp();
+  int kpos;
+  const bool okf = ggj<T, N, G, 2 * YW>(s, b, gl, bc, kpos);   // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T]
+  if (gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
+  __syncwarp();
+  tc::gemm32<false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, true);             // W = P~ Y1 over C_l
+  tc::gemm32<true, false>(Al, N, sCl, LD, w.Ep + oj, N, w.Ep + ok_, N, g.valid);   // P_new = P_l + A_l^T W
+  if (g.valid && gl < N) {
+    // tape into slot j: (A_r, C_r, P~), read before slot k is rewritten
+    T v[N];
+    grow_load<T, N>(v, Ar + r * N);
+    grow_store<T, N>(w.Ea + oj + r * N, v);
+    grow_load<T, N>(v, w.Ec + ok_ + r * N);
+    grow_store<T, N>(w.Ec + oj + r * N, v);
+    row_load<T, N>(v, sPt + r * LD);
+    grow_store<T, N>(w.Ep + oj + r * N, v);
+  }
+  __syncwarp();
+  tc::gemm32<false, false>(Ar, N, sY + YW, LD2, w.Ec + ok_, N, w.Ec + ok_, N, g.valid);   // C_new = C_r + A_r Y2
+  tc::gemm32<false, false>(Ar, N, sY, LD2, nullptr, 0, w.Ea + ok_, N, g.valid);          // A_new = A_r Y1
+  return okf;
+}
+
 template <typename T, int N>
 __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g, T* sm) {
+  if constexpr (kTensorCores<T, N>) return compress_op_tc<T, N>(w, rr, g, sm);
   using Dm = D<T, N>;
   constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT, LD2 = CompSmem<T, N>::LD2, YW = CompSmem<T, N>::YW;
   constexpr int NN = N * N;
@@ -470,20 +554,7 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   gload<T, N, N, LD, G>(sAr, w.Ea + ok_, gl);
   __syncwarp();
   T s[N], b[2 * YW];
-  if constexpr (kTensorCores<T, N>) {
-    // C_l P~ into the Y1 columns and C_l A_r^T into the Y2 columns of sY
-    tc::gemm32<false, false>(sCl, LD, sPt, LD, nullptr, 0, sY, LD2, true);
-    tc::gemm32<false, true>(sCl, LD, sAr, LD, nullptr, 0, sY + YW, LD2, true);
-    T t1[N], t2[N];
-    row_load<T, N>(s, sY + r * LD2);
-#pragma unroll
-    for (int c = 0; c < N; ++c) s[c] += (c == r) ? T(1) : T(0);   // S = I + C_l P~
-    row_load<T, N>(t1, sAl + r * LD);
-    row_load<T, N>(t2, sY + r * LD2 + YW);
-#pragma unroll
-    for (int c = 0; c < 2 * YW; ++c)
-      b[c] = c < N ? t1[c] : (c >= YW && c < YW + N) ? t2[c - YW] : T(0);
-  } else {
+  {
     T cl[N], t1[N], t2[N];
     row_load<T, N>(cl, sCl + r * LD);
     zero(s);
@@ -502,26 +573,6 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   const bool okf = ggj<T, N, G, 2 * YW>(s, b, gl, bc, kpos);   // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
   if (gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
-  if constexpr (kTensorCores<T, N>) {
-    // W = P~ Y1 over C_l; P_new = P_l + A_l^T W into slot k (P_r is folded into P~
-    // already); A_new = A_r Y1 into slot k (A_r stays in shared memory for the tape)
-    tc::gemm32<false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, true);
-    tc::gemm32<true, false>(sAl, LD, sCl, LD, w.Ep + oj, N, w.Ep + ok_, N, g.valid);
-    tc::gemm32<false, false>(sAr, LD, sY, LD2, nullptr, 0, w.Ea + ok_, N, g.valid);
-    if (g.valid && gl < N) {
-      // tape into slot j: (A_r, C_r, P~); C_r copied before slot k's C is updated
-      T v[N];
-      row_load<T, N>(v, sAr + r * LD);
-      grow_store<T, N>(w.Ea + oj + r * N, v);
-      grow_load<T, N>(v, w.Ec + ok_ + r * N);
-      grow_store<T, N>(w.Ec + oj + r * N, v);
-      row_load<T, N>(v, sPt + r * LD);
-      grow_store<T, N>(w.Ep + oj + r * N, v);
-    }
-    __syncwarp();
-    tc::gemm32<false, false>(sAr, LD, sY + YW, LD2, w.Ec + ok_, N, w.Ec + ok_, N, g.valid);  // C_r + A_r Y2
-    return okf;
-  }
   // A_new = A_r Y1, C_new = C_r + A_r Y2  (rows r); C_r read before slot k is overwritten
   T an[N], cn[N];
   {

@@ -1,10 +1,13 @@
 // Float-float KKT residual of eq. (kkt), organised by node for compile-time
 // (n, m): one group of G lanes per node, lane r owning row r.  Each node's
-// FP64 blocks are copied into shared memory with asynchronous 8-byte copies
-// (cp.async), double-buffered so that the next node's blocks are in flight
-// while the current node is computed; every FP64 matrix entry is read from HBM
-// exactly once per evaluation (the row-per-thread kernels of residual.cuh read
-// A_j and B_j twice and walk Q by strided rows).
+// FP64 blocks are moved into shared memory by the bulk-copy (TMA) engine: one
+// lane per group issues one `cp.async.bulk` per block (contiguous, 16-byte
+// aligned, a multiple of 16 bytes) that completes on an mbarrier, with two
+// buffers per group so that the next node's blocks are in flight while the
+// current node is computed.  Every FP64 matrix entry is read from HBM once per
+// evaluation (the row-per-thread kernels of residual.cuh read A_j and B_j
+// twice and walk Q by strided rows), and a node whose Delta_i is zero (the
+// per-node flag the condensation records) has no Delta block copied at all.
 //
 // Two launches:
 //   edge pass, node j:  the constraint row entering j
@@ -17,6 +20,13 @@
 // Absolute row sums of the KKT matrix (||K||_inf) follow the same split; the
 // maxima ||res||, ||z||, ||b||, ||K|| are folded per block (one tree) or per
 // tree (a forest), exactly as the row kernels do.
+//
+// Blocks sit in shared memory densely (a bulk copy cannot pad rows); a lane
+// walks its row starting at column r and wrapping around, so that the lanes of
+// a group read different banks.  Every wait on an mbarrier is bounded: a wait
+// that runs out sets ST_TIMEOUT in the status word, the warp stops taking
+// nodes, waits (again bounded) for the copies it has in flight and joins the
+// block's final reduction.
 #pragma once
 #include "residual.cuh"
 
@@ -29,23 +39,44 @@ struct RG {
   static constexpr int OPS = 32 / G;          // nodes per warp
 };
 
-__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+constexpr int kResStTimeout = 7;              // ST_TIMEOUT of the factor's status word
 
-// Asynchronous copy of an R x C FP64 block (contiguous rows) into shared rows
-// of stride LDS, by the G lanes of a group.
-template <int R, int C, int LDS, int G>
-__device__ __forceinline__ void stage_async(double* dst, const double* src, int gl) {
-#pragma unroll 4
-  for (int e = gl; e < R * C; e += G) {
-    const int a = e / C, b = e - (e / C) * C;
-    cp_async8(dst + a * LDS + b, src + e);
-  }
+// ------------------------------------------------------------- bulk copies
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// make initialised barriers visible to the bulk-copy engine
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// the one arrival of a phase, announcing `bytes` of copies that complete on it
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy (dst, src 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait until the phase of parity `parity` has completed; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit) {
+  for (int i = 0; i < limit; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
 }
 
 // s += sum_b a[b * STRIDE] * (xh[b] + xl[b]) (sign -1: minus), with four
@@ -57,6 +88,22 @@ __device__ __forceinline__ float ff_dot(FF& s, const double* a, const float* xh,
   float rs = 0.f;
 #pragma unroll
   for (int b = 0; b < K; ++b) rs += ff_fma_d(acc[b & 3], a[b * STRIDE], sign * xh[b], sign * xl[b]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ff_add2(s, acc[q].h, acc[q].l);
+  return rs;
+}
+// The same over a dense row, visiting columns c0, c0 + 1, ..., wrapping at K.
+template <int K>
+__device__ __forceinline__ float ff_dot_row(FF& s, const double* a, const float* xh, const float* xl, int c0,
+                                            float sign = 1.f) {
+  FF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  float rs = 0.f;
+  int c = c0;
+#pragma unroll
+  for (int b = 0; b < K; ++b) {
+    rs += ff_fma_d(acc[b & 3], a[c], sign * xh[c], sign * xl[c]);
+    c = c + 1 == K ? 0 : c + 1;
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) ff_add2(s, acc[q].h, acc[q].l);
   return rs;
@@ -79,8 +126,14 @@ __device__ __forceinline__ NodeRange warp_nodes(int N) {
 }
 
 struct NodeArgs {
-  float *wh, *wl;     // [N][n] float-float message w_j to the parent row
-  float* wk;          // [N][n] absolute column sums of [A_j^T | M_j] (when with_knorm)
+  float *wh, *wl;              // [N][n] float-float message w_j to the parent row
+  float* wk;                   // [N][n] absolute column sums of [A_j^T | M_j] (when with_knorm)
+  const unsigned char* dflag;  // per node: Delta_i has a nonzero entry (null: every Delta_i is read)
+  int* status;                 // ST_TIMEOUT when a bounded wait ran out (null: not reported)
+  int spin;                    // polls of one mbarrier wait before it gives up
+  int withhold;                // testing failure detection: the first group of the grid
+                               // announces its first node's bytes but copies nothing, so
+                               // that wait runs out
 };
 
 struct Maxima {
@@ -91,66 +144,105 @@ struct Maxima {
   }
 };
 
-// Shared-memory layout of one edge-pass buffer (doubles): A, [Delta], B, [M], R.
+// Group of the edge pass in shared memory: two mbarriers (16 bytes), two
+// buffers [A | Delta | B | M | R] of dense FP64 blocks, then the float-float
+// vectors x_p, y_j (N each) and u_j (M), hi and lo.  With n and m even every
+// block is a multiple of 16 bytes, so every block starts 16-byte aligned.
 template <int N, int M>
 struct EdgeBuf {
-  static constexpr int LDA = N + 1, LDB = M + 1;
+  static_assert(N % 2 == 0 && M % 2 == 0, "bulk copies need 16-byte multiples");
   __host__ __device__ static constexpr int doubles(bool has_delta, bool has_M) {
-    return N * LDA * (has_delta ? 2 : 1) + N * LDB * (has_M ? 2 : 1) + M * LDB;
+    return N * N * (has_delta ? 2 : 1) + N * M * (has_M ? 2 : 1) + M * M;
   }
-  // per group: two buffers + the float-float vectors x_p, y_j (N each), u_j (M), hi and lo
   __host__ __device__ static constexpr int group_bytes(bool has_delta, bool has_M) {
-    return ((2 * doubles(has_delta, has_M) * 8 + (4 * N + 2 * M) * 4) + 15) / 16 * 16;
+    return 16 + 2 * doubles(has_delta, has_M) * 8 + ((4 * N + 2 * M) * 4 + 15) / 16 * 16;
   }
 };
+
+__device__ __forceinline__ void report_timeout(int* status) {
+  if (status && (threadIdx.x & 31) == 0) atomicCAS(status, 0, kResStTimeout);
+}
 
 // Edge pass.  FOREST: fold maxima per tree.
 template <int N, int M, bool FOREST>
 __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, NodeArgs na) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using EB = EdgeBuf<N, M>;
-  constexpr int G = RG<N>::G, OPS = RG<N>::OPS, LDA = EB::LDA, LDB = EB::LDB;
+  constexpr int G = RG<N>::G, OPS = RG<N>::OPS;
+  constexpr unsigned kA = N * N * 8, kB = N * M * 8, kR = M * M * 8;
   const bool hd = a.Delta != nullptr, hm = a.M != nullptr, ks = a.with_knorm;
   const int gl = threadIdx.x & (G - 1), gid = (threadIdx.x & 31) / G;
   const int nd = EB::doubles(hd, hm);
   unsigned char* gbase = smem_raw + (size_t)((threadIdx.x >> 5) * OPS + gid) * EB::group_bytes(hd, hm);
-  double* buf0 = reinterpret_cast<double*>(gbase);
-  float* vxh = reinterpret_cast<float*>(gbase + 2 * (size_t)nd * 8);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(gbase);
+  double* buf0 = reinterpret_cast<double*>(gbase + 16);
+  float* vxh = reinterpret_cast<float*>(gbase + 16 + 2 * (size_t)nd * 8);
   float *vxl = vxh + N, *vyh = vxl + N, *vyl = vyh + N, *vuh = vyl + N, *vul = vuh + M;
   const size_t nn = (size_t)N * N, nm = (size_t)N * M;
-  auto issue = [&](int j, double* b) {
-    double* sA = b;
-    double* sD = sA + N * LDA;
-    double* sB = sD + (hd ? N * LDA : 0);
-    double* sM = sB + N * LDB;
-    double* sR = sM + (hm ? N * LDB : 0);
-    if (a.parent[j] >= 0) {
-      stage_async<N, N, LDA, G>(sA, a.A + (size_t)j * nn, gl);
-      stage_async<N, M, LDB, G>(sB, a.B + (size_t)j * nm, gl);
-      stage_async<M, M, LDB, G>(sR, a.R + (size_t)j * M * M, gl);
-      if (hm) stage_async<N, M, LDB, G>(sM, a.M + (size_t)j * nm, gl);
-    }
-    if (hd) stage_async<N, N, LDA, G>(sD, a.Delta + (size_t)j * nn, gl);
+  // block slots of buffer b: A, Delta, B, M, R
+  auto slot = [&](int b, int which) -> double* {
+    double* p = buf0 + (size_t)b * nd;
+    if (which == 0) return p;
+    p += N * N;
+    if (which == 1) return p;
+    if (hd) p += N * N;
+    if (which == 2) return p;
+    p += N * M;
+    if (which == 3) return p;
+    if (hm) p += N * M;
+    return p;
   };
+  auto has_delta = [&](int j) { return hd && (!na.dflag || na.dflag[j]); };
+  // lane 0 of the group: the copies of node j's blocks into buffer b
+  auto issue = [&](int j, int b, bool first) {
+    if (gl != 0) return;
+    const bool hp = a.parent[j] >= 0, dz = has_delta(j);
+    const unsigned bytes = (hp ? kA + kB + kR + (hm ? kB : 0u) : 0u) + (dz ? kA : 0u);
+    mbar_expect(bar + b, bytes);
+    if (na.withhold && bytes && blockIdx.x == 0 && threadIdx.x == 0 && first) return;
+    if (hp) {
+      bulk_load(slot(b, 0), a.A + (size_t)j * nn, kA, bar + b);
+      bulk_load(slot(b, 2), a.B + (size_t)j * nm, kB, bar + b);
+      bulk_load(slot(b, 4), a.R + (size_t)j * M * M, kR, bar + b);
+      if (hm) bulk_load(slot(b, 3), a.M + (size_t)j * nm, kB, bar + b);
+    }
+    if (dz) bulk_load(slot(b, 1), a.Delta + (size_t)j * nn, kA, bar + b);
+  };
+  if (gl == 0) {
+    mbar_init(bar);
+    mbar_init(bar + 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
   const NodeRange nr = warp_nodes<OPS>(a.N);
   Maxima mx;
   TreeAcc acc;
-  if (nr.begin < nr.end) issue(nr.begin + gid < nr.end ? nr.begin + gid : nr.end - 1, buf0);
-  cp_async_commit();
+  unsigned par = 0u;               // bit b: parity of buffer b's next phase to complete
+  unsigned pend = 0u;              // bit b: copies into buffer b issued and not yet waited for
+  bool timed_out = false;
+  if (nr.begin < nr.end) {
+    issue(nr.begin + gid < nr.end ? nr.begin + gid : nr.end - 1, 0, true);
+    pend = 1u;
+  }
   int t = 0;
   for (int base = nr.begin; base < nr.end; base += OPS, ++t) {
+    const int cb = t & 1;
     const int j0 = base + gid;
     const bool valid = j0 < nr.end;
     const int j = valid ? j0 : nr.end - 1;
-    double* cur = buf0 + (t & 1) * nd;
     if (base + OPS < nr.end) {                           // prefetch this group's next node
-      const int jn = base + OPS + gid < nr.end ? base + OPS + gid : nr.end - 1;
-      issue(jn, buf0 + ((t + 1) & 1) * nd);
+      issue(base + OPS + gid < nr.end ? base + OPS + gid : nr.end - 1, cb ^ 1, false);
+      pend |= 2u >> cb;
     }
-    cp_async_commit();
-    cp_async_wait<1>();
+    const bool ok = mbar_wait(bar + cb, (par >> cb) & 1u, na.spin);
+    if (__any_sync(TLQR_FULL_MASK, !ok)) {
+      timed_out = true;
+      break;
+    }
+    par ^= 1u << cb;
+    pend &= ~(1u << cb);
     const int p = a.parent[j];
-    const bool has_p = p >= 0;
+    const bool has_p = p >= 0, dz = has_delta(j);
     if (gl < N) {
       vyh[gl] = f.yh[(size_t)j * N + gl];
       vyl[gl] = f.yl[(size_t)j * N + gl];
@@ -162,11 +254,7 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
       vul[gl] = f.ul[(size_t)j * M + gl];
     }
     __syncwarp();
-    const double* sA = cur;
-    const double* sD = sA + N * LDA;
-    const double* sB = sD + (hd ? N * LDA : 0);
-    const double* sM = sB + N * LDB;
-    const double* sR = sM + (hm ? N * LDB : 0);
+    const double *sA = slot(cb, 0), *sD = slot(cb, 1), *sB = slot(cb, 2), *sM = slot(cb, 3), *sR = slot(cb, 4);
     const int r = gl < N ? gl : 0;
     unsigned long long row[4] = {0ull, 0ull, 0ull, 0ull};
     // constraint row r entering j
@@ -176,10 +264,10 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
       ff_add(s, a.c[tr]);
       ff_add2(s, -f.xh[tr], -f.xl[tr]);
       float rs = 1.f;
-      if (hd) rs += ff_dot<N, 1>(s, sD + r * LDA, vyh, vyl, -1.f);
+      if (dz) rs += ff_dot_row<N>(s, sD + r * N, vyh, vyl, r, -1.f);
       if (has_p) {
-        rs += ff_dot<N, 1>(s, sA + r * LDA, vxh, vxl);
-        rs += ff_dot<M, 1>(s, sB + r * LDB, vuh, vul);
+        rs += ff_dot_row<N>(s, sA + r * N, vxh, vxl, r);
+        rs += ff_dot<M, 1>(s, sB + r * M, vuh, vul);
       }
       const double out = ff_value(s);
       if (valid && gl < N) a.res_c[tr] = out;
@@ -201,14 +289,14 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
         for (int k = 0; k < (N + P - 1) / P; ++k) {
           const int b = part + k * P;
           if (b < N) {
-            if (hm) rs += ff_fma_d(s, sM[b * LDB + ua], vxh[b], vxl[b]);
-            rs += ff_fma_d(s, sB[b * LDB + ua], vyh[b], vyl[b]);
+            if (hm) rs += ff_fma_d(s, sM[b * M + ua], vxh[b], vxl[b]);
+            rs += ff_fma_d(s, sB[b * M + ua], vyh[b], vyl[b]);
           }
         }
 #pragma unroll
         for (int k = 0; k < (M + P - 1) / P; ++k) {
           const int c = part + k * P;
-          if (c < M) rs += ff_fma_d(s, sR[ua * LDB + c], vuh[c], vul[c]);
+          if (c < M) rs += ff_fma_d(s, sR[ua * M + c], vuh[c], vul[c]);
         }
         if (part == 0) ff_add(s, a.r[(size_t)j * M + ua]);
       }
@@ -235,8 +323,8 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
     // message w_j = A_j^T y_j + M_j u_j to the parent's stationarity rows
     if (has_p && gl < N) {
       FF wv{0.f, 0.f};
-      float wk = ff_dot<N, LDA>(wv, sA + r, vyh, vyl);
-      if (hm) wk += ff_dot<M, 1>(wv, sM + r * LDB, vuh, vul);
+      float wk = ff_dot<N, N>(wv, sA + r, vyh, vyl);
+      if (hm) wk += ff_dot<M, 1>(wv, sM + r * M, vuh, vul);
       if (valid) {
         na.wh[(size_t)j * N + r] = wv.h;
         na.wl[(size_t)j * N + r] = wv.l;
@@ -265,7 +353,12 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
     }
     __syncwarp();                                        // buffer and vectors free for reuse
   }
-  cp_async_wait<0>();
+  if (timed_out) {
+    report_timeout(na.status);
+    // the shared memory of copies still in flight must outlive them
+    for (int b = 0; b < 2; ++b)
+      if ((pend >> b) & 1u) mbar_wait(bar + b, (par >> b) & 1u, na.spin);
+  }
   if constexpr (FOREST) {
     acc.flush(a, ks ? 4 : 3);
   } else {
@@ -275,11 +368,12 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
   }
 }
 
+// Group of the node pass: two mbarriers, two dense Q buffers, x_i (hi, lo).
 template <int N>
 struct NodeBuf {
-  static constexpr int LDQ = N + 1;
-  static constexpr int doubles = N * LDQ;
-  static constexpr int group_bytes = ((2 * doubles * 8 + 2 * N * 4) + 15) / 16 * 16;
+  static_assert(N % 2 == 0, "bulk copies need 16-byte multiples");
+  static constexpr int doubles = N * N;
+  static constexpr int group_bytes = 16 + 2 * doubles * 8 + (2 * N * 4 + 15) / 16 * 16;
 };
 
 // Node pass: stationarity rows Q_i x_i + q_i - y_i + sum_children w_j.
@@ -287,44 +381,65 @@ template <int N, bool FOREST>
 __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, NodeArgs na) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using NB = NodeBuf<N>;
-  constexpr int G = RG<N>::G, OPS = RG<N>::OPS, LDQ = NB::LDQ;
+  constexpr int G = RG<N>::G, OPS = RG<N>::OPS;
+  constexpr unsigned kQ = N * N * 8;
   const int gl = threadIdx.x & (G - 1), gid = (threadIdx.x & 31) / G;
   unsigned char* gbase = smem_raw + (size_t)((threadIdx.x >> 5) * OPS + gid) * NB::group_bytes;
-  double* buf0 = reinterpret_cast<double*>(gbase);
-  float* vxh = reinterpret_cast<float*>(gbase + 2 * (size_t)NB::doubles * 8);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(gbase);
+  double* buf0 = reinterpret_cast<double*>(gbase + 16);
+  float* vxh = reinterpret_cast<float*>(gbase + 16 + 2 * (size_t)NB::doubles * 8);
   float* vxl = vxh + N;
   const bool ks = a.with_knorm;
+  auto issue = [&](int i, int b, bool first) {
+    if (gl != 0) return;
+    mbar_expect(bar + b, kQ);
+    if (na.withhold && blockIdx.x == 0 && threadIdx.x == 0 && first) return;
+    bulk_load(buf0 + (size_t)b * NB::doubles, a.Q + (size_t)i * N * N, kQ, bar + b);
+  };
+  if (gl == 0) {
+    mbar_init(bar);
+    mbar_init(bar + 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
   const NodeRange nr = warp_nodes<OPS>(a.N);
   Maxima mx;
   TreeAcc acc;
+  unsigned par = 0u, pend = 0u;
+  bool timed_out = false;
   if (nr.begin < nr.end) {
-    const int i0 = nr.begin + gid < nr.end ? nr.begin + gid : nr.end - 1;
-    stage_async<N, N, LDQ, G>(buf0, a.Q + (size_t)i0 * N * N, gl);
+    issue(nr.begin + gid < nr.end ? nr.begin + gid : nr.end - 1, 0, true);
+    pend = 1u;
   }
-  cp_async_commit();
   int t = 0;
   for (int base = nr.begin; base < nr.end; base += OPS, ++t) {
+    const int cb = t & 1;
     const int i0 = base + gid;
     const bool valid = i0 < nr.end;
     const int i = valid ? i0 : nr.end - 1;
-    const double* sQ = buf0 + (t & 1) * NB::doubles;
     if (base + OPS < nr.end) {
-      const int in = base + OPS + gid < nr.end ? base + OPS + gid : nr.end - 1;
-      stage_async<N, N, LDQ, G>(buf0 + ((t + 1) & 1) * NB::doubles, a.Q + (size_t)in * N * N, gl);
+      issue(base + OPS + gid < nr.end ? base + OPS + gid : nr.end - 1, cb ^ 1, false);
+      pend |= 2u >> cb;
     }
-    cp_async_commit();
-    cp_async_wait<1>();
+    const bool ok = mbar_wait(bar + cb, (par >> cb) & 1u, na.spin);
+    if (__any_sync(TLQR_FULL_MASK, !ok)) {
+      timed_out = true;
+      break;
+    }
+    par ^= 1u << cb;
+    pend &= ~(1u << cb);
     if (gl < N) {
       vxh[gl] = f.xh[(size_t)i * N + gl];
       vxl[gl] = f.xl[(size_t)i * N + gl];
     }
     __syncwarp();
+    const double* sQ = buf0 + (size_t)cb * NB::doubles;
     const int r = gl < N ? gl : 0;
     const size_t tr = (size_t)i * N + r;
     FF s{0.f, 0.f};
     ff_add(s, a.q[tr]);
     ff_add2(s, -f.yh[tr], -f.yl[tr]);
-    float rs = 1.f + ff_dot<N, 1>(s, sQ + r * LDQ, vxh, vxl);
+    float rs = 1.f + ff_dot_row<N>(s, sQ + r * N, vxh, vxl, r);
     for (int k = a.child_start[i]; k < a.child_start[i + 1]; ++k) {
       const int jc = a.child_list[k];
       ff_add2(s, na.wh[(size_t)jc * N + r], na.wl[(size_t)jc * N + r]);
@@ -344,7 +459,11 @@ __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, Node
     }
     __syncwarp();
   }
-  cp_async_wait<0>();
+  if (timed_out) {
+    report_timeout(na.status);
+    for (int b = 0; b < 2; ++b)
+      if ((pend >> b) & 1u) mbar_wait(bar + b, (par >> b) & 1u, na.spin);
+  }
   if constexpr (FOREST) {
     acc.flush(a, ks ? 4 : 3);
   } else {

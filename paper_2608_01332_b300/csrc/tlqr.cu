@@ -452,6 +452,9 @@ struct tlqr_factor_t {
   float *rwh = nullptr, *rwl = nullptr, *rwk = nullptr;
   unsigned long long* maxes = nullptr;
   unsigned long long* h_maxes = nullptr;   // pinned mirror
+  double* d_gate = nullptr;                 // speculative refinement: [0] eta of the first residual
+  double* h_gate = nullptr;                 // pinned mirror
+  bool speculate = false;                   // the last mixed solve needed a refinement step
   int* h_status = nullptr;                  // pinned mirror
   double* stage = nullptr;                  // FP64 staging (host-memory calls), lazily allocated
   size_t arena_bytes = 0;                   // the one device allocation holding plan arrays + workspace
@@ -510,6 +513,7 @@ struct tlqr_factor_t {
     for (void* p : allocs) cudaFree(p);
     if (panel_mem) cudaFree(panel_mem);
     if (h_maxes) cudaFreeHost(h_maxes);
+    if (h_gate) cudaFreeHost(h_gate);
     if (h_status) cudaFreeHost(h_status);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -611,6 +615,7 @@ void carve_factor(tlqr_factor_t* f, Carve& c) {
   f->status = c.take<int>(1, sizeof(int));
   f->res_x = c.take<double>(N * n, 8); f->res_u = c.take<double>(N * m, 8); f->res_c = c.take<double>(N * n, 8);
   f->maxes = c.take<unsigned long long>(4 * (size_t)P->n_trees, 8);
+  f->d_gate = c.take<double>(2, 8);
   f->xh = f->xl = f->uh = f->ul = f->yh = f->yl = nullptr;
   f->rwh = f->rwl = f->rwk = nullptr;
   if (f->opt.precision == TLQR_PREC_MIXED) {
@@ -721,7 +726,7 @@ cudaError_t launch_async(tlqr_factor_t* f, Recorder* rc, int kind, Kernel kernel
   a.flags = d.flags; a.counter = d.flags + A.n_flags; a.abort = d.flags + A.n_flags + 1;
   a.n_ops = A.n_ops;
   a.spin_limit = f->opt.spin_limit > 0 ? f->opt.spin_limit : kSpinLimit;
-  a.withhold = (f->opt.test_withhold && &d == &f->fa) ? 0 : -1;
+  a.withhold = ((f->opt.test_withhold & 1) && &d == &f->fa) ? 0 : -1;
   constexpr int gpb = 128 / fx::D<T, N>::G;
   if (!(rc && rc->capture) && smem > 0 && (e = ensure_smem(kernel, smem))) return e;
   const int blocks = std::max(1, std::min((A.n_ops + gpb - 1) / gpb, d.blocks));
@@ -972,16 +977,35 @@ bool has_fixed_pair(int n, int m) {
   return (m == 2 && (n == 4 || n == 6 || n == 8)) || (m == 4 && (n == 12 || n == 16)) || (m == 8 && n == 32);
 }
 
+// Resident blocks per SM of a kernel at a launch shape (cached; the first query
+// for a shape happens when the factor is configured, outside stream capture).
+template <typename Kernel>
+int resident_blocks(Kernel kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> have;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = have.find({(const void*)kernel, smem});
+  if (it != have.end()) return it->second;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
+  b = std::max(1, b);
+  have[{(const void*)kernel, smem}] = b;
+  return b;
+}
+
 // Node-organised float-float residual for compile-time (n, m): edge pass then
-// node pass (see residual_nodes.cuh).  Returns cudaErrorNotSupported when
-// (n, m) has no such kernels.
+// node pass with bulk-copy staging (see residual_nodes.cuh).  Grids are one
+// wave: every resident block slot of every SM, each warp walking a contiguous
+// node range.  Returns cudaErrorNotSupported when (n, m) has no such kernels.
 template <int N, int M>
 cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::NodeArgs& na, int sms,
                              cudaStream_t st, bool capturing) {
   constexpr int OPS = rn::RG<N>::OPS, threads = 128, gpb = (threads / 32) * OPS;
   const size_t se = (size_t)rn::EdgeBuf<N, M>::group_bytes(a.Delta != nullptr, a.M != nullptr) * gpb;
   const size_t sn = (size_t)rn::NodeBuf<N>::group_bytes * gpb;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(((long long)a.N + gpb - 1) / gpb, (long long)sms * 16));
   const bool forest = a.tree != nullptr;
   auto ek = forest ? rn::k_res_edge<N, M, true> : rn::k_res_edge<N, M, false>;
   auto nk = forest ? rn::k_res_node<N, true> : rn::k_res_node<N, false>;
@@ -990,8 +1014,11 @@ cudaError_t launch_res_nodes(const ResidualArgs& a, const FFArgs& fa, const rn::
     if (!e) e = ensure_smem(nk, sn);
     if (e) return e;
   }
-  ek<<<blocks, threads, se, st>>>(a, fa, na);
-  nk<<<blocks, threads, sn, st>>>(a, fa, na);
+  const long long need = ((long long)a.N + gpb - 1) / gpb;
+  const int be = (int)std::max<long long>(1, std::min<long long>(need, (long long)sms * resident_blocks(ek, threads, se)));
+  const int bn = (int)std::max<long long>(1, std::min<long long>(need, (long long)sms * resident_blocks(nk, threads, sn)));
+  ek<<<be, threads, se, st>>>(a, fa, na);
+  nk<<<bn, threads, sn, st>>>(a, fa, na);
   return cudaGetLastError();
 }
 
@@ -999,12 +1026,19 @@ cudaError_t configure_res_nodes(int n, int m) {
 #define X(n_, m_)                                                                              \
   if (n == n_ && m == m_) {                                                                    \
     constexpr int gpb = 4 * rn::RG<n_>::OPS;                                                   \
-    const size_t se = (size_t)rn::EdgeBuf<n_, m_>::group_bytes(true, true) * gpb;                \
     const size_t sn = (size_t)rn::NodeBuf<n_>::group_bytes * gpb;                                 \
-    cudaError_t e = ensure_smem(rn::k_res_edge<n_, m_, true>, se);                                \
-    if (!e) e = ensure_smem(rn::k_res_edge<n_, m_, false>, se);                                   \
-    if (!e) e = ensure_smem(rn::k_res_node<n_, true>, sn);                                        \
+    cudaError_t e = ensure_smem(rn::k_res_node<n_, true>, sn);                                    \
     if (!e) e = ensure_smem(rn::k_res_node<n_, false>, sn);                                       \
+    resident_blocks(rn::k_res_node<n_, true>, 128, sn);                                           \
+    resident_blocks(rn::k_res_node<n_, false>, 128, sn);                                          \
+    for (int hd = 0; hd < 2 && !e; ++hd)                                                       \
+      for (int hm = 0; hm < 2 && !e; ++hm) {                                                   \
+        const size_t se = (size_t)rn::EdgeBuf<n_, m_>::group_bytes(hd, hm) * gpb;                 \
+        e = ensure_smem(rn::k_res_edge<n_, m_, true>, se);                                        \
+        if (!e) e = ensure_smem(rn::k_res_edge<n_, m_, false>, se);                               \
+        resident_blocks(rn::k_res_edge<n_, m_, true>, 128, se);                                   \
+        resident_blocks(rn::k_res_edge<n_, m_, false>, 128, se);                                  \
+      }                                                                                        \
     return e;                                                                                  \
   }
   TLQR_FIXED_PAIRS(X)
@@ -1021,15 +1055,27 @@ cudaError_t dispatch_res_nodes(int n, int m, const ResidualArgs& a, const FFArgs
   return cudaErrorNotSupported;
 }
 
-// Which float-float residual runs: the node-organised kernels were measured
-// faster than the row-per-thread kernels at n = 16 (-25 % on a batch of 1,024
-// trees) and slower at n = 12 and n = 32 (B300, 2^16 to 3e6 nodes), so they
-// are used at n = 16 only.
-bool use_node_residual(const tlqr_factor_t* f) { return f->fixed_m > 0 && f->fixed_n == 16; }
+// Which float-float residual runs (options.residual): 1 = the row-per-thread
+// kernels, 2 = the node-organised bulk-copy kernels, 0 = the library's choice
+// per n (kResNodeDefault).  The node kernels need compile-time (n, m) and
+// 16-byte aligned matrix arrays; otherwise the row kernels run.
+bool res_node_default(int n) { return n == 12 || n == 16; }
+// polls of one mbarrier wait of the node residual before it gives up (each
+// poll may suspend the thread for a while, so this is ~a second or more)
+constexpr int kBarSpin = 1 << 20;
+bool use_node_residual(const tlqr_factor_t* f, const tlqr_problem& p) {
+  if (f->fixed_m == 0 || f->ts != 4) return false;
+  const int kind = f->opt.residual;
+  if (kind == 1 || (kind == 0 && !res_node_default(f->fixed_n))) return false;
+  auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15u) == 0; };
+  return al(p.Q) && al(p.A) && al(p.B) && al(p.R) && (!f->opt.has_M || al(p.M)) &&
+         (!f->opt.has_delta || al(p.Delta));
+}
 
 // ff = 1: float-float kernel on the FP32 pipe (refinement); ff = 0: plain FP64 kernel.
 cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, const double* x,
-                         const double* u, const double* y, int with_knorm, cudaStream_t st, int ff = 0) {
+                         const double* u, const double* y, int with_knorm, cudaStream_t st, int ff = 0,
+                         const unsigned char* dflag = nullptr) {
   ResidualArgs a{};
   const tlqr_plan_t* P = f->plan;
   a.N = P->N; a.n = f->opt.n; a.m = f->opt.m; a.with_knorm = with_knorm;
@@ -1049,7 +1095,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
     // split x, u, y once per call; for one tree ||z|| and ||b|| maxima come
     // from the same pass (a forest forms them per tree in the residual kernel)
     const size_t N = P->N, n = f->opt.n, m = f->opt.m;
-    const bool by_node = use_node_residual(f);      // node kernels form all four maxima themselves
+    const bool by_node = use_node_residual(f, p);   // node kernels form all four maxima themselves
     const int zs = (a.tree || by_node) ? -1 : 1, bs = (a.tree || by_node) ? -1 : 2;
     SplitList L{};
     auto add = [&](const double* src, float* hi, float* lo, size_t len, int slot) {
@@ -1070,12 +1116,20 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   }
   const size_t rows = (size_t)P->N * (2 * f->opt.n + f->opt.m);
   const int threads = 256;
-  const int blocks = (int)std::min<size_t>((rows + threads - 1) / threads, (size_t)f->sms * 32);
+  // grid-stride over the rows with at most 32 blocks per SM (measured faster
+  // than fewer blocks holding equal row counts, despite the uneven last rows)
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((rows + threads - 1) / threads, (size_t)f->sms * 32));
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
   EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr, P->N};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  if (ff && use_node_residual(f)) {
-    const rn::NodeArgs na{f->rwh, f->rwl, f->rwk};
+  if (ff && use_node_residual(f, p)) {
+    const rn::NodeArgs na{f->rwh,
+                          f->rwl,
+                          f->rwk,
+                          f->opt.has_delta ? dflag : nullptr,
+                          f->status,
+                          f->opt.spin_limit > 0 ? f->opt.spin_limit : kBarSpin,
+                          (f->opt.test_withhold & 2) ? 1 : 0};
     if ((e = dispatch_res_nodes(f->fixed_n, f->fixed_m, a, fa, na, f->sms, st, rc && rc->capture))) return e;
   } else if (a.tree) {
     if (ff) k_residual_ff_trees<<<blocks, threads, 0, st>>>(a, fa);
@@ -1445,13 +1499,16 @@ cudaError_t solve_impl(tlqr_factor_t* f, const double* q, const double* r, const
   });
 }
 
+// dflag: the factor's per-node "Delta_i is nonzero" flags when p holds the
+// matrices the factor was formed from (the node kernels then copy no zero
+// Delta block); null otherwise.
 cudaError_t residual_impl(tlqr_factor_t* f, const tlqr_problem& p, const double* x, const double* u,
-                          const double* y, int with_knorm, cudaStream_t st) {
+                          const double* y, int with_knorm, cudaStream_t st, const unsigned char* dflag = nullptr) {
   std::vector<uintptr_t> key = problem_key(p);
-  for (const void* v : {(const void*)x, (const void*)u, (const void*)y}) key.push_back(up(v));
+  for (const void* v : {(const void*)x, (const void*)u, (const void*)y, (const void*)dflag}) key.push_back(up(v));
   key.push_back((uintptr_t)with_knorm);
   return run_seq(f, &f->g_resid[with_knorm ? 1 : 0], key, st,
-                 [&](Recorder* rc) { return run_residual(f, rc, p, x, u, y, with_knorm, st, 1); });
+                 [&](Recorder* rc) { return run_residual(f, rc, p, x, u, y, with_knorm, st, 1, dflag); });
 }
 
 }  // namespace
@@ -1481,6 +1538,7 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   const int n = opts->n, m = opts->m;
   if (n < 1 || m < 1 || n > TLQR_MAX_DIM || m > TLQR_MAX_DIM) return TLQR_ERR_ARG;
   if (opts->precision != TLQR_PREC_FP64 && opts->precision != TLQR_PREC_MIXED) return TLQR_ERR_ARG;
+  if (opts->residual < 0 || opts->residual > 2) return TLQR_ERR_ARG;
   tlqr_factor_t* f = new (std::nothrow) tlqr_factor_t;
   if (!f) return TLQR_ERR_OOM;
   f->plan = plan;
@@ -1536,6 +1594,7 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   if (rc) { delete f; return rc; }
   const size_t N = plan->N, T = (size_t)plan->n_trees;
   if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_maxes, 4 * T * sizeof(unsigned long long));
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_gate, 2 * sizeof(double));
   if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_status, sizeof(int));
   if (err == cudaSuccess && f->dflag) err = cudaMemset(f->dflag, 0, N);
   if (err != cudaSuccess) {
@@ -1756,23 +1815,84 @@ extern "C" int tlqr_get_PK(tlqr_factor_t* f, int32_t mem, double* P, double* K, 
 }
 
 namespace {
+// Speculative refinement gate: the largest per-tree eta of the residual just
+// evaluated (slot-major maxima [4][T], the reduction of tree_stats) goes to
+// gate[0]; when it already meets the tolerance the residual vectors are
+// zeroed, so that the correction solve enqueued behind this kernel adds
+// exactly zero.  Every block forms eta itself (T words), so no grid sync.
+__global__ void k_refine_gate(const unsigned long long* maxes, int T, double tol, double* gate, double* rx,
+                              size_t nx, double* ru, size_t nu, double* rc, size_t nc) {
+  __shared__ double s_eta;
+  if (threadIdx.x == 0) {
+    double e = 0.0;
+    for (int t = 0; t < T; ++t) {
+      const double v0 = __longlong_as_double((long long)maxes[t]);
+      const double v1 = __longlong_as_double((long long)maxes[(size_t)T + t]);
+      const double v2 = __longlong_as_double((long long)maxes[2 * (size_t)T + t]);
+      const double v3 = __longlong_as_double((long long)maxes[3 * (size_t)T + t]);
+      const double den = v3 * v1 + v2;
+      double et = den > 0 ? v0 / den : v0;
+      if (!isfinite(v0)) et = INFINITY;
+      if (!(et <= e)) e = et;
+    }
+    s_eta = e;
+    if (blockIdx.x == 0) gate[0] = e;
+  }
+  __syncthreads();
+  if (!(s_eta <= tol)) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nx; t += stride) { rx[t] = 0.0; rc[t] = 0.0; }
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu; t += stride) ru[t] = 0.0;
+}
+
 // FP64 iterative refinement through the FP32 factors: the FP64 residual of
 // eq. (kkt) for the problem dp (matrices and right-hand side) is re-solved
 // and added to (x, u, y) until the largest per-tree eta <= refine_tol.
+// When the previous solve on this factor needed a step, the first step is
+// enqueued speculatively (residual, gate, correction, residual) and the host
+// waits once; the gate turns the correction into an exact no-op when the first
+// residual already met the tolerance, so the result equals the checked loop.
 int refine(tlqr_factor_t* f, const tlqr_problem& dp, double* x, double* u, double* y, cudaStream_t st) {
   int steps = 0, rc = 0;
   double absr = 0, eta = INFINITY;
-  for (;;) {
-    // residual graph: FP64 residual, ||.|| maxima and the status word to the host
-    if (residual_impl(f, dp, x, u, y, steps == 0 ? 1 : 0, st)) return TLQR_ERR_CUDA;
+  bool first = true;
+  if (f->speculate && f->opt.max_refine >= 1) {
+    const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+    if (residual_impl(f, dp, x, u, y, 1, st, f->dflag)) return TLQR_ERR_CUDA;
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((N * n + 255) / 256, (size_t)f->sms * 4));
+    k_refine_gate<<<blocks, 256, 0, st>>>(f->maxes, f->plan->n_trees, f->opt.refine_tol, f->d_gate, f->res_x,
+                                          N * n, f->res_u, N * m, f->res_c, N * n);
+    if (cudaGetLastError()) return TLQR_ERR_CUDA;
+    if (cudaMemcpyAsync(f->h_gate, f->d_gate, sizeof(double), cudaMemcpyDeviceToHost, st)) return TLQR_ERR_CUDA;
+    if (solve_impl(f, f->res_x, f->res_u, f->res_c, x, u, y, 1, st)) return TLQR_ERR_CUDA;
+    if (residual_impl(f, dp, x, u, y, 0, st, f->dflag)) return TLQR_ERR_CUDA;
     if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
     f->prof.harvest();
     if ((rc = map_status(*f->h_status))) { f->factored = false; return rc; }
     residual_stats(f, &absr, &eta);
+    steps = f->h_gate[0] <= f->opt.refine_tol ? 0 : 1;
+    first = false;
+  }
+  for (;;) {
+    if (first) {
+      // residual graph: FP64 residual, ||.|| maxima and the status word to the host
+      if (residual_impl(f, dp, x, u, y, 1, st, f->dflag)) return TLQR_ERR_CUDA;
+      if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+      f->prof.harvest();
+      if ((rc = map_status(*f->h_status))) { f->factored = false; return rc; }
+      residual_stats(f, &absr, &eta);
+      first = false;
+    }
     if (eta <= f->opt.refine_tol || steps >= f->opt.max_refine || !std::isfinite(eta)) break;
     if (solve_impl(f, f->res_x, f->res_u, f->res_c, x, u, y, 1, st)) return TLQR_ERR_CUDA;
     ++steps;
+    if (residual_impl(f, dp, x, u, y, 0, st, f->dflag)) return TLQR_ERR_CUDA;
+    if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+    f->prof.harvest();
+    if ((rc = map_status(*f->h_status))) { f->factored = false; return rc; }
+    residual_stats(f, &absr, &eta);
   }
+  f->speculate = steps >= 1;
   f->info.refine_steps = steps;
   f->info.eta = eta;
   f->info.abs_residual = absr;
@@ -1852,10 +1972,14 @@ extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solut
     if (!e) e = d2h(sol->y, y, N * n, st);
     if (e) return TLQR_ERR_CUDA;
   }
-  // one status read for factor, solve and recovery (synchronises the stream)
-  rc = read_status(f, st);
-  f->prof.harvest();
-  if (rc) { f->factored = false; return rc; }
+  // one status read for factor, solve and recovery (synchronises the stream);
+  // in MIXED precision the refinement has read it after the last kernel
+  // already unless P, K or host copies followed
+  if (f->opt.precision != TLQR_PREC_MIXED || sol->P || sol->K || sol->mem == TLQR_MEM_HOST) {
+    rc = read_status(f, st);
+    f->prof.harvest();
+    if (rc) { f->factored = false; return rc; }
+  }
   return TLQR_OK;
 }
 

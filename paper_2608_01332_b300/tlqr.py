@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(_HERE, "libtlqr.so")
 
 TLQR_OK = 0
 TLQR_ERR_ARG = 1
+TLQR_ERR_TIMEOUT = 7
 TLQR_MEM_DEVICE, TLQR_MEM_HOST = 0, 1
 TLQR_PREC_FP64, TLQR_PREC_MIXED = 0, 1
 TLQR_OP_ROOT, TLQR_OP_RAKE, TLQR_OP_COMPRESS = 0, 1, 2
@@ -43,7 +44,7 @@ class tlqr_options(ctypes.Structure):
     _fields_ = [("n", _i32), ("m", _i32), ("precision", _i32), ("has_M", _i32), ("has_delta", _i32),
                 ("max_refine", _i32), ("refine_tol", ctypes.c_double), ("use_graphs", _i32),
                 ("generic_kernels", _i32), ("async_ops", _i32), ("spin_limit", _i32), ("test_withhold", _i32),
-                ("tail_ops", _i32), ("async_solve", _i32), ("reserved", _i32 * 1)]
+                ("tail_ops", _i32), ("async_solve", _i32), ("residual", _i32)]
 
 
 class tlqr_problem(ctypes.Structure):
@@ -66,8 +67,8 @@ class tlqr_ipm_info(ctypes.Structure):
 
 
 class tlqr_autotune_entry(ctypes.Structure):
-    _fields_ = [("async_ops", _i32), ("async_solve", _i32), ("tail_ops", _i32), ("status", _i32),
-                ("ms", ctypes.c_double)]
+    _fields_ = [("async_ops", _i32), ("async_solve", _i32), ("tail_ops", _i32), ("residual", _i32),
+                ("status", _i32), ("ms", ctypes.c_double)]
 
 
 class tlqr_plan_stats_t(ctypes.Structure):
@@ -260,11 +261,11 @@ def tlqr_plan_schedule(plan, N: int):
 
 def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
                  refine_tol=1e-8, use_graphs=True, generic_kernels=False, async_ops=0, spin_limit=0,
-                 test_withhold=False, tail_ops=0, async_solve=0) -> tlqr_options:
+                 test_withhold=False, tail_ops=0, async_solve=0, residual=0) -> tlqr_options:
     o = tlqr_options()
-    o.tail_ops, o.async_solve = int(tail_ops), int(async_solve)
+    o.tail_ops, o.async_solve, o.residual = int(tail_ops), int(async_solve), int(residual)
     o.generic_kernels = int(bool(generic_kernels))
-    o.async_ops, o.spin_limit, o.test_withhold = int(async_ops), int(spin_limit), int(bool(test_withhold))
+    o.async_ops, o.spin_limit, o.test_withhold = int(async_ops), int(spin_limit), int(test_withhold)
     o.n, o.m, o.precision = int(n), int(m), int(precision)
     o.has_M, o.has_delta = int(bool(has_M)), int(bool(has_delta))
     o.max_refine, o.refine_tol, o.use_graphs = int(max_refine), float(refine_tol), int(bool(use_graphs))
@@ -354,8 +355,8 @@ def tlqr_autotune(plan, opts: tlqr_options, data: dict, trials: int = 5, stream=
     cnt = np.zeros(1, dtype=np.int32)
     _check(lib().tlqr_autotune(plan, ctypes.byref(opts), ctypes.byref(p), int(trials), ctypes.byref(best), table,
                                32, _iptr(cnt), _stream(stream)), "tlqr_autotune")
-    rows = [dict(async_ops=t.async_ops, async_solve=t.async_solve, tail_ops=t.tail_ops, status=t.status, ms=t.ms)
-            for t in table[:int(cnt[0])]]
+    rows = [dict(async_ops=t.async_ops, async_solve=t.async_solve, tail_ops=t.tail_ops, residual=t.residual,
+                 status=t.status, ms=t.ms) for t in table[:int(cnt[0])]]
     return best, rows
 
 

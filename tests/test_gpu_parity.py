@@ -599,3 +599,45 @@ def test_forest_residual_is_per_tree(permute):
         assert abs(absr[t] - ref["abs"]) <= 1e-12 * ref["abs"]
         assert abs(eta[t] - ref["eta"]) <= 1e-12 * ref["eta"]
     assert stats["eta"] == eta.max()
+
+
+def test_speculative_refinement_equals_checked_refinement():
+    """A MIXED factor whose last solve needed a refinement step enqueues the
+    next solve's first step without waiting (residual, device gate,
+    correction, residual).  The result must not depend on it: solving B after
+    A on one factor object equals solving B on a fresh one, bitwise -- for a B
+    that needs a step, and for one whose first residual already meets the
+    tolerance (the gate zeroes the correction's right-hand side)."""
+    rng = inputs.rng_for(96)
+    p = inputs.long_trunk_tree(rng, trunk=200, total=2000)
+    n, m = 12, 4
+    A = inputs.problem_data(p, n, m, rng)
+    B = inputs.problem_data(p, n, m, rng)
+    Z = dict(B)
+    Z.update(q=np.zeros_like(B["q"]), r=np.zeros_like(B["r"]), c=np.zeros_like(B["c"]))
+    N = len(p)
+
+    def run(seq):
+        s = tlqr.TreeLQR(p, n, m, MIXED)
+        outs = []
+        try:
+            for data in seq:
+                x = torch.zeros((N, n), dtype=torch.float64, device="cuda")
+                u = torch.zeros((N, m), dtype=torch.float64, device="cuda")
+                y = torch.zeros((N, n), dtype=torch.float64, device="cuda")
+                tlqr.tlqr_solve(s.f, {k: dev(v) for k, v in data.items()}, x, u, y)
+                torch.cuda.synchronize()
+                outs.append((x.cpu().numpy(), u.cpu().numpy(), y.cpu().numpy(), tlqr.tlqr_last_info(s.f)))
+        finally:
+            s.close()
+        return outs
+
+    seq = run([A, B, Z, B])
+    assert seq[0][3]["refine_steps"] >= 1                  # A needs a step: B's solve speculates
+    alone_B = run([B])[0]
+    alone_Z = run([Z])[0]
+    for got, ref in ((seq[1], alone_B), (seq[3], alone_B), (seq[2], alone_Z)):
+        for a, b in zip(got[:3], ref[:3]):
+            np.testing.assert_array_equal(a, b)
+        assert got[3]["refine_steps"] == ref[3]["refine_steps"]
+    assert seq[2][3]["refine_steps"] == 0 and np.all(seq[2][0] == 0.0)
