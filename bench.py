@@ -815,7 +815,7 @@ def run_ours(args, rank, world, dist):
         s64.close()
 
     # end to end through the public API with pinned host buffers
-    e2e = None
+    e2e = e2e_update = None
     if not args.no_e2e and (args.workload == "long_trunk" or args.e2e):
         hd = {k: (None if v is None else v.cpu().pin_memory()) for k, v in dd.items()}
         hx = torch.zeros((N, n), dtype=torch.float64).pin_memory()
@@ -838,6 +838,33 @@ def run_ours(args, rank, world, dist):
             e2e_tot = float(t.item())
         e2e = {"value": world * N * args.steps / e2e_tot, "unit": "nodes/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+        # the interior-point / receding-horizon pattern through tlqr_update_solve: diagonal
+        # increments of Q and R and the right-hand side cross the bus, the rest stays resident;
+        # the increments alternate in sign so the problem returns to the original every 2 steps
+        hdq = torch.full((N, n), 1e-2, dtype=torch.float64).pin_memory()
+        hdr = torch.full((N, m), 1e-2, dtype=torch.float64).pin_memory()
+        hdqn, hdrn = (-hdq).pin_memory(), (-hdr).pin_memory()
+        upd_in = dict(q=hd["q"], r=hd["r"], c=hd["c"])
+        tlqr.tlqr_update_solve(solver.f, hx, hu, hy, dq=hdq, dr=hdr, stream=stream, **upd_in)
+        tlqr.tlqr_update_solve(solver.f, hx, hu, hy, dq=hdqn, dr=hdrn, stream=stream, **upd_in)
+        barrier()
+        upd_t = []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            tlqr.tlqr_update_solve(solver.f, hx, hu, hy, dq=hdq if k % 2 == 0 else hdqn,
+                                   dr=hdr if k % 2 == 0 else hdrn, stream=stream, **upd_in)
+            upd_t.append(time.perf_counter() - t0)
+        barrier()
+        upd_tot = sum(upd_t)
+        if dist is not None:
+            t = torch.tensor([upd_tot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            upd_tot = float(t.item())
+        e2e_update = {"value": world * N * args.steps / upd_tot, "unit": "nodes/s",
+                      "h2d_bytes_per_step": (hdq.numel() + hdr.numel() + sum(v.numel() for v in upd_in.values())) * 8,
+                      "d2h_bytes_per_step": d2h,
+                      "call": "tlqr_update_solve: Q, R diagonal increments and q, r, c uploaded each step; "
+                              "A, B, Delta and the off-diagonal entries stay resident; factor + solve + refinement"}
 
     if rank != 0:
         solver.close()
@@ -889,11 +916,13 @@ def run_ours(args, rank, world, dist):
         "config": cfg,
         "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
         "eta": res["eta"], "refine_steps": info["refine_steps"] if mixed else 0,
+        "fp64_resolves": info.get("fp64_resolves", 0),
         "tree_eta": {"max": float(tree_eta.max()), "p50": float(np.percentile(tree_eta, 50))} if forest else None,
         "factor_solve": split,
         "multi_rhs": multi,
         "plain_fp64": fp64,
         "e2e": e2e,
+        "e2e_update": e2e_update,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
         "roofline": roof,

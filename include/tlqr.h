@@ -121,6 +121,12 @@ typedef struct {
                             blocks staged by bulk copies (TMA), compile-time (n, m)
                             and 16-byte aligned matrix arrays only (else 1);
                             0 = the library's choice for n                       */
+  int32_t fp64_resolve;  /* MIXED, compile-time-n kernels: 0 (default) = a linear
+                            solve of the contraction (S = I + C U, I + C P~ of eq.
+                            (compress-intermediates), F = I + Delta P of eq. (FW))
+                            whose FP32 pivots span more than 1e4 is solved again in
+                            FP64 and rounded to FP32 (up to 4096 per factorisation;
+                            tlqr_info.fp64_resolves counts them); < 0 = never       */
 } tlqr_options;
 
 #define TLQR_MAX_DIM 64
@@ -159,6 +165,8 @@ typedef struct {
   int32_t refine_steps;  /* MIXED: refinement steps taken by the last solve      */
   double eta;            /* backward error of the last solve, if it computed one   */
   double abs_residual;   /* ||K z - b||_inf of the last solve, if computed         */
+  int32_t fp64_resolves; /* MIXED: eliminations of the last factorisation solved
+                            again in FP64 (see tlqr_options.fp64_resolve)        */
 } tlqr_info;
 
 /* ------------------------------------------------------------------ plan */
@@ -306,6 +314,22 @@ int tlqr_solve_adjoint(tlqr_factor_t *f, int32_t mem, const double *xbar, const 
  * the last factorisation into P [N][n][n] and K [N][m][n] (either may be
  * NULL).  In MIXED precision these are the FP32 factors widened to FP64. */
 int tlqr_get_PK(tlqr_factor_t *f, int32_t mem, double *P, double *K, void *stream);
+
+/* Resident-problem update and re-solve, for interior-point and
+ * receding-horizon loops in which only diagonals and the right-hand side
+ * change between solves.  The problem the factor last factorised (its own
+ * staged copy when that problem came from host memory, else the caller's
+ * device arrays, which this call then modifies) is updated in place --
+ *   Q_i += diag(dq_i) (dq: N x n),  R_i += diag(dr_i) (dr: N x m)  (NULL: none)
+ *   q, r, c replaced by the arrays given (NULL: unchanged)
+ * -- then factorised and solved exactly as by tlqr_solve (refinement in
+ * MIXED), writing sol.  With mem = TLQR_MEM_HOST only dq, dr, q, r, c cross
+ * the bus: N (3n + 2m) doubles instead of the whole problem.  The matrices
+ * A, B, M, Delta and the off-diagonal entries of Q and R stay as they were.
+ * Errors: TLQR_ERR_ARG; TLQR_ERR_STATE when no problem has been factorised on
+ * f yet; otherwise as tlqr_solve. */
+int tlqr_update_solve(tlqr_factor_t *f, int32_t mem, const double *dq, const double *dr, const double *q,
+                      const double *r, const double *c, tlqr_solution *sol, void *stream);
 
 /* FP64 KKT residual of eq. (kkt) for a given (x, u, y) on the GPU.
  * stats[0] = ||K z - b||_inf, stats[1] = eta = ||K z - b||_inf /

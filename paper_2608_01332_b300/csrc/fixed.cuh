@@ -276,8 +276,10 @@ struct GjBuf {
 // work).  Double-buffered broadcast rows need one __syncwarp per step.
 // bc: GjBuf<T, N, R>::elems shared elements of this group, 16-byte aligned.
 // Returns false (uniformly in the group) on a zero or nonfinite pivot.
+// ratio: largest |pivot| over smallest |pivot| (the same in every lane of the
+// group), a lower bound on the condition number of S.
 template <typename T, int N, int G, int R>
-__device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kpos) {
+__device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kpos, float& ratio) {
   using Bf = GjBuf<T, N, R>;
   using V = typename Vec<T>::V;
   constexpr int W = Vec<T>::W;
@@ -285,6 +287,7 @@ __device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kp
   kpos = N;
   bool ok = true;
   T myinv = T(1);
+  T imin = T(INFINITY), imax = T(0);
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     T* row = bc + (k & 1) * Bf::ROW;
@@ -314,6 +317,8 @@ __device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kp
     __syncwarp();
     const T inv = row[Bf::NP + Bf::RP];
     ok = ok && tfinite(inv) && inv != T(0);
+    imin = fmin(imin, fabs(inv));
+    imax = fmax(imax, fabs(inv));
     if (gl != p && gl < N) {
       const T l = a[k] * inv;
 #pragma unroll
@@ -335,6 +340,139 @@ __device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kp
 #pragma unroll
   for (int c = 0; c < R; ++c) b[c] *= myinv;
   __syncwarp();
+  ratio = (float)(imax / imin);
+  return ok;
+}
+template <typename T, int N, int G, int R>
+__device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kpos) {
+  float ratio;
+  return ggj<T, N, G, R>(a, b, gl, bc, kpos, ratio);
+}
+
+// ---------------------------------------------------------------- FP64 re-solves
+// An FP32 elimination whose pivots span more than kSolveRatio (a lower bound
+// on the condition number of S = I + C P~, I + C U or F = I + Delta P) has
+// lost about log10(ratio) of FP32's seven digits.  Such a group solves the
+// system again in FP64: S and the right-hand side are formed in FP64 from the
+// operands (FP32 workspace blocks, FP64 problem data), written to a slot of a
+// global scratch (one slot per re-solve of a factorisation, handed out by an
+// atomic ticket), eliminated there by the group's lanes, and the solution is
+// rounded to FP32.  When the slots run out the FP32 solution stands.  The
+// functions below are not inlined: they run rarely and must not add registers
+// to the kernels that call them.
+constexpr float kSolveRatio = 1e4f;
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+}
+
+// A slot for this group (leader takes the ticket), or null when none is left.
+template <int G>
+__device__ __forceinline__ double* redo_slot(int* count, int cap, double* scratch, size_t slot, int gl) {
+  int t = 0;
+  if (gl == 0) t = atomicAdd(count, 1);
+  t = __shfl_sync(group_mask<G>(), t, 0, G);
+  return t < cap ? scratch + (size_t)t * slot : nullptr;
+}
+
+// Gauss-Jordan elimination with partial pivoting of a (n x n, row stride lda)
+// against b (n x nb, row stride ldb) in global memory by the G lanes of a
+// group, rows kept in place (lane gl < n owns row gl).  On return lane gl's
+// row of b holds row *kpos of X = a^{-1} b.  False on a zero or nonfinite pivot.
+template <int G>
+__device__ __forceinline__ bool gj64_rows(double* a, int lda, double* b, int ldb, int n, int nb, int gl, int& kpos) {
+  const unsigned mask = group_mask<G>();
+  bool done = gl >= n, ok = true;
+  int kp = n;
+  double myinv = 1.0;
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    double best = done ? -1.0 : fabs(a[gl * lda + k]);
+    if (isnan(best)) best = INFINITY;
+    int bl = gl;
+#pragma unroll
+    for (int off = G / 2; off; off >>= 1) {
+      const double ov = __shfl_xor_sync(mask, best, off, G);
+      const int ol = __shfl_xor_sync(mask, bl, off, G);
+      if (ov > best || (ov == best && ol < bl)) { best = ov; bl = ol; }
+    }
+    if (gl == bl) {
+      kp = k;
+      done = true;
+      myinv = 1.0 / a[gl * lda + k];
+    }
+    const double pinv = __shfl_sync(mask, myinv, bl, G);
+    ok = ok && isfinite(pinv) && pinv != 0.0;
+    __syncwarp(mask);
+    if (gl != bl && gl < n) {
+      const double l = a[gl * lda + k] * pinv;
+#pragma unroll 1
+      for (int c = k + 1; c < n; ++c) a[gl * lda + c] = fma(-l, a[bl * lda + c], a[gl * lda + c]);
+#pragma unroll 1
+      for (int c = 0; c < nb; ++c) b[gl * ldb + c] = fma(-l, b[bl * ldb + c], b[gl * ldb + c]);
+    }
+    __syncwarp(mask);
+  }
+  if (gl < n) {
+#pragma unroll 1
+    for (int c = 0; c < nb; ++c) b[gl * ldb + c] *= myinv;
+  }
+  __syncwarp(mask);
+  kpos = kp;
+  return ok;
+}
+
+// Forms rows gl < N of the system in the slot, eliminates it, and writes the
+// solution, rounded to FP32, into the shared rows `dst` (row stride ldd) where
+// the FP32 elimination would have put it:
+//   kind 0 (rake, reconstruction): S = I + L R,    B = B1            (N x N)
+//   kind 1 (compression):          S = I + L R,    B = [B1 | L B2^T] (N x 2N;
+//                                  the second block goes to column col2)
+//   kind 2 (local factor):         S = I + L64 R,  B = I             (N x N)
+// L, R, B1, B2: FP32 rows (shared or global memory, leading dimensions);
+// L64: FP64 rows (problem data).  Slot layout: S (N x N), then B (N x nb).
+enum : int { RS_TAU = 0, RS_COMPRESS = 1, RS_LOCAL = 2 };
+template <int N, int G>
+__device__ __noinline__ bool resolve64(double* sc, int kind, const float* L, int ldl, const double* L64,
+                                       const float* R, int ldr, const float* B1, int ldb1, const float* B2,
+                                       int ldb2, float* dst, int ldd, int col2, int gl) {
+  const int nb = kind == RS_COMPRESS ? 2 * N : N;
+  double *a = sc, *b = sc + N * N;
+  if (gl < N) {
+#pragma unroll 1
+    for (int c = 0; c < N; ++c) {
+      double v = c == gl ? 1.0 : 0.0;
+#pragma unroll 1
+      for (int t = 0; t < N; ++t) {
+        const double l = kind == RS_LOCAL ? L64[gl * ldl + t] : (double)L[gl * ldl + t];
+        v = fma(l, (double)R[t * ldr + c], v);
+      }
+      a[gl * N + c] = v;
+    }
+#pragma unroll 1
+    for (int c = 0; c < N; ++c) b[gl * nb + c] = kind == RS_LOCAL ? (c == gl ? 1.0 : 0.0) : (double)B1[gl * ldb1 + c];
+    if (kind == RS_COMPRESS) {
+#pragma unroll 1
+      for (int c = 0; c < N; ++c) {
+        double v = 0.0;
+#pragma unroll 1
+        for (int t = 0; t < N; ++t) v = fma((double)L[gl * ldl + t], (double)B2[c * ldb2 + t], v);
+        b[gl * nb + N + c] = v;
+      }
+    }
+  }
+  __syncwarp(group_mask<G>());
+  int kp;
+  const bool ok = gj64_rows<G>(a, N, b, nb, N, nb, gl, kp);
+  if (gl < N) {
+#pragma unroll 1
+    for (int c = 0; c < N; ++c) dst[kp * ldd + c] = (float)b[gl * nb + c];
+    if (kind == RS_COMPRESS) {
+#pragma unroll 1
+      for (int c = 0; c < N; ++c) dst[kp * ldd + col2 + c] = (float)b[gl * nb + N + c];
+    }
+  }
   return ok;
 }
 
@@ -361,8 +499,8 @@ struct TauSmem {
 // right-hand side and as the transposed left operand of the last product -- so
 // that a warp holds two staged matrices instead of three.
 template <typename T, int N>
-__device__ __forceinline__ bool tau_group_tc(const Grp& g, const T* Ug, const T* Ag, const T* Cg, const T* Pg, T* out,
-                                             T* sm) {
+__device__ __forceinline__ bool tau_group_tc(const Ws<T>& w, const Grp& g, const T* Ug, const T* Ag, const T* Cg,
+                                             const T* Pg, T* out, T* sm) {
   using Dm = D<T, N>;
   constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT;
   T *sU = sm, *sY = sm + MAT, *bc = sm + 2 * MAT;
@@ -378,8 +516,16 @@ __device__ __forceinline__ bool tau_group_tc(const Grp& g, const T* Ug, const T*
   grow_load<T, N>(b, Ag + r * N);               // row r of A (right-hand side)
   __syncwarp();
   int kpos;
-  const bool ok = ggj<T, N, G, N>(x, b, g.gl, bc, kpos);   // Y = (I + C U)^{-1} A, row kpos in b
-  if (g.gl < N) row_store<T, N>(sY + kpos * LD, b);
+  float pr;
+  bool ok = ggj<T, N, G, N>(x, b, g.gl, bc, kpos, pr);   // Y = (I + C U)^{-1} A, row kpos in b
+  bool stored = false;
+  if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
+    if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, g.gl)) {
+      ok = resolve64<N, G>(sc, RS_TAU, Cg, N, nullptr, sU, LD, Ag, N, nullptr, 0, sY, LD, 0, g.gl);
+      stored = true;
+    }
+  }
+  if (!stored && g.gl < N) row_store<T, N>(sY + kpos * LD, b);
   __syncwarp();
   tc::gemm32<false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, true);   // Z = U Y over U
   tc::gemm32<true, false>(Ag, N, sU, LD, Pg, N, out, N, g.valid);      // P + A^T Z
@@ -387,9 +533,9 @@ __device__ __forceinline__ bool tau_group_tc(const Grp& g, const T* Ug, const T*
 }
 
 template <typename T, int N>
-__device__ __forceinline__ bool tau_group(const Grp& g, const T* Ug, const T* Ag, const T* Cg, const T* Pg, T* out,
-                                          T* sm) {
-  if constexpr (kTensorCores<T, N>) return tau_group_tc<T, N>(g, Ug, Ag, Cg, Pg, out, sm);
+__device__ __forceinline__ bool tau_group(const Ws<T>& w, const Grp& g, const T* Ug, const T* Ag, const T* Cg,
+                                          const T* Pg, T* out, T* sm) {
+  if constexpr (kTensorCores<T, N>) return tau_group_tc<T, N>(w, g, Ug, Ag, Cg, Pg, out, sm);
   using Dm = D<T, N>;
   constexpr int G = Dm::G, LD = Dm::LD, MAT = Dm::MAT;
   T *sU = sm, *sA = sm + MAT, *sY = sm + 2 * MAT, *bc = sm + 3 * MAT;
@@ -410,8 +556,18 @@ __device__ __forceinline__ bool tau_group(const Grp& g, const T* Ug, const T* Ag
   row_load<T, N>(b, sA + r * LD);               // row r of A (right-hand side)
   __syncwarp();
   int kpos;
-  const bool ok = ggj<T, N, G, N>(x, b, g.gl, bc, kpos);   // Y = (I + C U)^{-1} A, row kpos in b
-  if (g.gl < N) row_store<T, N>(sY + kpos * LD, b);
+  float pr;
+  bool ok = ggj<T, N, G, N>(x, b, g.gl, bc, kpos, pr);   // Y = (I + C U)^{-1} A, row kpos in b
+  bool stored = false;
+  if constexpr (sizeof(T) == 4) {
+    if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
+      if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, g.gl)) {
+        ok = resolve64<N, G>(sc, RS_TAU, Cg, N, nullptr, sU, LD, sA, LD, nullptr, 0, sY, LD, 0, g.gl);
+        stored = true;
+      }
+    }
+  }
+  if (!stored && g.gl < N) row_store<T, N>(sY + kpos * LD, b);
   __syncwarp();
   T z[N];
   {
@@ -444,7 +600,7 @@ __global__ void __launch_bounds__(128, kRakeBlocks<T, N>) kf_rake(Ws<T> w, int b
   T* sm = reinterpret_cast<T*>(smem_raw + g.gid * TauSmem<T, N>::bytes);
   const int rr = begin + op, j = w.rake_leaf[rr];
   const size_t o = (size_t)j * N * N;
-  const bool ok = tau_group<T, N>(g, w.U + o, w.Ea + o, w.Ec + o, w.Ep + o, w.contrib + (size_t)rr * N * N, sm);
+  const bool ok = tau_group<T, N>(w, g, w.U + o, w.Ea + o, w.Ec + o, w.Ep + o, w.contrib + (size_t)rr * N * N, sm);
   if (!ok && g.valid && g.gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
 }
 
@@ -456,7 +612,7 @@ __global__ void __launch_bounds__(128, kRakeBlocks<T, N>) kf_expand(Ws<T> w, int
   T* sm = reinterpret_cast<T*>(smem_raw + g.gid * TauSmem<T, N>::bytes);
   const int rr = begin + op, j = w.comp_j[rr], k = w.comp_k[rr];
   const size_t oj = (size_t)j * N * N;
-  const bool ok = tau_group<T, N>(g, w.U + (size_t)k * N * N, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm);
+  const bool ok = tau_group<T, N>(w, g, w.U + (size_t)k * N * N, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm);
   if (!ok && g.valid && g.gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
 }
 
@@ -511,8 +667,16 @@ __device__ __forceinline__ bool compress_op_tc(const Ws<T>& w, int rr, const Grp
   for (int c = 0; c < 2 * YW; ++c) b[c] = c < N ? t1[c] : (c >= YW && c < YW + N) ? t2[c - YW] : T(0);
   __syncwarp();
   int kpos;
-  const bool okf = ggj<T, N, G, 2 * YW>(s, b, gl, bc, kpos);   // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T]
-  if (gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
+  float pr;
+  bool okf = ggj<T, N, G, 2 * YW>(s, b, gl, bc, kpos, pr);   // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T]
+  bool stored = false;
+  if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
+    if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, gl)) {
+      okf = resolve64<N, G>(sc, RS_COMPRESS, sCl, LD, nullptr, sPt, LD, Al, N, Ar, N, sY, LD2, YW, gl);
+      stored = true;
+    }
+  }
+  if (!stored && gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
   tc::gemm32<false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, true);             // W = P~ Y1 over C_l
   tc::gemm32<true, false>(Al, N, sCl, LD, w.Ep + oj, N, w.Ep + ok_, N, g.valid);   // P_new = P_l + A_l^T W
@@ -570,8 +734,18 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   }
   __syncwarp();
   int kpos;
-  const bool okf = ggj<T, N, G, 2 * YW>(s, b, gl, bc, kpos);   // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
-  if (gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
+  float pr;
+  bool okf = ggj<T, N, G, 2 * YW>(s, b, gl, bc, kpos, pr);   // [Y1 | Y2] = S^{-1} [A_l | C_l A_r^T], row kpos
+  bool stored = false;
+  if constexpr (sizeof(T) == 4) {
+    if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
+      if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, gl)) {
+        okf = resolve64<N, G>(sc, RS_COMPRESS, sCl, LD, nullptr, sPt, LD, sAl, LD, sAr, LD, sY, LD2, YW, gl);
+        stored = true;
+      }
+    }
+  }
+  if (!stored && gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
   // A_new = A_r Y1, C_new = C_r + A_r Y2  (rows r); C_r read before slot k is overwritten
   T an[N], cn[N];
@@ -758,7 +932,7 @@ __global__ void kf_async(Ws<T> w, AsyncArgs a) {
     if (kind == AK_RAKE) {
       const int j = w.rake_leaf[idx];
       const size_t o = (size_t)j * NN;
-      ok = tau_group<T, N>(g, w.U + o, w.Ea + o, w.Ec + o, w.Ep + o, w.contrib + (size_t)idx * NN, sm);
+      ok = tau_group<T, N>(w, g, w.U + o, w.Ea + o, w.Ec + o, w.Ep + o, w.contrib + (size_t)idx * NN, sm);
     } else if (kind == AK_ABSORB) {
       const int i = w.seg_parent[idx], b = w.seg_start[idx], e = w.seg_start[idx + 1];
       T* Ui = w.U + (size_t)i * NN;
@@ -773,7 +947,7 @@ __global__ void kf_async(Ws<T> w, AsyncArgs a) {
     } else {
       const int j = w.comp_j[idx], k = w.comp_k[idx];
       const size_t oj = (size_t)j * NN;
-      ok = tau_group<T, N>(g, w.U + (size_t)k * NN, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm);
+      ok = tau_group<T, N>(w, g, w.U + (size_t)k * NN, w.Ea + oj, w.Ec + oj, w.Ep + oj, w.U + oj, sm);
     }
     if (!ok && valid && gl == 0) atomicCAS(w.status, 0, ST_SINGULAR);
     async_publish(a, pos, valid, gl);
@@ -1354,8 +1528,19 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
 #pragma unroll
     for (int c = 0; c < N; ++c) { f[c] += (c == r) ? T(1) : T(0); e[c] = (c == r) ? T(1) : T(0); }
     int kpos;
-    ok = ggj<T, N, G, N>(f, e, gl, bc, kpos);  // rows of F^{-1}
-    if (gl < N) row_store<T, N>(sFi + kpos * LD, e);
+    float pr;
+    ok = ggj<T, N, G, N>(f, e, gl, bc, kpos, pr);  // rows of F^{-1}
+    bool stored = false;
+    if constexpr (sizeof(T) == 4) {
+      if (w.redo_count && dnz && g.valid && !(pr <= kSolveRatio)) {
+        if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, gl)) {
+          ok = resolve64<N, G>(sc, RS_LOCAL, nullptr, N, w.Delta + oj, sP, LD, nullptr, 0, nullptr, 0, sFi, LD, 0,
+                               gl);
+          stored = true;
+        }
+      }
+    }
+    if (!stored && gl < N) row_store<T, N>(sFi + kpos * LD, e);
     __syncwarp();
     if (dnz) {
       zero(wrow);

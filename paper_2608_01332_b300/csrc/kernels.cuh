@@ -44,6 +44,13 @@ struct Ws {
   T *U, *Ea, *Ec, *Ep, *contrib;
   T *K, *Tm, *Tr, *W, *Finv, *LG;
   unsigned char* dflag;   // per node: Delta_i has a nonzero entry
+  // FP64 re-solves of ill-conditioned eliminations (FP32 compile-time-n
+  // kernels): a ticket counter, the number of slots and the slots (slot
+  // doubles each); redo_count == nullptr disables them
+  int* redo_count;
+  int redo_cap;
+  double* redo_scratch;
+  size_t redo_slot;
   // solve workspace
   T *h, *z, *s, *cv, *bv, *kv, *xs;
   int* status;

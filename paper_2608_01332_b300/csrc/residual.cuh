@@ -28,6 +28,7 @@ struct ResidualArgs {
   unsigned long long* maxes;   // [0] ||res||, [1] ||z||, [2] ||b||, [3] ||K|| (row sums); slot-major [4][T]
   const int* tree;             // forest: tree ordinal of each node (null: one tree)
   int T;                       // number of trees (1 for a single tree)
+  const unsigned char* dflag;  // per node: Delta_i has a nonzero entry (null: every Delta_i is read)
 };
 
 __device__ __forceinline__ double amax(double acc, double v) { return isnan(v) ? INFINITY : fmax(acc, fabs(v)); }
@@ -129,7 +130,7 @@ __device__ __forceinline__ double fp64_row(const ResidualArgs& a, size_t t, bool
   const double* yi = a.y + (size_t)i * n;
   double s = a.c[tc] - a.x[tc];
   rs = 1.0;
-  if (a.Delta) {
+  if (a.Delta && (!a.dflag || a.dflag[i])) {
     const double* Dr = a.Delta + (size_t)i * nn + (size_t)r * n;
     for (int b = 0; b < n; ++b) { s = fma(-Dr[b], yi[b], s); if (ks) rs += fabs(Dr[b]); }
   }
@@ -478,7 +479,7 @@ __device__ __forceinline__ double ff_row(const ResidualArgs& a, const FFArgs& f,
   ff_add(s, a.c[tc]);
   ff_add2(s, -f.xh[tc], -f.xl[tc]);
   rs = 1.f;
-  if (a.Delta) {
+  if (a.Delta && (!a.dflag || a.dflag[i])) {
     const double* Dr = a.Delta + (size_t)i * nn + (size_t)r * n;
 #pragma unroll 4
     for (int b = 0; b < n; ++b) {

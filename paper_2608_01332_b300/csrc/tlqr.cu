@@ -36,6 +36,8 @@ namespace {
 
 constexpr int kMaxWarpsPerBlock = 8;
 constexpr int kTailOps = 128;        // per-phase operation count below which rounds join the tail kernel
+// FP64 re-solve slots per factorisation (3 n^2 doubles each)
+constexpr int kRedoCap = 4096;
 constexpr int kTailThreads = fx::kTailBlock;
 constexpr int kPanel = 8;            // right-hand sides per panel of tlqr_solve_rhs_panel
 constexpr int kAsyncOps = 1024;     // default: rounds with at most this many operations run level-asynchronously
@@ -457,6 +459,10 @@ struct tlqr_factor_t {
   bool speculate = false;                   // the last mixed solve needed a refinement step
   int* h_status = nullptr;                  // pinned mirror
   double* stage = nullptr;                  // FP64 staging (host-memory calls), lazily allocated
+  double* upd = nullptr;                    // diagonal increments of tlqr_update_solve (when the staged P is too small)
+  double* redo_scratch = nullptr;           // FP64 re-solve slots (see fixed.cuh, kSolveRatio)
+  int redo_cap = 0;
+  size_t redo_slot = 0;
   size_t arena_bytes = 0;                   // the one device allocation holding plan arrays + workspace
   size_t stage_elems = 0;
   // problem pointers of the last factorisation (device), for refinement/residual
@@ -499,6 +505,10 @@ struct tlqr_factor_t {
     w.dflag = dflag;
     w.h = (T*)h; w.z = (T*)z; w.s = (T*)s; w.cv = (T*)cv; w.bv = (T*)bv; w.kv = (T*)kv; w.xs = (T*)xs;
     w.status = status;
+    w.redo_count = redo_scratch ? status + 1 : nullptr;
+    w.redo_cap = redo_cap;
+    w.redo_scratch = redo_scratch;
+    w.redo_slot = redo_slot;
     w.nrhs = 1;
     w.sv = (size_t)P->N * opt.n;
     w.sm = (size_t)P->N * opt.m;
@@ -612,7 +622,15 @@ void carve_factor(tlqr_factor_t* f, Carve& c) {
   f->h = c.take(N * n * ts); f->z = c.take(N * n * ts); f->s = c.take(N * n * ts); f->cv = c.take(nrake * n * ts);
   f->bv = c.take(N * n * ts); f->kv = c.take(N * m * ts); f->xs = c.take(N * n * ts);
   f->dflag = c.take<unsigned char>(N, 1);
-  f->status = c.take<int>(1, sizeof(int));
+  f->status = c.take<int>(2, sizeof(int));          // [0] status word, [1] FP64 re-solve tickets
+  f->redo_scratch = nullptr;
+  f->redo_cap = 0;
+  f->redo_slot = 0;
+  if (f->ts == 4 && f->fixed_n > 0 && f->opt.fp64_resolve >= 0) {
+    f->redo_cap = kRedoCap;
+    f->redo_slot = 3 * nn;                              // S (n x n) and a right-hand side of up to 2n columns
+    f->redo_scratch = c.take<double>((size_t)f->redo_cap * f->redo_slot, 8);
+  }
   f->res_x = c.take<double>(N * n, 8); f->res_u = c.take<double>(N * m, 8); f->res_c = c.take<double>(N * n, 8);
   f->maxes = c.take<unsigned long long>(4 * (size_t)P->n_trees, 8);
   f->d_gate = c.take<double>(2, 8);
@@ -751,7 +769,7 @@ cudaError_t run_factor(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, cu
   constexpr int MX = MF > 0 ? MF : 2;
   constexpr int G = fx::D<T, NX>::G;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(f->status, 0, sizeof(int), st))) return e;
+  if ((e = cudaMemsetAsync(f->status, 0, 2 * sizeof(int), st))) return e;
   if constexpr (MF > 0) {
     if ((e = launch_groups(rc, TLQR_K_CONDENSE, fx::kf_condense<T, NX, MX>, P->N, G, fx::CondSmem<T, NX, MX>::bytes,
                            st, w, P->N))) return e;
@@ -1059,7 +1077,11 @@ cudaError_t dispatch_res_nodes(int n, int m, const ResidualArgs& a, const FFArgs
 // kernels, 2 = the node-organised bulk-copy kernels, 0 = the library's choice
 // per n (kResNodeDefault).  The node kernels need compile-time (n, m) and
 // 16-byte aligned matrix arrays; otherwise the row kernels run.
-bool res_node_default(int n) { return n == 12 || n == 16; }
+// Measured on B300 (refinement residual per step, row kernels vs node kernels):
+// n = 12 (long trunk, 65,536 nodes) 0.25 vs 0.34 ms; n = 16 (1,024 trees,
+// 2.9 M nodes) 23.7 vs 14.2 ms; n = 32 (2^20 nodes) 23.1 vs 24.4 ms.
+bool res_node_default(int n) { return n == 16; }
+
 // polls of one mbarrier wait of the node residual before it gives up (each
 // poll may suspend the thread for a while, so this is ~a second or more)
 constexpr int kBarSpin = 1 << 20;
@@ -1083,6 +1105,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   a.Q = p.Q; a.q = p.q; a.M = f->opt.has_M ? p.M : nullptr; a.R = p.R; a.r = p.r; a.A = p.A;
   a.B = p.B; a.c = p.c; a.Delta = f->opt.has_delta ? p.Delta : nullptr;
   a.x = x; a.u = u; a.y = y;
+  a.dflag = a.Delta ? dflag : nullptr;
   a.res_x = f->res_x; a.res_u = f->res_u; a.res_c = f->res_c;
   a.maxes = f->maxes;
   a.T = P->n_trees;
@@ -1144,7 +1167,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   if ((e = cudaMemcpyAsync(f->h_maxes, f->maxes, 4 * (size_t)a.T * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, st)))
     return e;
-  return cudaMemcpyAsync(f->h_status, f->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  return cudaMemcpyAsync(f->h_status, f->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
 }
 
 // Run one launch sequence, through a cached CUDA graph when graphs are on.
@@ -1319,8 +1342,9 @@ int check_problem(const tlqr_factor_t* f, const tlqr_problem* p, bool rhs) {
 
 // Read the device status word (synchronises the stream).
 int read_status(tlqr_factor_t* f, cudaStream_t st) {
-  if (cudaMemcpyAsync(f->h_status, f->status, sizeof(int), cudaMemcpyDeviceToHost, st)) return TLQR_ERR_CUDA;
+  if (cudaMemcpyAsync(f->h_status, f->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) return TLQR_ERR_CUDA;
   if (cudaStreamSynchronize(st)) return TLQR_ERR_CUDA;
+  f->info.fp64_resolves = std::min(f->h_status[1], f->redo_cap);
   return map_status(*f->h_status);
 }
 
@@ -1595,7 +1619,8 @@ extern "C" int tlqr_factor_create(const tlqr_plan_t* plan, const tlqr_options* o
   const size_t N = plan->N, T = (size_t)plan->n_trees;
   if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_maxes, 4 * T * sizeof(unsigned long long));
   if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_gate, 2 * sizeof(double));
-  if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_status, sizeof(int));
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&f->h_status, 2 * sizeof(int));
+  if (err == cudaSuccess) f->h_status[0] = f->h_status[1] = 0;
   if (err == cudaSuccess && f->dflag) err = cudaMemset(f->dflag, 0, N);
   if (err != cudaSuccess) {
     delete f;
@@ -1896,6 +1921,7 @@ int refine(tlqr_factor_t* f, const tlqr_problem& dp, double* x, double* u, doubl
   f->info.refine_steps = steps;
   f->info.eta = eta;
   f->info.abs_residual = absr;
+  f->info.fp64_resolves = std::min(f->h_status[1], f->redo_cap);
   if (!std::isfinite(eta)) return TLQR_ERR_NONFINITE;
   if (eta > f->opt.refine_tol) return TLQR_ERR_NO_CONVERGENCE;
   return TLQR_OK;
@@ -1941,18 +1967,11 @@ extern "C" int tlqr_solve_adjoint(tlqr_factor_t* f, int32_t mem, const double* x
   return rc;
 }
 
-extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solution* sol, void* stream) {
-  if (!f || !sol || !sol->x || !sol->u || !sol->y) return TLQR_ERR_ARG;
-  if (sol->mem != TLQR_MEM_DEVICE && sol->mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
-  int rc = check_problem(f, prob, true);
-  if (rc) return rc;
-  StreamScope scope(f, stream);
-  cudaStream_t st = scope.st;
+namespace {
+// Factor, solve and (MIXED) refine the device problem dp, writing sol.
+int solve_device_problem(tlqr_factor_t* f, const tlqr_problem& dp, tlqr_solution* sol, cudaStream_t st) {
   const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
-  tlqr_problem dp = *prob;
-  if (prob->mem == TLQR_MEM_HOST) {
-    if ((rc = stage_problem(f, prob, &dp, true, true, st))) return rc;
-  }
+  int rc = 0;
   double *x = sol->x, *u = sol->u, *y = sol->y;
   if (sol->mem == TLQR_MEM_HOST) {
     if ((rc = ensure_stage(f))) return rc;
@@ -1981,6 +2000,85 @@ extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solut
     if (rc) { f->factored = false; return rc; }
   }
   return TLQR_OK;
+}
+
+// Q_i += diag(dq_i), R_i += diag(dr_i) in place (either increment may be null).
+__global__ void k_add_diagonals(int N, int n, int m, double* Q, const double* dq, double* R, const double* dr) {
+  const size_t total = (size_t)N * (n + m);
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    if (t < (size_t)N * n) {
+      if (!dq) continue;
+      const size_t i = t / n, r = t - i * n;
+      Q[i * n * n + r * (n + 1)] += dq[t];
+    } else {
+      if (!dr) continue;
+      const size_t tu = t - (size_t)N * n, i = tu / m, r = tu - i * m;
+      R[i * m * m + r * (m + 1)] += dr[tu];
+    }
+  }
+}
+}  // namespace
+
+extern "C" int tlqr_solve(tlqr_factor_t* f, const tlqr_problem* prob, tlqr_solution* sol, void* stream) {
+  if (!f || !sol || !sol->x || !sol->u || !sol->y) return TLQR_ERR_ARG;
+  if (sol->mem != TLQR_MEM_DEVICE && sol->mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
+  int rc = check_problem(f, prob, true);
+  if (rc) return rc;
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
+  tlqr_problem dp = *prob;
+  if (prob->mem == TLQR_MEM_HOST) {
+    if ((rc = stage_problem(f, prob, &dp, true, true, st))) return rc;
+  }
+  return solve_device_problem(f, dp, sol, st);
+}
+
+extern "C" int tlqr_update_solve(tlqr_factor_t* f, int32_t mem, const double* dq, const double* dr, const double* q,
+                                 const double* r, const double* c, tlqr_solution* sol, void* stream) {
+  if (!f || !sol || !sol->x || !sol->u || !sol->y) return TLQR_ERR_ARG;
+  if (mem != TLQR_MEM_DEVICE && mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
+  if (sol->mem != TLQR_MEM_DEVICE && sol->mem != TLQR_MEM_HOST) return TLQR_ERR_ARG;
+  if (!f->dprob.Q || !f->dprob.R || !f->dprob.q) return TLQR_ERR_STATE;   // nothing resident yet
+  StreamScope scope(f, stream);
+  cudaStream_t st = scope.st;
+  const size_t N = f->plan->N, n = f->opt.n, m = f->opt.m;
+  tlqr_problem dp = f->dprob;
+  const double *ddq = dq, *ddr = dr;
+  int rc = 0;
+  if (mem == TLQR_MEM_HOST) {
+    // the right-hand side goes to the staging area; the increments to a scratch
+    // of N (n + m) doubles (the staged P block, unused until P is exported)
+    if ((rc = ensure_stage(f))) return rc;
+    Stage s = stage_layout(f);
+    cudaError_t e = cudaSuccess;
+    if (q) { e = h2d(s.q, q, N * n, st); dp.q = s.q; }
+    if (!e && r) { e = h2d(s.r, r, N * m, st); dp.r = s.r; }
+    if (!e && c) { e = h2d(s.c, c, N * n, st); dp.c = s.c; }
+    double* inc = N * n * n >= N * (n + m) ? s.P : nullptr;
+    if (!inc && (dq || dr)) {
+      if (!f->upd) {
+        f->upd = dalloc<double>(N * (n + m), &e);
+        if (e) return TLQR_ERR_OOM;
+        f->allocs.push_back(f->upd);
+      }
+      inc = f->upd;
+    }
+    if (!e && dq) { e = h2d(inc, dq, N * n, st); ddq = inc; }
+    if (!e && dr) { e = h2d(inc + N * n, dr, N * m, st); ddr = inc + N * n; }
+    if (e) return TLQR_ERR_CUDA;
+  } else {
+    if (q) dp.q = q;
+    if (r) dp.r = r;
+    if (c) dp.c = c;
+  }
+  if (ddq || ddr) {
+    const size_t total = N * (n + m);
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)f->sms * 8));
+    k_add_diagonals<<<blocks, 256, 0, st>>>((int)N, (int)n, (int)m, const_cast<double*>(dp.Q), ddq,
+                                            const_cast<double*>(dp.R), ddr);
+    if (cudaGetLastError()) return TLQR_ERR_CUDA;
+  }
+  return solve_device_problem(f, dp, sol, st);
 }
 
 extern "C" int tlqr_kkt_residual(tlqr_factor_t* f, const tlqr_problem* prob, int32_t mem, const double* x,

@@ -18,6 +18,7 @@ _LIB_PATH = os.path.join(_HERE, "libtlqr.so")
 TLQR_OK = 0
 TLQR_ERR_ARG = 1
 TLQR_ERR_TIMEOUT = 7
+TLQR_ERR_NO_CONVERGENCE = 8
 TLQR_MEM_DEVICE, TLQR_MEM_HOST = 0, 1
 TLQR_PREC_FP64, TLQR_PREC_MIXED = 0, 1
 TLQR_OP_ROOT, TLQR_OP_RAKE, TLQR_OP_COMPRESS = 0, 1, 2
@@ -44,7 +45,8 @@ class tlqr_options(ctypes.Structure):
     _fields_ = [("n", _i32), ("m", _i32), ("precision", _i32), ("has_M", _i32), ("has_delta", _i32),
                 ("max_refine", _i32), ("refine_tol", ctypes.c_double), ("use_graphs", _i32),
                 ("generic_kernels", _i32), ("async_ops", _i32), ("spin_limit", _i32), ("test_withhold", _i32),
-                ("tail_ops", _i32), ("async_solve", _i32), ("residual", _i32)]
+                ("tail_ops", _i32), ("async_solve", _i32), ("residual", _i32),
+                ("fp64_resolve", _i32)]
 
 
 class tlqr_problem(ctypes.Structure):
@@ -82,7 +84,8 @@ class tlqr_kernel_profile(ctypes.Structure):
 
 
 class tlqr_info(ctypes.Structure):
-    _fields_ = [("refine_steps", _i32), ("eta", ctypes.c_double), ("abs_residual", ctypes.c_double)]
+    _fields_ = [("refine_steps", _i32), ("eta", ctypes.c_double), ("abs_residual", ctypes.c_double),
+                ("fp64_resolves", _i32)]
 
 
 _lib = None
@@ -96,7 +99,7 @@ EXPORTS = ["tlqr_plan_create", "tlqr_plan_create_forest", "tlqr_plan_destroy", "
            "tlqr_factor_workspace_bytes", "tlqr_factor_bytes", "tlqr_async_schedule", "tlqr_solve_adjoint",
            "tlqr_lift_node_controls_device", "tlqr_project_lifted_device", "tlqr_factor_dims", "tlqr_ipm_box",
            "tlqr_pipe_peak", "tlqr_solve_rhs_panel",
-           "tlqr_factor_options", "tlqr_autotune"]
+           "tlqr_factor_options", "tlqr_autotune", "tlqr_update_solve"]
 
 KERNEL_KINDS = ["condense", "rake", "absorb", "compress", "expand", "local_factor", "compose_T", "aff_init",
                 "aff_rake", "aff_absorb", "aff_compress", "aff_expand", "local_solve", "state_compress",
@@ -147,6 +150,7 @@ def lib():
         L.tlqr_ipm_box.argtypes = ([_vp, _vp, ctypes.POINTER(tlqr_problem), _dp, _dp, ctypes.POINTER(tlqr_ipm_options)]
                                    + [_dp] * 5 + [ctypes.POINTER(tlqr_ipm_info), _vp])
         L.tlqr_solve_adjoint.argtypes = [_vp, _i32] + [_dp] * 6 + [_vp]
+        L.tlqr_update_solve.argtypes = [_vp, _i32] + [_dp] * 5 + [ctypes.POINTER(tlqr_solution), _vp]
         L.tlqr_async_schedule.argtypes = [_vp, _i32, _i32, _i32] + [_ip] * 7
         L.tlqr_batched_expand.argtypes = [_i32, _i32] + [_dp] * 5 + [_i32, _vp]
         L.tlqr_batched_local_factor.argtypes = [_i32, _i32, _i32] + [_dp] * 8 + [_i32, _vp]
@@ -261,9 +265,10 @@ def tlqr_plan_schedule(plan, N: int):
 
 def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
                  refine_tol=1e-8, use_graphs=True, generic_kernels=False, async_ops=0, spin_limit=0,
-                 test_withhold=False, tail_ops=0, async_solve=0, residual=0) -> tlqr_options:
+                 test_withhold=False, tail_ops=0, async_solve=0, residual=0, fp64_resolve=0) -> tlqr_options:
     o = tlqr_options()
     o.tail_ops, o.async_solve, o.residual = int(tail_ops), int(async_solve), int(residual)
+    o.fp64_resolve = int(fp64_resolve)
     o.generic_kernels = int(bool(generic_kernels))
     o.async_ops, o.spin_limit, o.test_withhold = int(async_ops), int(spin_limit), int(test_withhold)
     o.n, o.m, o.precision = int(n), int(m), int(precision)
@@ -319,6 +324,16 @@ def tlqr_solve(f, data: dict, x, u, y, P=None, K=None, stream=None) -> None:
     p = make_problem(data)
     s = make_solution(x, u, y, P, K)
     _check(lib().tlqr_solve(f, ctypes.byref(p), ctypes.byref(s), _stream(stream)), "tlqr_solve")
+
+
+def tlqr_update_solve(f, x, u, y, dq=None, dr=None, q=None, r=None, c=None, P=None, K=None, stream=None) -> None:
+    """Add diag(dq_i) to Q_i and diag(dr_i) to R_i of the resident problem, replace
+    q, r, c (None: unchanged), then factor and solve it into x, u, y."""
+    inputs = [a for a in (dq, dr, q, r, c) if a is not None]
+    mem = _mem_all(inputs) if inputs else TLQR_MEM_DEVICE
+    s = make_solution(x, u, y, P, K)
+    _check(lib().tlqr_update_solve(f, mem, *[_ptr(a) for a in (dq, dr, q, r, c)], ctypes.byref(s), _stream(stream)),
+           "tlqr_update_solve")
 
 
 def tlqr_solve_rhs(f, q, r, c, x, u, y, stream=None) -> None:
@@ -408,7 +423,7 @@ def tlqr_kkt_residual_noalloc(plan, n: int, m: int, data: dict, x, u, y, stream=
 def tlqr_last_info(f) -> dict:
     i = tlqr_info()
     _check(lib().tlqr_last_info(f, ctypes.byref(i)), "tlqr_last_info")
-    return dict(refine_steps=i.refine_steps, eta=i.eta, abs_residual=i.abs_residual)
+    return dict(refine_steps=i.refine_steps, eta=i.eta, abs_residual=i.abs_residual, fp64_resolves=i.fp64_resolves)
 
 
 def tlqr_tree_residuals(f, n_trees: int):
