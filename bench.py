@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--e2e", action="store_true", help="run the end-to-end leg for the 10^6-node workloads too")
     ap.add_argument("--no-spine", action="store_true",
                     help="skip the per-round roofline of the N=2^20 spine tree in the default line")
+    ap.add_argument("--pdl", type=int, default=None, choices=[0, -1],
+                    help="programmatic dependent launch of the pass kernels (0 on, -1 off); default: on")
     ap.add_argument("--residual", type=int, default=None, choices=[0, 1, 2],
                     help="refinement residual kernels (1 rows, 2 node-organised); default: the tuned table's")
     ap.add_argument("--quick", action="store_true",
@@ -722,6 +724,8 @@ def run_ours(args, rank, world, dist):
     tuned = autotune.tuned_options(args.workload) if mixed and args.total is None else {}
     if args.residual is not None:
         tuned["residual"] = args.residual
+    if args.pdl is not None:
+        tuned["pdl"] = args.pdl
     solver = tlqr.TreeLQR(w.parent, n, m, prec, has_delta=has_delta, forest=forest, **tuned)
     stats = solver.stats()
 

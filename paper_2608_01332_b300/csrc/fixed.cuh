@@ -15,9 +15,9 @@
 // the rows where they are (implicit pivoting): the pivot is found with one
 // unsigned-max reduction over the group and its row is broadcast through
 // shared memory.  Loops over n are fully unrolled, so
-// all register indexing is static.  At n = 32 in FP32 (one warp per operation)
-// the block products run on the tensor cores instead (mma32.cuh); the
-// eliminations stay on the FP32 pipe.
+// all register indexing is static.  At n = 16 and n = 32 in FP32 the block
+// products run on the tensor cores instead (mma32.cuh); the eliminations stay
+// on the FP32 pipe.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -45,11 +45,12 @@ struct D {
   static constexpr int MAT = N * LD;                   // elements of one staged matrix
 };
 
-// n = 32 in FP32: one warp per operation, and the n x n block products run on
-// the tensor cores (3xTF32 mma.sync, mma32.cuh); the Gauss-Jordan
-// solves stay on the FP32 pipe.
+// n = 16 (two operations per warp, one 16 x 16 product per half warp) and
+// n = 32 (one operation per warp) in FP32: the n x n block products run on the
+// tensor cores (3xTF32 mma.sync, mma32.cuh); the Gauss-Jordan solves stay on
+// the FP32 pipe.
 template <typename T, int N>
-constexpr bool kTensorCores = std::is_same<T, float>::value && N == 32;
+constexpr bool kTensorCores = std::is_same<T, float>::value && (N == 32 || N == 16);
 
 template <typename T> __device__ __forceinline__ T vget(const typename Vec<T>::V& v, int i);
 template <> __device__ __forceinline__ float vget<float>(const float4& v, int i) {
@@ -494,7 +495,7 @@ struct TauSmem {
   static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
-// Tensor-core version (n = 32, FP32): U and C staged, C U on the tensor
+// Tensor-core version (n = 16, 32, FP32): U and C staged, C U on the tensor
 // cores, A read from global memory twice -- rows for the elimination's
 // right-hand side and as the transposed left operand of the last product -- so
 // that a warp holds two staged matrices instead of three.
@@ -509,7 +510,7 @@ __device__ __forceinline__ bool tau_group_tc(const Ws<T>& w, const Grp& g, const
   __syncwarp();
   const int r = g.gl < N ? g.gl : 0;
   T x[N], b[N];
-  tc::gemm32<false, false>(sY, LD, sU, LD, nullptr, 0, sY, LD, true);   // C U over C
+  tc::gemm<N, false, false>(sY, LD, sU, LD, nullptr, 0, sY, LD, true);   // C U over C
   row_load<T, N>(x, sY + r * LD);
 #pragma unroll
   for (int c = 0; c < N; ++c) x[c] += (c == r) ? T(1) : T(0);
@@ -527,8 +528,8 @@ __device__ __forceinline__ bool tau_group_tc(const Ws<T>& w, const Grp& g, const
   }
   if (!stored && g.gl < N) row_store<T, N>(sY + kpos * LD, b);
   __syncwarp();
-  tc::gemm32<false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, true);   // Z = U Y over U
-  tc::gemm32<true, false>(Ag, N, sU, LD, Pg, N, out, N, g.valid);      // P + A^T Z
+  tc::gemm<N, false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, true);   // Z = U Y over U
+  tc::gemm<N, true, false>(Ag, N, sU, LD, Pg, N, out, N, g.valid);      // P + A^T Z
   return ok;
 }
 
@@ -588,12 +589,14 @@ __device__ __forceinline__ bool tau_group(const Ws<T>& w, const Grp& g, const T*
 
 // 128-thread blocks; resident blocks per SM the register budget must allow:
 // five for the n = 32 tensor-core version (two staged matrices per warp, so
-// shared memory allows five) and for FP64, eight for the FP32 group kernels
+// shared memory allows five) and for FP64, eight for the other FP32 group
+// kernels (n = 16 included)
 template <typename T, int N>
 constexpr int kRakeBlocks = (sizeof(T) == 8 || N >= 32) ? 5 : 8;
 
 template <typename T, int N>
 __global__ void __launch_bounds__(128, kRakeBlocks<T, N>) kf_rake(Ws<T> w, int begin, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int op;
   const Grp g = group_of<T, N>(count, &op);
@@ -606,6 +609,7 @@ __global__ void __launch_bounds__(128, kRakeBlocks<T, N>) kf_rake(Ws<T> w, int b
 
 template <typename T, int N>
 __global__ void __launch_bounds__(128, kRakeBlocks<T, N>) kf_expand(Ws<T> w, int begin, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int op;
   const Grp g = group_of<T, N>(count, &op);
@@ -632,7 +636,7 @@ struct CompSmem {
   static constexpr int bytes = ((elems * (int)sizeof(T) + 15) / 16) * 16;
 };
 
-// Tensor-core compression (n = 32, FP32): P~ and C_l staged, the block products
+// Tensor-core compression (n = 16, 32, FP32): P~ and C_l staged, the block products
 // on the tensor cores, A_l and A_r read from global memory (so a warp holds two
 // staged matrices and the [Y1 | Y2] panel instead of four and the panel).  The
 // order keeps every read ahead of the write that replaces it: A_l (slot j) is
@@ -655,8 +659,8 @@ __device__ __forceinline__ bool compress_op_tc(const Ws<T>& w, int rr, const Grp
   }
   gload<T, N, N, LD, G>(sCl, w.Ec + oj, gl);
   __syncwarp();
-  tc::gemm32<false, false>(sCl, LD, sPt, LD, nullptr, 0, sY, LD2, true);   // C_l P~ -> Y1 columns
-  tc::gemm32<false, true>(sCl, LD, Ar, N, nullptr, 0, sY + YW, LD2, true);  // C_l A_r^T -> Y2 columns
+  tc::gemm<N, false, false>(sCl, LD, sPt, LD, nullptr, 0, sY, LD2, true);   // C_l P~ -> Y1 columns
+  tc::gemm<N, false, true>(sCl, LD, Ar, N, nullptr, 0, sY + YW, LD2, true);  // C_l A_r^T -> Y2 columns
   T s[N], b[2 * YW], t1[N], t2[N];
   row_load<T, N>(s, sY + r * LD2);
 #pragma unroll
@@ -678,8 +682,8 @@ __device__ __forceinline__ bool compress_op_tc(const Ws<T>& w, int rr, const Grp
   }
   if (!stored && gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
-  tc::gemm32<false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, true);             // W = P~ Y1 over C_l
-  tc::gemm32<true, false>(Al, N, sCl, LD, w.Ep + oj, N, w.Ep + ok_, N, g.valid);   // P_new = P_l + A_l^T W
+  tc::gemm<N, false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, true);             // W = P~ Y1 over C_l
+  tc::gemm<N, true, false>(Al, N, sCl, LD, w.Ep + oj, N, w.Ep + ok_, N, g.valid);   // P_new = P_l + A_l^T W
   if (g.valid && gl < N) {
     // tape into slot j: (A_r, C_r, P~), read before slot k is rewritten
     T v[N];
@@ -691,8 +695,8 @@ __device__ __forceinline__ bool compress_op_tc(const Ws<T>& w, int rr, const Grp
     grow_store<T, N>(w.Ep + oj + r * N, v);
   }
   __syncwarp();
-  tc::gemm32<false, false>(Ar, N, sY + YW, LD2, w.Ec + ok_, N, w.Ec + ok_, N, g.valid);   // C_new = C_r + A_r Y2
-  tc::gemm32<false, false>(Ar, N, sY, LD2, nullptr, 0, w.Ea + ok_, N, g.valid);          // A_new = A_r Y1
+  tc::gemm<N, false, false>(Ar, N, sY + YW, LD2, w.Ec + ok_, N, w.Ec + ok_, N, g.valid);   // C_new = C_r + A_r Y2
+  tc::gemm<N, false, false>(Ar, N, sY, LD2, nullptr, 0, w.Ea + ok_, N, g.valid);          // A_new = A_r Y1
   return okf;
 }
 
@@ -793,6 +797,7 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
 
 template <typename T, int N>
 __global__ void kf_compress(Ws<T> w, int begin, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int op;
   const Grp g = group_of<T, N>(count, &op);
@@ -907,6 +912,7 @@ struct AsyncSmem {
 
 template <typename T, int N>
 __global__ void kf_async(Ws<T> w, AsyncArgs a) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using Dm = D<T, N>;
   constexpr int G = Dm::G, OPS = Dm::OPS, NN = N * N;
@@ -975,7 +981,7 @@ __device__ __forceinline__ void compose_op(const Ws<T>& w, int rr, const Grp& g,
     __syncwarp();
     if (g.valid && gl < N) grow_store<T, N>(w.Tr + (size_t)j * NN + r * N, tk);
     __syncwarp();
-    tc::gemm32<false, false>(w.Tm + (size_t)k * NN, N, sTj, LD, nullptr, 0, w.Tm + (size_t)k * NN, N, g.valid);
+    tc::gemm<N, false, false>(w.Tm + (size_t)k * NN, N, sTj, LD, nullptr, 0, w.Tm + (size_t)k * NN, N, g.valid);
     return;
   }
   __syncwarp();
@@ -990,6 +996,7 @@ __device__ __forceinline__ void compose_op(const Ws<T>& w, int rr, const Grp& g,
 
 template <typename T, int N>
 __global__ void kf_compose_T(Ws<T> w, int begin, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int op;
   const Grp g = group_of<T, N>(count, &op);
@@ -1120,36 +1127,42 @@ __device__ __forceinline__ void state_expand_op(const Ws<T>& w, const int* nodes
 
 template <typename T, int N>
 __global__ void kf_aff_rake(Ws<T> w, int begin, int count) {
+  pdl_entry();
   int op;
   const Grp g = group_of<T, N>(count, &op);
   aff_rake_op<T, N>(w, begin + op, g.valid, g.gl);
 }
 template <typename T, int N>
 __global__ void kf_aff_absorb(Ws<T> w, int begin, int count) {
+  pdl_entry();
   int op;
   const Grp g = group_of<T, N>(count, &op);
   aff_absorb_op<T, N>(w, begin + op, g.valid, g.gl);
 }
 template <typename T, int N>
 __global__ void kf_aff_compress(Ws<T> w, int begin, int count) {
+  pdl_entry();
   int op;
   const Grp g = group_of<T, N>(count, &op);
   aff_compress_op<T, N>(w, begin + op, g.valid, g.gl);
 }
 template <typename T, int N>
 __global__ void kf_aff_expand(Ws<T> w, int begin, int count) {
+  pdl_entry();
   int op;
   const Grp g = group_of<T, N>(count, &op);
   aff_expand_op<T, N>(w, begin + op, g.valid, g.gl);
 }
 template <typename T, int N>
 __global__ void kf_state_compress(Ws<T> w, int begin, int count) {
+  pdl_entry();
   int op;
   const Grp g = group_of<T, N>(count, &op);
   state_compress_op<T, N>(w, begin + op, g.valid, g.gl);
 }
 template <typename T, int N>
 __global__ void kf_state_expand(Ws<T> w, const int* nodes, const int* from, int begin, int count) {
+  pdl_entry();
   int op;
   const Grp g = group_of<T, N>(count, &op);
   state_expand_op<T, N>(w, nodes, from, begin + op, g.valid, g.gl);
@@ -1162,6 +1175,7 @@ __global__ void kf_state_expand(Ws<T> w, const int* nodes, const int* from, int 
 // kernels; no shared memory.
 template <typename T, int N>
 __global__ void kf_async_vec(Ws<T> w, AsyncArgs a) {
+  pdl_entry();
   constexpr int G = D<T, N>::G, OPS = D<T, N>::OPS;
   const int lane = threadIdx.x & 31;
   const int gl = lane & (G - 1), gsub = lane / G;
@@ -1219,6 +1233,7 @@ constexpr int kTailBlock = 1024;
 // backward rounds R-1..r0 (expand).
 template <typename T, int N>
 __global__ void __launch_bounds__(kTailBlock) kf_aff_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
+  pdl_entry();
   constexpr int G = D<T, N>::G;
   const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
   for (int r = r0; r < R; ++r) {
@@ -1241,6 +1256,7 @@ __global__ void __launch_bounds__(kTailBlock) kf_aff_tail(Ws<T> w, const RoundDe
 // (compressed centres before the leaves raked in the same round).
 template <typename T, int N>
 __global__ void __launch_bounds__(kTailBlock) kf_state_tail(Ws<T> w, const RoundDesc* rounds, int r0, int R) {
+  pdl_entry();
   constexpr int G = D<T, N>::G;
   const int gl = threadIdx.x & (G - 1), gid = threadIdx.x / G, gpb = blockDim.x / G;
   for (int r = r0; r < R; ++r) {
@@ -1401,6 +1417,7 @@ struct CondSmem {
 // (ignored) edge slot and stores nothing but U and the flag.
 template <typename T, int N, int M>
 __global__ void kf_condense(Ws<T> w, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int G = D<T, N>::G, NN = N * N, NM = N * M, MLD = CondSmem<T, N, M>::MLD;
   int i;
@@ -1493,6 +1510,7 @@ struct LfSmem {
 // factors F = I and ignores the result), so the warp stays converged.
 template <typename T, int N, int M>
 __global__ void kf_local_factor(Ws<T> w, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using Dm = D<T, N>;
   using L = LfSmem<T, N, M>;
@@ -1677,6 +1695,7 @@ struct AiSmem {
 // Affine edge data eq. (affine-edge): h = q, z = K^T (r + B^T w) + A^T w, w = W c.
 template <typename T, int N, int M>
 __global__ void kf_aff_init(Ws<T> w, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using A_ = AiSmem<T, N, M>;
   constexpr int G = D<T, N>::G, LD = A_::LD, MLD = A_::MLD, NN = N * N, NM = N * M;
@@ -1732,6 +1751,7 @@ struct LsSmem {
 // Local affine solve eq. (local-affine-solve) and the root state eq. (xroot).
 template <typename T, int N, int M>
 __global__ void kf_local_solve(Ws<T> w, int count) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using L = LsSmem<T, N, M>;
   constexpr int G = D<T, N>::G, LD = L::LD, MLD = L::MLD, NN = N * N, NM = N * M;
@@ -1841,6 +1861,7 @@ __global__ void kf_local_solve(Ws<T> w, int count) {
 // Recovery eq. (recover) into FP64 x, u, y (written or accumulated).
 template <typename T, int N, int M>
 __global__ void kf_recover(Ws<T> w, double* x, double* u, double* y, int accumulate, int count) {
+  pdl_entry();
   constexpr int NN = N * N, NM = N * M;
   int j;
   const Grp g = group_of<T, N>(count, &j);

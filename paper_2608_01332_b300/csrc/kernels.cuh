@@ -76,6 +76,17 @@ struct Ws {
 template <typename T>
 __device__ __forceinline__ bool node_is_root(const Ws<T>& w, int j) { return w.parent ? (w.parent[j] < 0) : false; }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may be scheduled while its predecessor in the stream is still
+// draining.  Every kernel of the factorisation and solve passes starts here:
+// it waits until the predecessor grid has completed and its writes are
+// visible, then allows its own successor to begin launching.  Without a
+// programmatic predecessor both instructions return at once.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) {
   if (lane_id() == 0) atomicCAS(status, 0, code);
 }
@@ -116,6 +127,7 @@ __device__ bool tau_warp(int n, const S* Ug, const S* Ag, const S* Cg, const S* 
 // per-node "Delta nonzero" flag.  sm: 2 n^2 + m^2 + 2 n m T.
 template <typename T>
 __global__ void k_condense(Ws<T> w, int warp_bytes) {
+  pdl_entry();
   const int i = warp_op();
   if (i >= w.N) return;
   const int n = w.n, m = w.m, nn = n * n;
@@ -169,6 +181,7 @@ __global__ void k_condense(Ws<T> w, int warp_bytes) {
 // ---------------------------------------------------------------- rake
 template <typename T>
 __global__ void k_rake(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.rake_leaf[r], nn = w.n * w.n;
@@ -182,6 +195,7 @@ __global__ void k_rake(Ws<T> w, int begin, int count, int warp_bytes) {
 // in increasing leaf index (Sec. X-B, oplus = addition).
 template <typename T>
 __global__ void k_absorb(Ws<T> w, int seg_begin, int count) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int s = seg_begin + t, i = w.seg_parent[s], nn = w.n * w.n;
@@ -199,6 +213,7 @@ __global__ void k_absorb(Ws<T> w, int seg_begin, int count) {
 // sm: 7 n^2 T + n ints.
 template <typename T>
 __global__ void k_compress(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.comp_j[r], k = w.comp_k[r];
@@ -247,6 +262,7 @@ __global__ void k_compress(Ws<T> w, int begin, int count, int warp_bytes) {
 // P_j = tau(s_j, P_k), written over U_j.
 template <typename T>
 __global__ void k_expand(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.comp_j[r], k = w.comp_k[r], nn = w.n * w.n;
@@ -261,6 +277,7 @@ __global__ void k_expand(Ws<T> w, int begin, int count, int warp_bytes) {
 // B^T W B (m^2 T) and m^2 doubles for the FP64 fallback of the G Cholesky.
 template <typename T>
 __global__ void k_local_factor(Ws<T> w, int warp_bytes) {
+  pdl_entry();
   const int j = warp_op();
   if (j >= w.N) return;
   const int n = w.n, m = w.m, nn = n * n;
@@ -340,6 +357,7 @@ __global__ void k_local_factor(Ws<T> w, int warp_bytes) {
 // compression, in forward round order: Tr_j <- T_k ; T_k <- T_k T_j.
 template <typename T>
 __global__ void k_compose_T(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.comp_j[r], k = w.comp_k[r], n = w.n, nn = n * n;
@@ -358,6 +376,7 @@ __global__ void k_compose_T(Ws<T> w, int begin, int count, int warp_bytes) {
 // sm: 2 n^2 + n m + m n + 4 (n + m) T.
 template <typename T>
 __global__ void k_aff_init(Ws<T> w, int warp_bytes) {
+  pdl_entry();
   const int j = warp_op();
   if (j >= w.N) return;
   const int n = w.n, m = w.m, nn = n * n;
@@ -384,6 +403,7 @@ __global__ void k_aff_init(Ws<T> w, int warp_bytes) {
 // Affine rake eq. (affine-rake): contribution Z h_j + z, Z = T_j^T (current composite).
 template <typename T>
 __global__ void k_aff_rake(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.rake_leaf[r], n = w.n, nn = n * n;
@@ -397,6 +417,7 @@ __global__ void k_aff_rake(Ws<T> w, int begin, int count, int warp_bytes) {
 
 template <typename T>
 __global__ void k_aff_absorb(Ws<T> w, int seg_begin, int count) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int s = seg_begin + t, i = w.seg_parent[s], n = w.n;
@@ -411,6 +432,7 @@ __global__ void k_aff_absorb(Ws<T> w, int seg_begin, int count) {
 // Affine compress eq. (affine-compose): s_j = h_j + z_r ; z_k <- z_l + Z_l s_j.
 template <typename T>
 __global__ void k_aff_compress(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.comp_j[r], k = w.comp_k[r], n = w.n, nn = n * n;
@@ -426,6 +448,7 @@ __global__ void k_aff_compress(Ws<T> w, int begin, int count, int warp_bytes) {
 // Affine expansion: p_j = Z_r p_k + s_j with Z_r = Tr_j^T (over h_j).
 template <typename T>
 __global__ void k_aff_expand(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.comp_j[r], k = w.comp_k[r], n = w.n, nn = n * n;
@@ -441,6 +464,7 @@ __global__ void k_aff_expand(Ws<T> w, int begin, int count, int warp_bytes) {
 //   f = Delta p - c, g = p - W f, k = -G^{-1}(r + B^T g), b = F^{-1}(B k - f).
 template <typename T>
 __global__ void k_local_solve(Ws<T> w, int warp_bytes) {
+  pdl_entry();
   const int j = warp_op();
   if (j >= w.N) return;
   const int n = w.n, m = w.m, nn = n * n;
@@ -497,6 +521,7 @@ __global__ void k_local_solve(Ws<T> w, int warp_bytes) {
 // were composed once in the factorisation): b_k <- T_r b_l + b_r, T_r = Tr_j.
 template <typename T>
 __global__ void k_state_compress(Ws<T> w, int begin, int count, int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = w.comp_j[r], k = w.comp_k[r], n = w.n, nn = n * n;
@@ -513,6 +538,7 @@ __global__ void k_state_compress(Ws<T> w, int begin, int count, int warp_bytes) 
 template <typename T>
 __global__ void k_state_expand(Ws<T> w, const int* nodes, const int* from, int begin, int count,
                                int warp_bytes) {
+  pdl_entry();
   const int t = warp_op();
   if (t >= count) return;
   const int r = begin + t, j = nodes[r], i = from[r], n = w.n, nn = n * n;
@@ -528,6 +554,7 @@ __global__ void k_state_expand(Ws<T> w, const int* nodes, const int* from, int b
 // FP64, written or (accumulate = 1) added to x, u, y.
 template <typename T>
 __global__ void k_recover(Ws<T> w, double* x, double* u, double* y, int accumulate, int warp_bytes) {
+  pdl_entry();
   const int j = warp_op();
   if (j >= w.N) return;
   const int n = w.n, m = w.m, nn = n * n;
@@ -566,6 +593,7 @@ __global__ void k_recover(Ws<T> w, double* x, double* u, double* y, int accumula
 // Widen P (= U after the reverse pass) and K to FP64 outputs.
 template <typename T>
 __global__ void k_export_PK(int N, int n, int m, const int* parent, const T* U, const T* K, double* P, double* Ko) {
+  pdl_entry();
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

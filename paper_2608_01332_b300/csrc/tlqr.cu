@@ -94,6 +94,7 @@ struct EvPair { int kind; cudaEvent_t a, b; int64_t units = 0; };
 struct Recorder {
   uint32_t mask = 0;
   bool capture = false;
+  bool pdl = false;                    // launch with programmatic dependent launch (see pdl_entry)
   int64_t launches[TLQR_K_COUNT] = {}, units[TLQR_K_COUNT] = {};
   std::vector<EvPair> recs;
   std::vector<cudaEvent_t>* pool = nullptr;
@@ -149,6 +150,30 @@ struct Profiler {
   }
 };
 
+// kernel<<<grid, block, smem, st>>>(args...), with programmatic stream
+// serialisation when pdl is set: the kernel may be scheduled while its
+// predecessor drains and waits for it on the device (pdl_entry), which hides
+// the launch gap between the short kernels of a pass.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args) {
+  if (!pdl) {
+    kernel<<<grid, block, smem, st>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Launch `count` warps, each with `wbytes` of dynamic shared memory.
 template <typename Kernel, typename... Args>
 cudaError_t launch_warps(Recorder* rc, int kind, Kernel kernel, int count, size_t wbytes, cudaStream_t st,
@@ -164,8 +189,7 @@ cudaError_t launch_warps(Recorder* rc, int kind, Kernel kernel, int count, size_
   const bool timed = rc && (rc->mask >> kind) & 1u;
   EvPair ev{kind, nullptr, nullptr, count};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  kernel<<<blocks, 32 * wpb, smem, st>>>(args...);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(rc && rc->pdl && !timed, kernel, blocks, 32 * wpb, smem, st, args...);
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[kind]++; rc->units[kind] += count; }
   return e;
@@ -702,8 +726,7 @@ cudaError_t launch_groups(Recorder* rc, int kind, Kernel kernel, int count, int 
   const bool timed = rc && (rc->mask >> kind) & 1u;
   EvPair ev{kind, nullptr, nullptr, count};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  kernel<<<blocks, threads, smem, st>>>(args...);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(rc && rc->pdl && !timed, kernel, blocks, threads, smem, st, args...);
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[kind]++; rc->units[kind] += count; }
   return e;
@@ -715,8 +738,7 @@ cudaError_t launch_tail(Recorder* rc, int kind, Kernel kernel, cudaStream_t st, 
   const bool timed = rc && (rc->mask >> kind) & 1u;
   EvPair ev{kind, nullptr, nullptr, 1};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  kernel<<<1, kTailThreads, 0, st>>>(args...);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(rc && rc->pdl && !timed, kernel, 1, kTailThreads, 0, st, args...);
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[kind]++; rc->units[kind] += 1; }
   return e;
@@ -751,8 +773,7 @@ cudaError_t launch_async(tlqr_factor_t* f, Recorder* rc, int kind, Kernel kernel
   const bool timed = rc && (rc->mask >> kind) & 1u;
   EvPair ev{kind, nullptr, nullptr, A.n_ops};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  kernel<<<blocks, 128, smem, st>>>(w, a);
-  e = cudaGetLastError();
+  e = launch_k(rc && rc->pdl && !timed, kernel, blocks, 128, smem, st, w, a);
   if (timed) { rc->record(ev.b, st); rc->recs.push_back(ev); }
   if (rc) { rc->launches[kind]++; rc->units[kind] += A.n_ops; }
   return e;
@@ -1176,6 +1197,7 @@ cudaError_t run_seq(tlqr_factor_t* f, GraphCache* g, std::vector<uintptr_t> key,
   key.push_back(f->prof.mask);
   if (!f->opt.use_graphs || f->graphs_broken || !g) {
     Recorder r;
+    r.pdl = f->opt.pdl >= 0;
     r.mask = f->prof.mask;
     r.pool = &f->prof.pool;
     cudaError_t e = body(&r);
@@ -1185,6 +1207,7 @@ cudaError_t run_seq(tlqr_factor_t* f, GraphCache* g, std::vector<uintptr_t> key,
   if (!g->exec || g->key != key) {
     g->clear();
     Recorder r;
+    r.pdl = f->opt.pdl >= 0;
     r.mask = f->prof.mask;
     r.capture = true;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);

@@ -46,7 +46,7 @@ class tlqr_options(ctypes.Structure):
                 ("max_refine", _i32), ("refine_tol", ctypes.c_double), ("use_graphs", _i32),
                 ("generic_kernels", _i32), ("async_ops", _i32), ("spin_limit", _i32), ("test_withhold", _i32),
                 ("tail_ops", _i32), ("async_solve", _i32), ("residual", _i32),
-                ("fp64_resolve", _i32)]
+                ("fp64_resolve", _i32), ("pdl", _i32)]
 
 
 class tlqr_problem(ctypes.Structure):
@@ -265,10 +265,11 @@ def tlqr_plan_schedule(plan, N: int):
 
 def make_options(n, m, precision=TLQR_PREC_FP64, has_M=False, has_delta=False, max_refine=10,
                  refine_tol=1e-8, use_graphs=True, generic_kernels=False, async_ops=0, spin_limit=0,
-                 test_withhold=False, tail_ops=0, async_solve=0, residual=0, fp64_resolve=0) -> tlqr_options:
+                 test_withhold=False, tail_ops=0, async_solve=0, residual=0, fp64_resolve=0,
+                 pdl=0) -> tlqr_options:
     o = tlqr_options()
     o.tail_ops, o.async_solve, o.residual = int(tail_ops), int(async_solve), int(residual)
-    o.fp64_resolve = int(fp64_resolve)
+    o.fp64_resolve, o.pdl = int(fp64_resolve), int(pdl)
     o.generic_kernels = int(bool(generic_kernels))
     o.async_ops, o.spin_limit, o.test_withhold = int(async_ops), int(spin_limit), int(test_withhold)
     o.n, o.m, o.precision = int(n), int(m), int(precision)

@@ -1,12 +1,15 @@
 """FP64 re-solves of ill-conditioned eliminations in mixed precision.
 
-With Delta = 0 and a control weight R whose spectrum spans 1e-8 .. 1
-(kappa(R) = 1e8, cheap controls), C = B R^{-1} B^T reaches ~1e8 and the
-systems S = I + C U and S = I + C P~ of the rake, compression and
-reconstruction have pivots spanning far more than 1e4: the FP32 kernels
-re-solve those in FP64 (eq. (terminal-fold), eq. (compress-intermediates)).
-The refined solution must match the FP64 oracle and reach eta <= 1e-8; the
-factorisation must report the re-solves it took, and none when they are off.
+With Delta = 0, a control weight R of condition number 1e8 (spectrum
+1 .. 1e8) and a state weight Q scaled by 1e6, the node data U and value
+Hessians P reach ~1e7 while C = B R^{-1} B^T stays O(1), so the systems
+S = I + C U and S = I + C P~ of the rake, compression and reconstruction
+have pivots spanning ~1e6-1e7, far more than 1e4: the FP32 kernels re-solve
+those in FP64 (eq. (terminal-fold), eq. (compress-intermediates)).  (A tiny
+R instead would make C ~ 1e8 but also ruin the FP32 condensation itself,
+which no re-solve of S can repair.)  The refined solution must match the
+FP64 oracle and reach eta <= 1e-8; the factorisation must report the
+re-solves it took, and none when they are off.
 """
 import numpy as np
 import pytest
@@ -24,7 +27,7 @@ def _ill_case(n, m, N, seed):
     rng = inputs.rng_for(seed)
     p, _ = inputs.permute_labels(inputs.random_recursive(N, rng), rng)
     d = inputs.problem_data(p, n, m, rng, kappa_R=1e8)
-    d["R"] = d["R"] * 1e-8                      # spectrum 1e-8 .. 1
+    d["Q"] = d["Q"] * 1e6
     return p, d
 
 
