@@ -424,20 +424,25 @@ __device__ __forceinline__ bool gj64_rows(double* a, int lda, double* b, int ldb
   return ok;
 }
 
-// Forms rows gl < N of the system in the slot, eliminates it, and writes the
-// solution, rounded to FP32, into the shared rows `dst` (row stride ldd) where
-// the FP32 elimination would have put it:
-//   kind 0 (rake, reconstruction): S = I + L R,    B = B1            (N x N)
-//   kind 1 (compression):          S = I + L R,    B = [B1 | L B2^T] (N x 2N;
-//                                  the second block goes to column col2)
-//   kind 2 (local factor):         S = I + L64 R,  B = I             (N x N)
+// Forms rows gl < N of the system in the slot, eliminates it, writes the
+// solution X, rounded to FP32, into the shared rows `dst` (row stride ldd)
+// where the FP32 elimination would have put it, and forms in FP64 the product
+// with the right factor that follows every one of these solves -- R X -- whose
+// large-times-small terms (R large along the directions where X is small) FP32
+// cannot resolve, writing it rounded into `wdst` (row stride ldwd):
+//   kind 0 (rake, reconstruction): S = I + L R, B = B1, X = S^{-1} A, R X = U Y
+//   kind 1 (compression):          S = I + L R, B = [B1 | L B2^T] (the second
+//                                  block of X goes to column col2), R X1 = P~ Y1
+//   kind 2 (local factor):         S = I + L64 R, B = I, X = F^{-1}, R X = P F^{-1}
 // L, R, B1, B2: FP32 rows (shared or global memory, leading dimensions);
-// L64: FP64 rows (problem data).  Slot layout: S (N x N), then B (N x nb).
+// L64: FP64 rows (problem data).  Slot layout: S (N x N), then B (N x nb);
+// wdst may alias R (the product is staged in the slot first).
 enum : int { RS_TAU = 0, RS_COMPRESS = 1, RS_LOCAL = 2 };
 template <int N, int G>
 __device__ __noinline__ bool resolve64(double* sc, int kind, const float* L, int ldl, const double* L64,
                                        const float* R, int ldr, const float* B1, int ldb1, const float* B2,
-                                       int ldb2, float* dst, int ldd, int col2, int gl) {
+                                       int ldb2, float* dst, int ldd, int col2, float* wdst, int ldwd, int gl) {
+  const unsigned mask = group_mask<G>();
   const int nb = kind == RS_COMPRESS ? 2 * N : N;
   double *a = sc, *b = sc + N * N;
   if (gl < N) {
@@ -463,17 +468,38 @@ __device__ __noinline__ bool resolve64(double* sc, int kind, const float* L, int
       }
     }
   }
-  __syncwarp(group_mask<G>());
+  __syncwarp(mask);
   int kp;
   const bool ok = gj64_rows<G>(a, N, b, nb, N, nb, gl, kp);
+  // rows of X by index (first N columns) into the slot's S block, rounded X into dst
   if (gl < N) {
 #pragma unroll 1
-    for (int c = 0; c < N; ++c) dst[kp * ldd + c] = (float)b[gl * nb + c];
+    for (int c = 0; c < N; ++c) {
+      a[kp * N + c] = b[gl * nb + c];
+      dst[kp * ldd + c] = (float)b[gl * nb + c];
+    }
     if (kind == RS_COMPRESS) {
 #pragma unroll 1
       for (int c = 0; c < N; ++c) dst[kp * ldd + col2 + c] = (float)b[gl * nb + N + c];
     }
   }
+  __syncwarp(mask);
+  // row gl of R X in FP64 (into the lane's own row of the B block), then rounded into wdst
+  if (gl < N) {
+#pragma unroll 1
+    for (int c = 0; c < N; ++c) {
+      double v = 0.0;
+#pragma unroll 1
+      for (int t = 0; t < N; ++t) v = fma((double)R[gl * ldr + t], a[t * N + c], v);
+      b[gl * nb + c] = v;
+    }
+  }
+  __syncwarp(mask);
+  if (gl < N) {
+#pragma unroll 1
+    for (int c = 0; c < N; ++c) wdst[gl * ldwd + c] = (float)b[gl * nb + c];
+  }
+  __syncwarp(mask);
   return ok;
 }
 
@@ -522,13 +548,13 @@ __device__ __forceinline__ bool tau_group_tc(const Ws<T>& w, const Grp& g, const
   bool stored = false;
   if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
     if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, g.gl)) {
-      ok = resolve64<N, G>(sc, RS_TAU, Cg, N, nullptr, sU, LD, Ag, N, nullptr, 0, sY, LD, 0, g.gl);
-      stored = true;
+      ok = resolve64<N, G>(sc, RS_TAU, Cg, N, nullptr, sU, LD, Ag, N, nullptr, 0, sY, LD, 0, sU, LD, g.gl);
+      stored = true;                            // Y in sY and Z = U Y (FP64) in sU
     }
   }
   if (!stored && g.gl < N) row_store<T, N>(sY + kpos * LD, b);
   __syncwarp();
-  tc::gemm<N, false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, true);   // Z = U Y over U
+  tc::gemm<N, false, false>(sU, LD, sY, LD, nullptr, 0, sU, LD, !stored);   // Z = U Y over U
   tc::gemm<N, true, false>(Ag, N, sU, LD, Pg, N, out, N, g.valid);      // P + A^T Z
   return ok;
 }
@@ -563,8 +589,8 @@ __device__ __forceinline__ bool tau_group(const Ws<T>& w, const Grp& g, const T*
   if constexpr (sizeof(T) == 4) {
     if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
       if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, g.gl)) {
-        ok = resolve64<N, G>(sc, RS_TAU, Cg, N, nullptr, sU, LD, sA, LD, nullptr, 0, sY, LD, 0, g.gl);
-        stored = true;
+        ok = resolve64<N, G>(sc, RS_TAU, Cg, N, nullptr, sU, LD, sA, LD, nullptr, 0, sY, LD, 0, sU, LD, g.gl);
+        stored = true;                          // Y in sY and Z = U Y (FP64) in sU
       }
     }
   }
@@ -578,7 +604,7 @@ __device__ __forceinline__ bool tau_group(const Ws<T>& w, const Grp& g, const T*
     row_mm<T, N, N, LD>(z, urow, sY);           // row r of Z = U Y
   }
   __syncwarp();
-  if (g.gl < N) row_store<T, N>(sU + r * LD, z); // Z over U
+  if (!stored && g.gl < N) row_store<T, N>(sU + r * LD, z); // Z over U
   __syncwarp();
   T o[N];
   grow_load<T, N>(o, Pg + r * N);
@@ -676,13 +702,13 @@ __device__ __forceinline__ bool compress_op_tc(const Ws<T>& w, int rr, const Grp
   bool stored = false;
   if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
     if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, gl)) {
-      okf = resolve64<N, G>(sc, RS_COMPRESS, sCl, LD, nullptr, sPt, LD, Al, N, Ar, N, sY, LD2, YW, gl);
-      stored = true;
+      okf = resolve64<N, G>(sc, RS_COMPRESS, sCl, LD, nullptr, sPt, LD, Al, N, Ar, N, sY, LD2, YW, sCl, LD, gl);
+      stored = true;                            // [Y1 | Y2] in sY and W = P~ Y1 (FP64) in sCl
     }
   }
   if (!stored && gl < N) row_store<T, 2 * YW>(sY + kpos * LD2, b);
   __syncwarp();
-  tc::gemm<N, false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, true);             // W = P~ Y1 over C_l
+  tc::gemm<N, false, false>(sPt, LD, sY, LD2, nullptr, 0, sCl, LD, !stored);          // W = P~ Y1 over C_l
   tc::gemm<N, true, false>(Al, N, sCl, LD, w.Ep + oj, N, w.Ep + ok_, N, g.valid);   // P_new = P_l + A_l^T W
   if (g.valid && gl < N) {
     // tape into slot j: (A_r, C_r, P~), read before slot k is rewritten
@@ -744,8 +770,9 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
   if constexpr (sizeof(T) == 4) {
     if (w.redo_count && g.valid && !(pr <= kSolveRatio)) {
       if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, gl)) {
-        okf = resolve64<N, G>(sc, RS_COMPRESS, sCl, LD, nullptr, sPt, LD, sAl, LD, sAr, LD, sY, LD2, YW, gl);
-        stored = true;
+        okf = resolve64<N, G>(sc, RS_COMPRESS, sCl, LD, nullptr, sPt, LD, sAl, LD, sAr, LD, sY, LD2, YW, sCl, LD,
+                              gl);
+        stored = true;                          // [Y1 | Y2] in sY and W = P~ Y1 (FP64) in sCl
       }
     }
   }
@@ -768,7 +795,7 @@ __device__ __forceinline__ bool compress_op(const Ws<T>& w, int rr, const Grp& g
     zero(wr);
     row_mm<T, N, N, LD2>(wr, pt, sY);
     __syncwarp();
-    if (gl < N) row_store<T, N>(sCl + r * LD, wr);
+    if (!stored && gl < N) row_store<T, N>(sCl + r * LD, wr);
   }
   __syncwarp();
   T pn[N];
@@ -1553,8 +1580,8 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
       if (w.redo_count && dnz && g.valid && !(pr <= kSolveRatio)) {
         if (double* sc = redo_slot<G>(w.redo_count, w.redo_cap, w.redo_scratch, w.redo_slot, gl)) {
           ok = resolve64<N, G>(sc, RS_LOCAL, nullptr, N, w.Delta + oj, sP, LD, nullptr, 0, nullptr, 0, sFi, LD, 0,
-                               gl);
-          stored = true;
+                               sD, LD, gl);
+          stored = true;                        // F^{-1} in sFi and W = P F^{-1} (FP64) in sD
         }
       }
     }
@@ -1565,6 +1592,7 @@ __global__ void kf_local_factor(Ws<T> w, int count) {
       T pr[N];
       row_load<T, N>(pr, sP + r * LD);
       row_mm<T, N, N, LD>(wrow, pr, sFi);       // row r of W = P F^{-1}
+      if (stored) row_load<T, N>(wrow, sD + r * LD);
       if (g.valid) {
 #pragma unroll
         for (int e2 = gl; e2 < NN; e2 += G) {

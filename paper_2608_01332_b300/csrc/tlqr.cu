@@ -2243,14 +2243,22 @@ int batched_ops(int kind, int count, int n, int m, const double* const* in, doub
     *W = (T*)take(count * nn, sizeof(T)), *Finv = (T*)take(count * nn, sizeof(T)),
     *LG = (T*)take(count * mm, sizeof(T));
   int* idx = (int*)take(S, sizeof(int));
-  int* status = (int*)take(1, sizeof(int));
+  int* status = (int*)take(2, sizeof(int));            // status word, FP64 re-solve tickets
   double* zeros = (double*)take(count * nn, sizeof(double));
   unsigned char* flags = (unsigned char*)take(count, 1);
+  // FP32 compile-time-n kernels: one FP64 re-solve slot per operation (the solver's rule)
+  double* redo = (sizeof(T) == 4 && !generic) ? (double*)take((size_t)count * 3 * nn, sizeof(double)) : nullptr;
   if (err) { for (void* p : mine) cudaFree(p); return TLQR_ERR_OOM; }
+  if (redo) {
+    w.redo_count = status + 1;
+    w.redo_cap = count;
+    w.redo_scratch = redo;
+    w.redo_slot = 3 * nn;
+  }
   std::vector<int> hidx(S);
   for (size_t t = 0; t < S; ++t) hidx[t] = (int)t;
   cudaError_t e = cudaMemcpyAsync(idx, hidx.data(), S * sizeof(int), cudaMemcpyHostToDevice, st);
-  if (!e) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (!e) e = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);
   w.U = U; w.Ea = Ea; w.Ec = Ec; w.Ep = Ep; w.contrib = contrib; w.status = status;
   w.K = K; w.Tm = Tm; w.Tr = Tr; w.W = W; w.Finv = Finv; w.LG = LG;
   auto in_ = [&](T* dst, const double* src, size_t elems) { if (!e) e = convert(dst, src, elems, sms, st); };

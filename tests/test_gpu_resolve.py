@@ -14,7 +14,7 @@ re-solves it took, and none when they are off.
 import numpy as np
 import pytest
 
-from oracle import riccati
+from oracle import ops, riccati
 from paper_2608_01332_b300 import inputs, tlqr
 
 torch = pytest.importorskip("torch")
@@ -61,10 +61,11 @@ def test_ill_conditioned_S_is_resolved_in_fp64(n, m):
     assert res["eta"] <= 1e-8 and abs(res["eta"] - info["eta"]) <= 1e-13
     ref = riccati.tree_riccati(p, n, m, d)
     assert riccati.forward_error(out, ref, p) <= 1e-6
-    # switched off: no re-solves are taken (whatever the refinement then reaches)
+    # switched off: no re-solves; the FP32 products U Y carry errors of ~1e-2 of P here,
+    # enough to make some G = R + B^T P B indefinite, so the factorisation may fail
     code_off, info_off, _ = _solve(p, n, m, d, fp64_resolve=-1)
     assert info_off["fp64_resolves"] == 0
-    assert code_off in (0, tlqr.TLQR_ERR_NO_CONVERGENCE, 4, 5)
+    assert code_off in (0, 3, 4, 5, tlqr.TLQR_ERR_NO_CONVERGENCE)
 
 
 def test_well_conditioned_problem_takes_no_resolve():
@@ -75,3 +76,45 @@ def test_well_conditioned_problem_takes_no_resolve():
     d = inputs.problem_data(p, 12, 4, rng, delta="subset", delta_value=1e-6)
     code, info, _ = _solve(p, 12, 4, d, has_delta=True)
     assert code == 0 and info["fp64_resolves"] == 0 and info["eta"] <= 1e-8
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+@pytest.mark.parametrize("n,m", [(8, 2), (12, 4), (16, 4), (32, 8)])
+def test_batched_rake_and_compression_with_large_U(n, m):
+    """The per-operation kernels on blocks with U ~ 1e6 and C = B R^{-1} B^T of
+    rank m (kappa(R) = 1e8): the re-solve forms U Y and P~ Y1 in FP64, so the
+    compile-time-n kernels stay within 1e-5 (relative to the largest entry) of
+    the FP64 oracle, where the run-time-n kernels (no re-solves) lose ~1e-2."""
+    rng = inputs.rng_for(1900 + n)
+    count = 48
+    B = rng.standard_normal((count, n, m)) / np.sqrt(n)
+    ev = np.logspace(0, 8, m)
+    C = (B / ev[None, None, :]) @ B.transpose(0, 2, 1)
+    G = rng.standard_normal((count, n, n))
+    U = 1e6 * (G @ G.transpose(0, 2, 1)) / n + 1e5 * np.eye(n)
+    A = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    H = rng.standard_normal((count, n, n))
+    P = 0.05 * H @ H.transpose(0, 2, 1) / n
+    ref = np.stack([ops.tau(A[t], C[t], P[t], U[t]) for t in range(count)])
+    errs = {}
+    for name, prec in (("fixed", MIXED), ("generic", MIXED | tlqr.TLQR_BATCHED_GENERIC)):
+        out = _dev(np.zeros((count, n, n)))
+        tlqr.tlqr_batched_tau(_dev(A), _dev(C), _dev(P), _dev(U), out, prec)
+        errs[name] = np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert errs["fixed"] <= 1e-5, errs
+    assert errs["generic"] > 10 * errs["fixed"], errs
+    # compression with the large block in P~ = P_r + U
+    Ar = rng.standard_normal((count, n, n)) / np.sqrt(n)
+    K = rng.standard_normal((count, n, n))
+    Cr = 0.1 * K @ K.transpose(0, 2, 1) / n
+    Pr = P.copy()
+    outs = [_dev(np.zeros((count, n, n))) for _ in range(4)]
+    tlqr.tlqr_batched_compose(_dev(A), _dev(C), _dev(P), _dev(Ar), _dev(Cr), _dev(Pr), _dev(U), *outs, MIXED)
+    got = [o.cpu().numpy() for o in outs]
+    for t in range(count):
+        (a, c, pn), tape = ops.compose((Ar[t], Cr[t], Pr[t]), (A[t], C[t], P[t]), U[t])
+        for g_, want in ((got[0][t], a), (got[1][t], c), (got[2][t], pn), (got[3][t], tape[2])):
+            assert np.abs(g_ - want).max() <= 1e-5 * max(1.0, np.abs(want).max())
