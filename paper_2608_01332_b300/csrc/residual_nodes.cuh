@@ -21,6 +21,9 @@
 // maxima ||res||, ||z||, ||b||, ||K|| are folded per block (one tree) or per
 // tree (a forest), exactly as the row kernels do.
 //
+// The node's FP64 vectors (x_j, x_parent, y_j, u_j, c_j, r_j, q_j) travel the
+// same way, and each lane splits its entries into float-float pairs in shared
+// memory, so no separate split pass over x, u, y is needed.
 // Blocks sit in shared memory densely (a bulk copy cannot pad rows); a lane
 // walks its row starting at column r and wrapping around, so that the lanes of
 // a group read different banks.  Every wait on an mbarrier is bounded: a wait
@@ -145,14 +148,18 @@ struct Maxima {
 };
 
 // Group of the edge pass in shared memory: two mbarriers (16 bytes), two
-// buffers [A | Delta | B | M | R] of dense FP64 blocks, then the float-float
-// vectors x_p, y_j (N each) and u_j (M), hi and lo.  With n and m even every
-// block is a multiple of 16 bytes, so every block starts 16-byte aligned.
+// buffers [A | Delta | B | M | R | x_j x_p y_j c_j q_j (N each) u_j r_j (M each)]
+// of dense FP64 blocks and vectors, then the float-float vectors x_p, y_j (N
+// each) and u_j (M), hi and lo.  With n and m even every block and vector is a
+// multiple of 16 bytes, so each starts 16-byte aligned.
 template <int N, int M>
 struct EdgeBuf {
   static_assert(N % 2 == 0 && M % 2 == 0, "bulk copies need 16-byte multiples");
-  __host__ __device__ static constexpr int doubles(bool has_delta, bool has_M) {
+  __host__ __device__ static constexpr int mats(bool has_delta, bool has_M) {
     return N * N * (has_delta ? 2 : 1) + N * M * (has_M ? 2 : 1) + M * M;
+  }
+  __host__ __device__ static constexpr int doubles(bool has_delta, bool has_M) {
+    return mats(has_delta, has_M) + 5 * N + 2 * M;
   }
   __host__ __device__ static constexpr int group_bytes(bool has_delta, bool has_M) {
     return 16 + 2 * doubles(has_delta, has_M) * 8 + ((4 * N + 2 * M) * 4 + 15) / 16 * 16;
@@ -169,10 +176,10 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using EB = EdgeBuf<N, M>;
   constexpr int G = RG<N>::G, OPS = RG<N>::OPS;
-  constexpr unsigned kA = N * N * 8, kB = N * M * 8, kR = M * M * 8;
+  constexpr unsigned kA = N * N * 8, kB = N * M * 8, kR = M * M * 8, kN = N * 8, kM = M * 8;
   const bool hd = a.Delta != nullptr, hm = a.M != nullptr, ks = a.with_knorm;
   const int gl = threadIdx.x & (G - 1), gid = (threadIdx.x & 31) / G;
-  const int nd = EB::doubles(hd, hm);
+  const int nd = EB::doubles(hd, hm), nmat = EB::mats(hd, hm);
   unsigned char* gbase = smem_raw + (size_t)((threadIdx.x >> 5) * OPS + gid) * EB::group_bytes(hd, hm);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(gbase);
   double* buf0 = reinterpret_cast<double*>(gbase + 16);
@@ -194,12 +201,15 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
   };
   auto has_delta = [&](int j) { return hd && (!na.dflag || na.dflag[j]); };
   // lane 0 of the group: the copies of node j's blocks into buffer b
+  // vectors of buffer b: x_j, x_p, y_j, c_j, q_j (N each), u_j, r_j (M each)
+  auto vslot = [&](int b) -> double* { return buf0 + (size_t)b * nd + nmat; };
   auto issue = [&](int j, int b, bool first) {
     if (gl != 0) return;
-    const bool hp = a.parent[j] >= 0, dz = has_delta(j);
-    const unsigned bytes = (hp ? kA + kB + kR + (hm ? kB : 0u) : 0u) + (dz ? kA : 0u);
+    const int p = a.parent[j];
+    const bool hp = p >= 0, dz = has_delta(j);
+    const unsigned bytes = (hp ? kA + kB + kR + (hm ? kB : 0u) + kN : 0u) + (dz ? kA : 0u) + 4 * kN + 2 * kM;
     mbar_expect(bar + b, bytes);
-    if (na.withhold && bytes && blockIdx.x == 0 && threadIdx.x == 0 && first) return;
+    if (na.withhold && blockIdx.x == 0 && threadIdx.x == 0 && first) return;
     if (hp) {
       bulk_load(slot(b, 0), a.A + (size_t)j * nn, kA, bar + b);
       bulk_load(slot(b, 2), a.B + (size_t)j * nm, kB, bar + b);
@@ -207,6 +217,14 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
       if (hm) bulk_load(slot(b, 3), a.M + (size_t)j * nm, kB, bar + b);
     }
     if (dz) bulk_load(slot(b, 1), a.Delta + (size_t)j * nn, kA, bar + b);
+    double* v = vslot(b);
+    bulk_load(v, a.x + (size_t)j * N, kN, bar + b);
+    if (hp) bulk_load(v + N, a.x + (size_t)p * N, kN, bar + b);
+    bulk_load(v + 2 * N, a.y + (size_t)j * N, kN, bar + b);
+    bulk_load(v + 3 * N, a.c + (size_t)j * N, kN, bar + b);
+    bulk_load(v + 4 * N, a.q + (size_t)j * N, kN, bar + b);
+    bulk_load(v + 5 * N, a.u + (size_t)j * M, kM, bar + b);
+    bulk_load(v + 5 * N + M, a.r + (size_t)j * M, kM, bar + b);
   };
   if (gl == 0) {
     mbar_init(bar);
@@ -243,16 +261,19 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
     pend &= ~(1u << cb);
     const int p = a.parent[j];
     const bool has_p = p >= 0, dz = has_delta(j);
+    const double* V = vslot(cb);
+    const double *vxj = V, *vxp = V + N, *vyj = V + 2 * N, *vcj = V + 3 * N, *vqj = V + 4 * N, *vuj = V + 5 * N,
+                 *vrj = V + 5 * N + M;
     if (gl < N) {
-      vyh[gl] = f.yh[(size_t)j * N + gl];
-      vyl[gl] = f.yl[(size_t)j * N + gl];
-      vxh[gl] = has_p ? f.xh[(size_t)p * N + gl] : 0.f;
-      vxl[gl] = has_p ? f.xl[(size_t)p * N + gl] : 0.f;
+      dsplit(vyj[gl], vyh[gl], vyl[gl]);
+      if (has_p) {
+        dsplit(vxp[gl], vxh[gl], vxl[gl]);
+      } else {
+        vxh[gl] = 0.f;
+        vxl[gl] = 0.f;
+      }
     }
-    if (gl < M) {
-      vuh[gl] = f.uh[(size_t)j * M + gl];
-      vul[gl] = f.ul[(size_t)j * M + gl];
-    }
+    if (gl < M) dsplit(vuj[gl], vuh[gl], vul[gl]);
     __syncwarp();
     const double *sA = slot(cb, 0), *sD = slot(cb, 1), *sB = slot(cb, 2), *sM = slot(cb, 3), *sR = slot(cb, 4);
     const int r = gl < N ? gl : 0;
@@ -261,8 +282,10 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
     {
       const size_t tr = (size_t)j * N + r;
       FF s{0.f, 0.f};
-      ff_add(s, a.c[tr]);
-      ff_add2(s, -f.xh[tr], -f.xl[tr]);
+      ff_add(s, vcj[r]);
+      float xh, xl;
+      dsplit(vxj[r], xh, xl);
+      ff_add2(s, -xh, -xl);
       float rs = 1.f;
       if (dz) rs += ff_dot_row<N>(s, sD + r * N, vyh, vyl, r, -1.f);
       if (has_p) {
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
           const int c = part + k * P;
           if (c < M) rs += ff_fma_d(s, sR[ua * M + c], vuh[c], vul[c]);
         }
-        if (part == 0) ff_add(s, a.r[(size_t)j * M + ua]);
+        if (part == 0) ff_add(s, vrj[ua]);
       }
 #pragma unroll
       for (int off = P / 2; off; off >>= 1) {
@@ -335,13 +358,12 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
     {
       double zv = 0.0, bv = 0.0;
       if (gl < N) {
-        const size_t tr = (size_t)j * N + gl;
-        zv = amax(amax(0.0, a.x[tr]), a.y[tr]);
-        bv = fmax(fabs(a.q[tr]), fabs(a.c[tr]));
+        zv = amax(amax(0.0, vxj[gl]), vyj[gl]);
+        bv = fmax(fabs(vqj[gl]), fabs(vcj[gl]));
       }
       if (has_p && gl < M) {
-        zv = amax(zv, a.u[(size_t)j * M + gl]);
-        bv = fmax(bv, fabs(a.r[(size_t)j * M + gl]));
+        zv = amax(zv, vuj[gl]);
+        bv = fmax(bv, fabs(vrj[gl]));
       }
       row[1] = dbits_abs(zv);
       row[2] = dbits_abs(bv);
@@ -368,11 +390,12 @@ __global__ void __launch_bounds__(128) k_res_edge(ResidualArgs a, FFArgs f, Node
   }
 }
 
-// Group of the node pass: two mbarriers, two dense Q buffers, x_i (hi, lo).
+// Group of the node pass: two mbarriers, two buffers [Q | x_i q_i y_i] (FP64),
+// x_i (hi, lo).
 template <int N>
 struct NodeBuf {
   static_assert(N % 2 == 0, "bulk copies need 16-byte multiples");
-  static constexpr int doubles = N * N;
+  static constexpr int doubles = N * N + 3 * N;
   static constexpr int group_bytes = 16 + 2 * doubles * 8 + (2 * N * 4 + 15) / 16 * 16;
 };
 
@@ -382,7 +405,7 @@ __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, Node
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using NB = NodeBuf<N>;
   constexpr int G = RG<N>::G, OPS = RG<N>::OPS;
-  constexpr unsigned kQ = N * N * 8;
+  constexpr unsigned kQ = N * N * 8, kN = N * 8;
   const int gl = threadIdx.x & (G - 1), gid = (threadIdx.x & 31) / G;
   unsigned char* gbase = smem_raw + (size_t)((threadIdx.x >> 5) * OPS + gid) * NB::group_bytes;
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(gbase);
@@ -392,9 +415,13 @@ __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, Node
   const bool ks = a.with_knorm;
   auto issue = [&](int i, int b, bool first) {
     if (gl != 0) return;
-    mbar_expect(bar + b, kQ);
+    mbar_expect(bar + b, kQ + 3 * kN);
     if (na.withhold && blockIdx.x == 0 && threadIdx.x == 0 && first) return;
-    bulk_load(buf0 + (size_t)b * NB::doubles, a.Q + (size_t)i * N * N, kQ, bar + b);
+    double* q = buf0 + (size_t)b * NB::doubles;
+    bulk_load(q, a.Q + (size_t)i * N * N, kQ, bar + b);
+    bulk_load(q + N * N, a.x + (size_t)i * N, kN, bar + b);
+    bulk_load(q + N * N + N, a.q + (size_t)i * N, kN, bar + b);
+    bulk_load(q + N * N + 2 * N, a.y + (size_t)i * N, kN, bar + b);
   };
   if (gl == 0) {
     mbar_init(bar);
@@ -428,17 +455,17 @@ __global__ void __launch_bounds__(128) k_res_node(ResidualArgs a, FFArgs f, Node
     }
     par ^= 1u << cb;
     pend &= ~(1u << cb);
-    if (gl < N) {
-      vxh[gl] = f.xh[(size_t)i * N + gl];
-      vxl[gl] = f.xl[(size_t)i * N + gl];
-    }
-    __syncwarp();
     const double* sQ = buf0 + (size_t)cb * NB::doubles;
+    const double *vxi = sQ + N * N, *vqi = vxi + N, *vyi = vqi + N;
+    if (gl < N) dsplit(vxi[gl], vxh[gl], vxl[gl]);
+    __syncwarp();
     const int r = gl < N ? gl : 0;
     const size_t tr = (size_t)i * N + r;
     FF s{0.f, 0.f};
-    ff_add(s, a.q[tr]);
-    ff_add2(s, -f.yh[tr], -f.yl[tr]);
+    ff_add(s, vqi[r]);
+    float yh, yl;
+    dsplit(vyi[r], yh, yl);
+    ff_add2(s, -yh, -yl);
     float rs = 1.f + ff_dot_row<N>(s, sQ + r * N, vxh, vxl, r);
     for (int k = a.child_start[i]; k < a.child_start[i + 1]; ++k) {
       const int jc = a.child_list[k];

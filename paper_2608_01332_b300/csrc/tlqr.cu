@@ -1106,13 +1106,14 @@ bool res_node_default(int n) { return n == 16; }
 // polls of one mbarrier wait of the node residual before it gives up (each
 // poll may suspend the thread for a while, so this is ~a second or more)
 constexpr int kBarSpin = 1 << 20;
-bool use_node_residual(const tlqr_factor_t* f, const tlqr_problem& p) {
+bool use_node_residual(const tlqr_factor_t* f, const tlqr_problem& p, const double* x, const double* u,
+                       const double* y) {
   if (f->fixed_m == 0 || f->ts != 4) return false;
   const int kind = f->opt.residual;
   if (kind == 1 || (kind == 0 && !res_node_default(f->fixed_n))) return false;
   auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15u) == 0; };
   return al(p.Q) && al(p.A) && al(p.B) && al(p.R) && (!f->opt.has_M || al(p.M)) &&
-         (!f->opt.has_delta || al(p.Delta));
+         (!f->opt.has_delta || al(p.Delta)) && al(p.q) && al(p.r) && al(p.c) && al(x) && al(u) && al(y);
 }
 
 // ff = 1: float-float kernel on the FP32 pipe (refinement); ff = 0: plain FP64 kernel.
@@ -1135,12 +1136,13 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   cudaError_t e = cudaMemsetAsync(f->maxes, 0, (with_knorm ? 4 : 3) * (size_t)a.T * sizeof(unsigned long long), st);
   if (e) return e;
   FFArgs fa{};
-  if (ff) {
+  // the node kernels split x, u, y themselves and form all four maxima
+  const bool by_node = ff && use_node_residual(f, p, x, u, y);
+  if (ff && !by_node) {
     // split x, u, y once per call; for one tree ||z|| and ||b|| maxima come
     // from the same pass (a forest forms them per tree in the residual kernel)
     const size_t N = P->N, n = f->opt.n, m = f->opt.m;
-    const bool by_node = use_node_residual(f, p);   // node kernels form all four maxima themselves
-    const int zs = (a.tree || by_node) ? -1 : 1, bs = (a.tree || by_node) ? -1 : 2;
+    const int zs = a.tree ? -1 : 1, bs = a.tree ? -1 : 2;
     SplitList L{};
     auto add = [&](const double* src, float* hi, float* lo, size_t len, int slot) {
       L.src[L.count] = src; L.hi[L.count] = hi; L.lo[L.count] = lo; L.len[L.count] = len; L.slot[L.count] = slot;
@@ -1166,7 +1168,7 @@ cudaError_t run_residual(tlqr_factor_t* f, Recorder* rc, const tlqr_problem& p, 
   const bool timed = rc && (rc->mask >> TLQR_K_RESIDUAL) & 1u;
   EvPair ev{TLQR_K_RESIDUAL, nullptr, nullptr, P->N};
   if (timed) { ev.a = rc->event(); ev.b = rc->event(); rc->record(ev.a, st); }
-  if (ff && use_node_residual(f, p)) {
+  if (by_node) {
     const rn::NodeArgs na{f->rwh,
                           f->rwl,
                           f->rwk,
