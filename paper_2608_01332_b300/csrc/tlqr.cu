@@ -1098,10 +1098,11 @@ cudaError_t dispatch_res_nodes(int n, int m, const ResidualArgs& a, const FFArgs
 // kernels, 2 = the node-organised bulk-copy kernels, 0 = the library's choice
 // per n (kResNodeDefault).  The node kernels need compile-time (n, m) and
 // 16-byte aligned matrix arrays; otherwise the row kernels run.
-// Measured on B300 (refinement residual per step, row kernels vs node kernels):
-// n = 12 (long trunk, 65,536 nodes) 0.25 vs 0.34 ms; n = 16 (1,024 trees,
-// 2.9 M nodes) 23.7 vs 14.2 ms; n = 32 (2^20 nodes) 23.1 vs 24.4 ms.
-bool res_node_default(int n) { return n == 16; }
+// Measured on B300 (refinement residual per step, row kernels vs node kernels
+// with bulk-copied blocks and vectors): n = 12 (long trunk, 65,536 nodes) 0.24
+// vs 0.32 ms; n = 16 (1,024 trees, 2.9 M nodes) 23.7 vs 14.5 ms; n = 32
+// (2^20 nodes) 23.1 vs 21.1 ms.
+bool res_node_default(int n) { return n == 16 || n == 32; }
 
 // polls of one mbarrier wait of the node residual before it gives up (each
 // poll may suspend the thread for a while, so this is ~a second or more)
