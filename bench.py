@@ -193,6 +193,8 @@ def run_serve(args, rank, world, dist):
     srv.drain()
     span = time.perf_counter() - t0
     errors = [repr(r.error) for r in warm + burst if r.error is not None]
+    print(json.dumps({"serve_progress": "burst", "requests": len(burst), "seconds": span}), file=sys.stderr,
+          flush=True)
 
     def solves(r):                              # Newton solves a request ran (IPM requests may stop early)
         if r.bounds is None:
@@ -232,6 +234,8 @@ def run_serve(args, rank, world, dist):
                                                             for r in reqs for i in r.infos]))
                      if traffic.ipm else None})
         rates.append(summ)
+        print(json.dumps({"serve_progress": "rate", **{k: v for k, v in summ.items() if not isinstance(v, list)}}),
+              file=sys.stderr, flush=True)
     stats = dict(srv.stats)
     peak = srv.peak
     srv.close()

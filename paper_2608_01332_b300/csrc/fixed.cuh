@@ -277,8 +277,10 @@ struct GjBuf {
 // work).  Double-buffered broadcast rows need one __syncwarp per step.
 // bc: GjBuf<T, N, R>::elems shared elements of this group, 16-byte aligned.
 // Returns false (uniformly in the group) on a zero or nonfinite pivot.
-// ratio: largest |pivot| over smallest |pivot| (the same in every lane of the
-// group), a lower bound on the condition number of S.
+// ratio (the same in every lane of the group): a lower bound on the condition
+// number of S, the larger of (largest |pivot|) / (smallest |pivot|) and
+// ||S||_inf ||X||_inf / ||B||_inf (since ||X|| <= ||S^{-1}|| ||B||).  The pivot
+// ratio alone can stay far below kappa(S) when S = I + (low-rank, large).
 template <typename T, int N, int G, int R>
 __device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kpos, float& ratio) {
   using Bf = GjBuf<T, N, R>;
@@ -289,6 +291,20 @@ __device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kp
   bool ok = true;
   T myinv = T(1);
   T imin = T(INFINITY), imax = T(0);
+  // row sums of |S| and |B| (this lane's row; FP32 kernels only, where the
+  // estimate decides on a re-solve)
+  float s_norm = 0.f, b_norm = 0.f;
+  if constexpr (sizeof(T) == 4) {
+    float sn = 0.f, bn = 0.f;
+    if (gl < N) {
+#pragma unroll
+      for (int c = 0; c < N; ++c) sn += fabsf(a[c]);
+#pragma unroll
+      for (int c = 0; c < R; ++c) bn += fabsf(b[c]);
+    }
+    s_norm = __uint_as_float(group_umax<G>(__float_as_uint(sn)));
+    b_norm = __uint_as_float(group_umax<G>(__float_as_uint(bn)));
+  }
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     T* row = bc + (k & 1) * Bf::ROW;
@@ -340,8 +356,18 @@ __device__ __forceinline__ bool ggj(T (&a)[N], T (&b)[R], int gl, T* bc, int& kp
   }
 #pragma unroll
   for (int c = 0; c < R; ++c) b[c] *= myinv;
+  float est = 0.f;
+  if constexpr (sizeof(T) == 4) {
+    float xn = 0.f;
+    if (gl < N) {
+#pragma unroll
+      for (int c = 0; c < R; ++c) xn += fabsf(b[c]);
+    }
+    const float x_norm = __uint_as_float(group_umax<G>(__float_as_uint(xn)));
+    est = b_norm > 0.f ? s_norm * x_norm / b_norm : 0.f;
+  }
   __syncwarp();
-  ratio = (float)(imax / imin);
+  ratio = fmaxf((float)(imax / imin), est);
   return ok;
 }
 template <typename T, int N, int G, int R>
