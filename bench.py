@@ -193,8 +193,8 @@ def run_serve(args, rank, world, dist):
     srv.drain()
     span = time.perf_counter() - t0
     errors = [repr(r.error) for r in warm + burst if r.error is not None]
-    print(json.dumps({"serve_progress": "burst", "requests": len(burst), "seconds": span}), file=sys.stderr,
-          flush=True)
+    print(json.dumps({"serve_progress": "burst", "requests": len(burst), "seconds": span, "errors": errors[:3]}),
+          file=sys.stderr, flush=True)
 
     def solves(r):                              # Newton solves a request ran (IPM requests may stop early)
         if r.bounds is None:
@@ -234,7 +234,8 @@ def run_serve(args, rank, world, dist):
                                                             for r in reqs for i in r.infos]))
                      if traffic.ipm else None})
         rates.append(summ)
-        print(json.dumps({"serve_progress": "rate", **{k: v for k, v in summ.items() if not isinstance(v, list)}}),
+        print(json.dumps({"serve_progress": "rate", **{k: v for k, v in summ.items() if not isinstance(v, list)},
+                          "errors": [repr(r.error) for r in reqs if r.error is not None][:3]}),
               file=sys.stderr, flush=True)
     stats = dict(srv.stats)
     peak = srv.peak
@@ -304,7 +305,11 @@ def load_peaks():
 # launch divided by its operation count) from one `ncu --set full` capture of
 # the round-1 launch of the headline workload; keyed by (kernel kind, n, m,
 # precision).  Entries must be dropped when the kernel changes.
-NCU_BYTES_PER_OP = {}
+# residual (float-float row kernel, refinement launches skipping zero Delta
+# rows) on the long trunk, N = 65,536: dram__bytes_read.sum + write.sum =
+# 274.67 MB and 271.72 MB for the two launches of a step (with / without the
+# ||K|| row sums), i.e. 4,168.6 bytes per node (profiles/k_residual_ff_long_trunk_N65536.md)
+NCU_BYTES_PER_OP = {("residual", 12, 4, "mixed"): 4168.6}
 
 
 # ----------------------------------------------------------------- algorithmic work per unit
@@ -906,8 +911,8 @@ def run_ours(args, rank, world, dist):
         bpo = NCU_BYTES_PER_OP.get((dominant, n, m, args.mode))
         if bpo is not None:
             roof["traffic"] = bpo * pd["units"] / pd["timed"]
-            roof["traffic_note"] = ("ncu DRAM bytes per operation of the round-1 launch x this run's average "
-                                    "operations per launch (bytes per launch)")
+            roof["traffic_note"] = ("ncu DRAM bytes per unit of this kernel (capture summarised under profiles/) "
+                                    "x this run's average units per launch (bytes per launch)")
 
     cfg = {"workload": w.name, "N": N, "n": n, "m": m, "precision": args.mode, "rounds": stats["rounds"],
            "execution": tuned or "library defaults",
