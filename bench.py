@@ -86,8 +86,10 @@ def parse():
     ap.add_argument("--e2e", action="store_true", help="run the end-to-end leg for the 10^6-node workloads too")
     ap.add_argument("--no-spine", action="store_true",
                     help="skip the per-round roofline of the N=2^20 spine tree in the default line")
-    ap.add_argument("--pdl", type=int, default=None, choices=[0, -1],
-                    help="programmatic dependent launch of the pass kernels (0 on, -1 off); default: on")
+    ap.add_argument("--pdl", type=int, default=None, choices=[0, 1],
+                    help="programmatic dependent launch of the pass kernels (1 on, 0 off); default: off")
+    ap.add_argument("--fp64-resolve", type=int, default=None, choices=[0, -1],
+                    help="FP64 re-solves of ill-conditioned eliminations (0 on, -1 off); default: on")
     ap.add_argument("--residual", type=int, default=None, choices=[0, 1, 2],
                     help="refinement residual kernels (1 rows, 2 node-organised); default: the tuned table's")
     ap.add_argument("--quick", action="store_true",
@@ -174,7 +176,8 @@ def run_serve(args, rank, world, dist):
     prec = tlqr.TLQR_PREC_MIXED if args.mode == "mixed" else tlqr.TLQR_PREC_FP64
     traffic = ServeTraffic(dev, ipm=args.serve_mode == "ipm")
     slots = args.slots
-    srv = serve.Server(slots=slots)
+    over = {k: v for k, v in (("pdl", args.pdl), ("fp64_resolve", args.fp64_resolve)) if v is not None}
+    srv = serve.Server(slots=slots, backend=serve.TlqrBackend(**over))
     k = 0
     # warm-up: every topology once (plans, factors, graphs)
     warm = []
@@ -735,6 +738,8 @@ def run_ours(args, rank, world, dist):
         tuned["residual"] = args.residual
     if args.pdl is not None:
         tuned["pdl"] = args.pdl
+    if args.fp64_resolve is not None:
+        tuned["fp64_resolve"] = args.fp64_resolve
     solver = tlqr.TreeLQR(w.parent, n, m, prec, has_delta=has_delta, forest=forest, **tuned)
     stats = solver.stats()
 

@@ -108,9 +108,10 @@ class Request:
 class TlqrBackend:
     """The GPU path: C-ABI plans and factors, torch for buffers and streams."""
 
-    def __init__(self, device=None):
+    def __init__(self, device=None, **option_overrides):
         import torch
         self.torch = torch
+        self.option_overrides = option_overrides    # extra tlqr options for every factor (make_options keywords)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
 
     def plan(self, parent):
@@ -120,7 +121,7 @@ class TlqrBackend:
         tlqr.tlqr_plan_destroy(plan)
 
     def options(self, req: Request):
-        return tlqr.make_options(req.n, req.m, req.precision, has_delta=req.has_delta)
+        return tlqr.make_options(req.n, req.m, req.precision, has_delta=req.has_delta, **self.option_overrides)
 
     def workspace_bytes(self, plan, opts) -> int:
         return tlqr.tlqr_factor_workspace_bytes(plan, opts)
