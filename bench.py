@@ -86,8 +86,8 @@ def parse():
     ap.add_argument("--e2e", action="store_true", help="run the end-to-end leg for the 10^6-node workloads too")
     ap.add_argument("--no-spine", action="store_true",
                     help="skip the per-round roofline of the N=2^20 spine tree in the default line")
-    ap.add_argument("--pdl", type=int, default=None, choices=[0, 1],
-                    help="programmatic dependent launch of the pass kernels (1 on, 0 off); default: off")
+    ap.add_argument("--pdl", type=int, default=None, choices=[0, -1],
+                    help="programmatic dependent launch of the pass kernels (0 on, -1 off); default: on")
     ap.add_argument("--fp64-resolve", type=int, default=None, choices=[0, -1],
                     help="FP64 re-solves of ill-conditioned eliminations (0 on, -1 off); default: on")
     ap.add_argument("--residual", type=int, default=None, choices=[0, 1, 2],

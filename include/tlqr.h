@@ -127,11 +127,11 @@ typedef struct {
                             whose FP32 pivots span more than 1e4 is solved again in
                             FP64 and rounded to FP32 (up to 4096 per factorisation;
                             tlqr_info.fp64_resolves counts them); < 0 = never       */
-  int32_t pdl;           /* 1 = the kernels of the factorisation and of the
+  int32_t pdl;           /* 0 (default) = the kernels of the factorisation and of the
                             right-hand-side passes are launched with programmatic
                             dependent launch (each may be scheduled while its
                             predecessor drains, and waits for its results on the
-                            device); 0 (default) = plain stream-ordered launches    */
+                            device); < 0 = plain stream-ordered launches            */
 } tlqr_options;
 
 #define TLQR_MAX_DIM 64

@@ -1200,7 +1200,7 @@ cudaError_t run_seq(tlqr_factor_t* f, GraphCache* g, std::vector<uintptr_t> key,
   key.push_back(f->prof.mask);
   if (!f->opt.use_graphs || f->graphs_broken || !g) {
     Recorder r;
-    r.pdl = f->opt.pdl > 0;
+    r.pdl = f->opt.pdl >= 0;
     r.mask = f->prof.mask;
     r.pool = &f->prof.pool;
     cudaError_t e = body(&r);
@@ -1210,7 +1210,7 @@ cudaError_t run_seq(tlqr_factor_t* f, GraphCache* g, std::vector<uintptr_t> key,
   if (!g->exec || g->key != key) {
     g->clear();
     Recorder r;
-    r.pdl = f->opt.pdl > 0;
+    r.pdl = f->opt.pdl >= 0;
     r.mask = f->prof.mask;
     r.capture = true;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
