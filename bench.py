@@ -109,10 +109,14 @@ WORKLOADS = {
 # ----------------------------------------------------------------- serving workload
 class ServeTraffic:
     """Requests of the serving workload: a pool of driving-style topologies
-    (N uniform in [500, 50000]); a request picks one, draws its base data on
-    the device, and each of its solves perturbs the barrier-like diagonal of Q
-    and R and draws a fresh gradient (q, r) -- in place, so that the buffers
-    (and the factor's captured graphs) stay the same across its solves."""
+    (N uniform in [500, 50000]), each with its model matrices drawn once on the
+    device (the plant of one scenario-tree shape; drawing Haar-orthogonal A
+    blocks for every request would cost more host time than the solves); a
+    request picks a topology and draws its own gradient (q, r) -- and, as an
+    interior-point request, its own control bounds; in the perturbation mode
+    each of its solves also perturbs the barrier-like diagonal of Q and R --
+    in place, so that the buffers (and the factor's captured graphs) stay the
+    same across its solves."""
 
     def __init__(self, device, seed=inputs.BASE_SEED + 4, topologies=16, n=6, m=2, iterations=20,
                  lo=500, hi=50000, ipm=True):
@@ -121,6 +125,7 @@ class ServeTraffic:
         self.ipm = ipm
         self.trees = [inputs.driving_tree(rng, int(rng.integers(lo, hi + 1))) for _ in range(topologies)]
         self.rng = rng
+        self.bases = [inputs.problem_data_device(p, n, m, seed * 1000 + t, device) for t, p in enumerate(self.trees)]
 
     def request(self, k, precision, t=None):
         """Request k (its data are a function of k alone) on topology t (drawn when None)."""
@@ -129,15 +134,21 @@ class ServeTraffic:
         if t is None:
             t = int(self.rng.integers(len(self.trees)))
         parent = self.trees[t]
-        base = inputs.problem_data_device(parent, self.n, self.m, self.seed * 1000 + k, self.device)
-        live = {kk: (None if v is None else v.clone()) for kk, v in base.items()}
         g = torch.Generator(device=self.device)
         g.manual_seed(self.seed * 7919 + k)
         N, n, m = len(parent), self.n, self.m
         nr = torch.from_numpy(parent >= 0).to(self.device)
+        base = dict(self.bases[t])
+        base["q"] = torch.randn((N, n), generator=g, dtype=torch.float64, device=self.device)
+        base["r"] = torch.randn((N, m), generator=g, dtype=torch.float64, device=self.device) * nr[:, None]
+
+        live = None
 
         def data(it, stream):
+            nonlocal live
             with torch.cuda.stream(stream):
+                if live is None:                # the request's own copies, made on its slot's stream
+                    live = {kk: (None if v is None else v.clone()) for kk, v in base.items()}
                 sq = torch.rand((N, n), generator=g, dtype=torch.float64, device=self.device)
                 sr = torch.rand((N, m), generator=g, dtype=torch.float64, device=self.device) * nr[:, None]
                 live["Q"].copy_(base["Q"]).diagonal(dim1=1, dim2=2).add_(sq)
