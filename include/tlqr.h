@@ -568,7 +568,11 @@ typedef struct {
   double tol;            /* target mean complementarity, default 1e-9 */
   int32_t no_fp64_fallback; /* 1: never allocate the FP64 factor object; a MIXED Newton
                                solve whose refinement stalls is used as it stands
-                               (an inexact Newton step) -- for callers that budget
+                               (an inexact Newton step), and a Newton system the FP32
+                               factors cannot take (not positive definite, singular or
+                               nonfinite once the barrier terms outgrow FP32) ends the
+                               iteration at the current iterate with
+                               TLQR_ERR_NO_CONVERGENCE -- for callers that budget
                                device memory per request */
 } tlqr_ipm_options;
 

@@ -311,6 +311,7 @@ extern "C" int tlqr_ipm_box(const tlqr_plan_t* plan, tlqr_factor_t* f, const tlq
   tlqr_factor_t* f64 = nullptr;
   auto fail64 = [&](int code) { if (f64) tlqr_factor_destroy(f64); return fail(code); };
   bool use64 = false;                        // MIXED: Newton systems now solved in FP64
+  bool stopped = false;                      // MIXED without FP64 fallback: a Newton system failed
   const bool mixed = o64_possible(f), allow64 = !(opts && opts->no_fp64_fallback);
   auto make64 = [&]() -> int {
     if (f64) return TLQR_OK;
@@ -335,6 +336,12 @@ extern "C" int tlqr_ipm_box(const tlqr_plan_t* plan, tlqr_factor_t* f, const tlq
         rc == TLQR_ERR_NO_CONVERGENCE || rc == TLQR_ERR_NOT_PD || rc == TLQR_ERR_NONFINITE || rc == TLQR_ERR_SINGULAR;
     if (rc == TLQR_ERR_NO_CONVERGENCE && opts && opts->no_fp64_fallback) {
       rc = TLQR_OK;                           // inexact Newton step at the accuracy refinement reached
+    } else if (precision_failure && !use64 && mixed && !allow64) {
+      // the FP32 factors cannot take this Newton system (the barrier terms have outgrown
+      // them) and no FP64 factor may be allocated: stop at the current iterate, which the
+      // failed step has not touched; the call returns TLQR_ERR_NO_CONVERGENCE
+      stopped = true;
+      break;
     } else if (precision_failure && !use64 && mixed && allow64) {
       if ((rc = make64())) return fail64(rc);
       rc = tlqr_solve(f64, &pt, &sol, stream);
@@ -367,13 +374,13 @@ extern "C" int tlqr_ipm_box(const tlqr_plan_t* plan, tlqr_factor_t* f, const tlq
     if (mean_gap <= o.tol && alpha >= 1.0) break;
     mu = o.sigma * mean_gap;
   }
-  const bool converged = mean_gap <= o.tol && alpha >= 1.0;
+  const bool converged = !stopped && mean_gap <= o.tol && alpha >= 1.0;
   if (converged) {
     k_ipm_duals<<<blocks, threads, 0, st>>>(a, prob->M, prob->B);
     if (cudaGetLastError() || cudaStreamSynchronize(st)) return fail64(TLQR_ERR_CUDA);
   }
   if (info) {
-    info->iterations = std::min(it, o.max_iter);
+    info->iterations = std::min(stopped ? it - 1 : it, o.max_iter);
     info->mu = mu;
     info->mean_gap = mean_gap;
     info->last_alpha = alpha;
