@@ -366,8 +366,8 @@ int tlqr_kkt_residual(tlqr_factor_t *f, const tlqr_problem *prob, int32_t mem, c
  *     that needs more scratch (about N (2n + m) 8 + 12 N bytes, plus 4 N + 32 T
  *     for a forest of T trees) is rejected with TLQR_ERR_ARG before any work is
  *     issued.
- *   - The first call on a device looks up the array's device address with that
- *     device current; make that first call before any stream capture.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current.
  *   - Each call copies the plan's index arrays from host memory and waits for
  *     `stream`.
  *   - All calls share the one array and it keeps the previous call's contents:

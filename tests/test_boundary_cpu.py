@@ -173,3 +173,33 @@ def test_noalloc_residual_refuses_host_arrays():
         assert rc == tlqr.TLQR_ERR_ARG
     finally:
         tlqr.tlqr_plan_destroy(plan)
+
+
+def test_factor_options_are_validated_before_any_device_work():
+    """Out-of-range options are refused with TLQR_ERR_ARG before the call
+    touches the device (so this holds on a host without a GPU)."""
+    import ctypes
+    plan = tlqr.tlqr_plan_create(inputs.chain(8))
+    try:
+        for kw in (dict(residual=3), dict(residual=-1), dict(precision=7)):
+            base = dict(n=4, m=2, precision=tlqr.TLQR_PREC_MIXED)
+            base.update(kw)
+            o = tlqr.make_options(base.pop("n"), base.pop("m"), base.pop("precision"), **base)
+            h = ctypes.c_void_p()
+            assert tlqr.lib().tlqr_factor_create(plan, ctypes.byref(o), ctypes.byref(h)) == tlqr.TLQR_ERR_ARG
+            assert not h.value
+        o = tlqr.make_options(tlqr.TLQR_MAX_DIM + 1, 2, tlqr.TLQR_PREC_FP64)
+        h = ctypes.c_void_p()
+        assert tlqr.lib().tlqr_factor_create(plan, ctypes.byref(o), ctypes.byref(h)) == tlqr.TLQR_ERR_ARG
+    finally:
+        tlqr.tlqr_plan_destroy(plan)
+
+
+def test_update_solve_refuses_bad_arguments_without_a_device():
+    """tlqr_update_solve checks its arguments first: no factor, or a memory
+    kind that is neither host nor device, is TLQR_ERR_ARG."""
+    import ctypes
+    x, u, y = np.zeros((4, 3)), np.zeros((4, 2)), np.zeros((4, 3))
+    sol = tlqr.make_solution(x, u, y, None, None)
+    rc = tlqr.lib().tlqr_update_solve(None, tlqr.TLQR_MEM_HOST, None, None, None, None, None, ctypes.byref(sol), None)
+    assert rc == tlqr.TLQR_ERR_ARG
