@@ -771,11 +771,7 @@ def run_ours(args, rank, world, dist):
         ts, prof_plain = timed(solver, args.steps, solve, ())
         ts_k, prof = timed(solver, args.steps, solve, (dominant,))
     info = tlqr.tlqr_last_info(solver.f)
-    tot_ms = sum(ts)
-    if dist is not None:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(ts), dist, dev)
     ms_per_step = tot_ms / args.steps
     value = world * N / (ms_per_step / 1e3)
     gpu_launches = int(sum(p["launches"] for p in prof_plain.values()))
@@ -860,11 +856,7 @@ def run_ours(args, rank, world, dist):
             tlqr.tlqr_solve(solver.f, hd, hx, hu, hy, stream=stream)
             e2e_t.append(time.perf_counter() - t0)
         barrier()
-        e2e_tot = sum(e2e_t)
-        if dist is not None:
-            t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_tot = float(t.item())
+        e2e_tot = max_over_ranks(sum(e2e_t), dist, dev)
         e2e = {"value": world * N * args.steps / e2e_tot, "unit": "nodes/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
         # the interior-point / receding-horizon pattern through tlqr_update_solve: diagonal
@@ -884,11 +876,7 @@ def run_ours(args, rank, world, dist):
                                    dr=hdr if k % 2 == 0 else hdrn, stream=stream, **upd_in)
             upd_t.append(time.perf_counter() - t0)
         barrier()
-        upd_tot = sum(upd_t)
-        if dist is not None:
-            t = torch.tensor([upd_tot], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            upd_tot = float(t.item())
+        upd_tot = max_over_ranks(sum(upd_t), dist, dev)
         e2e_update = {"value": world * N * args.steps / upd_tot, "unit": "nodes/s",
                       "h2d_bytes_per_step": (hdq.numel() + hdr.numel() + sum(v.numel() for v in upd_in.values())) * 8,
                       "d2h_bytes_per_step": d2h,
@@ -978,6 +966,17 @@ def run_ours(args, rank, world, dist):
             line["forward_error_vs_oracle"] = riccati.forward_error(sol_dev, ref, w.parent)
     solver.close()
     print(json.dumps(line), flush=True)
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest `value` over the ranks of the job (the value itself with no
+    process group): the timed region of the slowest replica sets the job's time."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def main():

@@ -129,3 +129,31 @@ def test_round_roofline_with_tail_rounds():
     assert rows[-1]["round"] == f"6-{R} (tail)" and abs(rows[-1]["ms"] - tail_ms) < 1e-12
     assert rows[-1]["rakes"] == int(nr[6:].sum()) and rows[-1]["compresses"] == int(nc[6:].sum())
     assert abs(sum(r["ms"] for r in rows) - sum(x[2] for x in L)) < 1e-12
+
+
+def _max_worker(rank, world, port, out):
+    import torch.distributed as tdist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out[rank] = bench.max_over_ranks(1.5 + rank, tdist, "cpu")
+    finally:
+        tdist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    """The job time of the repo arm is the slowest rank's: every rank of a
+    two-rank gloo job gets the larger of the two values; without a process
+    group the value is returned as is."""
+    import torch.multiprocessing as mp
+    assert bench.max_over_ranks(3.25, None, "cpu") == 3.25
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_max_worker, args=(r, 2, 29531, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert dict(out) == {0: 2.5, 1: 2.5}
