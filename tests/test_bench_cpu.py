@@ -157,3 +157,23 @@ def test_max_over_ranks_two_gloo_ranks():
         p.join(120)
         assert p.exitcode == 0
     assert dict(out) == {0: 2.5, 1: 2.5}
+
+
+def test_committed_autotune_table_gives_valid_options():
+    """Every workload of the committed autotuner table maps to options that
+    the library accepts (the values the tuner tries), and its best entry is
+    the fastest of the candidates it recorded."""
+    from paper_2608_01332_b300 import autotune
+    table = autotune.load_table()
+    assert set(table) >= {"long_trunk", "batch", "spine", "serve"}
+    for name, entry in table.items():
+        opts = autotune.tuned_options(name)
+        assert opts["async_ops"] in (-1, 256, 1024, 4096)
+        assert opts["async_solve"] in (-1, 1)
+        assert opts["tail_ops"] in (-1, 0, 64, 128, 512)
+        assert opts.get("residual", 0) in (0, 1, 2)
+        o = tlqr.make_options(entry["n"], entry["m"], tlqr.TLQR_PREC_MIXED, **opts)
+        assert o.async_ops == opts["async_ops"]
+        ok = [c for c in entry["candidates"] if c["status"] == 0 and c["ms"] > 0]
+        best = min(ok, key=lambda c: c["ms"])
+        assert all(best[k] == entry["best"][k] for k in ("async_ops", "async_solve", "tail_ops"))
