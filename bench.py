@@ -193,9 +193,11 @@ def run_serve(args, rank, world, dist):
     # warm-up: every topology once (plans, factors, graphs)
     warm = []
     for t in range(len(traffic.trees)):
-        r = traffic.request(k, prec)
+        warm.append(traffic.request(k, prec))
         k += 1
-        warm.append(srv.submit(r))
+    torch.cuda.synchronize(dev)                 # request data are drawn on this thread's stream
+    for r in warm:
+        srv.submit(r)
     srv.drain()
     # capacity: a closed burst of requests
     burst = [traffic.request(k + i, prec) for i in range(args.requests)]
