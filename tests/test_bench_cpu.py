@@ -177,3 +177,24 @@ def test_committed_autotune_table_gives_valid_options():
         ok = [c for c in entry["candidates"] if c["status"] == 0 and c["ms"] > 0]
         best = min(ok, key=lambda c: c["ms"])
         assert all(best[k] == entry["best"][k] for k in ("async_ops", "async_solve", "tail_ops"))
+
+
+def test_work_model_matches_the_stated_counts():
+    """The roofline's algorithmic work per operation: the leading-order dense
+    counts (c3, n = 32: rake 26/3 n^3 + n^2 ~ 285 kflop, compression
+    50/3 n^3 + n^2 ~ 547 kflop, reconstruction 26/3 n^3, composite 2 n^3) and
+    the residual's FP64 bytes per node at c1 (n = 12, m = 4, 10 % of Delta
+    blocks nonzero): Q, A (2 f), B, R, the nonzero Delta and 8n + 4m vector
+    entries, 3,827.2 bytes."""
+    n = 32
+    fl, _ = bench.per_unit("rake", n, 8, 4)
+    assert abs(fl - (26 / 3 * n ** 3 + n ** 2)) < 1e-6 and 284e3 < fl < 286e3
+    fl, _ = bench.per_unit("compress", n, 8, 4)
+    assert 546e3 < fl < 548e3
+    assert bench.per_unit("expand", n, 8, 4)[0] == pytest.approx(26 / 3 * n ** 3)
+    assert bench.per_unit("compose_T", n, 8, 4)[0] == 2 * n ** 3
+    _, by = bench.per_unit("residual", 12, 4, 8, 0.1)
+    assert by == pytest.approx(3827.2)
+    # packed symmetric traffic: a rake reads A (f) and U, C, P and writes its contribution (4 s words)
+    _, by = bench.per_unit("rake", 12, 4, 4)
+    assert by == (144 + 4 * 78) * 4
